@@ -1,0 +1,160 @@
+/*
+ * deepinv.h -- C ABI of libdeepinv.so, the GB300 (sm_103a) hot path of
+ * DeepInverse (Mousavi & Baraniuk, "Learning to Invert: Signal Recovery via
+ * Deep Convolutional Networks", arXiv 1701.03891).
+ *
+ * The library recovers signals x in R^N from undersampled linear measurements
+ * y = Phi x in R^M (Sec. 1) with the network of Sec. 4: a fully connected
+ * layer fixed to Phi^T (x~ = Phi^T y, reshaped to n1 x n2), then three
+ * convolutional layers, Eq. (1), with 64, 32 and 1 filters of 11 x 11
+ * (Sec. 5).  It also trains that network on the MSE loss of Sec. 4.
+ *
+ * Conventions shared by every call:
+ *  - Tensor arguments are DEVICE pointers owned by the caller, contiguous,
+ *    row-major float32 unless stated otherwise.  Images are stored row-major,
+ *    pixel j = r * n2 + c (the reshape of Sec. 4).  The library never frees
+ *    caller memory and never keeps a caller pointer after the call returns.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    call is asynchronous on that stream unless its comment says otherwise.
+ *  - Arguments are checked before any launch.  A negative return value is a
+ *    deepinv_status; the outputs are then untouched and deepinv_last_error()
+ *    returns a message for the calling thread.
+ *  - No call aborts the process or traps the GPU.  Waits inside kernels are
+ *    bounded; a wait that runs out makes the call report DEEPINV_ETIMEOUT
+ *    through deepinv_device_status().
+ *  - Precision: DEEPINV_F32 runs every product in float32 on CUDA cores;
+ *    DEEPINV_BF16 runs the FC layer and the convolutions on the tcgen05 tensor
+ *    cores with bfloat16 operands (round to nearest even) and float32
+ *    accumulation.
+ */
+#ifndef DEEPINV_H
+#define DEEPINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEEPINV_OK = 0,
+    DEEPINV_EINVAL = -1,       /* bad argument: null pointer, bad size, bad shape */
+    DEEPINV_ENOMEM = -2,       /* device allocation failed */
+    DEEPINV_ECUDA = -3,        /* a CUDA runtime call failed (message in deepinv_last_error) */
+    DEEPINV_EUNSUPPORTED = -4, /* valid request this build has no kernel for */
+    DEEPINV_ETIMEOUT = -5,     /* a bounded wait ran out (in a kernel or in the server) */
+    DEEPINV_EBUSY = -6         /* admission refused: the request does not fit the budget now */
+} deepinv_status;
+
+typedef enum {
+    DEEPINV_F32 = 0,
+    DEEPINV_BF16 = 1
+} deepinv_precision;
+
+/* Network shape (Sec. 4 and Sec. 5).  The paper's network is
+ * l1 = 64, l2 = 32, l3 = 1, k = 11; the BF16 path requires exactly that,
+ * the F32 path accepts any l1, l2, l3 >= 1 and odd k <= 15. */
+typedef struct {
+    int n1, n2;      /* image rows and columns, N = n1 * n2 */
+    int M;           /* number of measurements, 1 <= M <= N */
+    int l1, l2, l3;  /* filters of conv1, conv2, conv3 */
+    int k;           /* square kernel size, odd */
+    int final_relu;  /* 1: ReLU after conv3 as well (the paper's "each layer") */
+    int train_fc;    /* 1: the FC weights are a trainable copy initialised to Phi^T */
+    int prec;        /* deepinv_precision */
+} deepinv_net_desc;
+
+typedef struct deepinv_net deepinv_net;       /* opaque; owns weights and workspace */
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char* deepinv_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int deepinv_version(void);
+
+/* Sticky device-side status of the library on the current device: DEEPINV_OK,
+ * or DEEPINV_ETIMEOUT if a bounded wait in a kernel ran out since the last
+ * reset.  Synchronises the device.  `reset` != 0 clears it. */
+int deepinv_device_status(int reset);
+
+/* y = Phi x for B signals (Sec. 1).
+ * phi [M][N], x [B][N] -> y [B][M], all float32 device memory.
+ * prec selects float32 CUDA-core products or bfloat16 tensor-core products
+ * with float32 accumulation.  B >= 0 (B == 0 is a no-op). */
+int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y,
+                    int prec, void* stream);
+
+/* Create a network (Sec. 4).  phi [M][N] is copied (it defines the FC layer,
+ * x~ = Phi^T y); w[l] is [l_l][l_{l-1}][k][k] and b[l] is [l_l] for l = 0,1,2
+ * (conv1..conv3, l_0 = 1), all device float32, copied into float32 master
+ * weights plus the kernel layouts of desc->prec.  Synchronises `stream`.
+ * On success *out owns device memory until deepinv_net_destroy. */
+int deepinv_net_create(const deepinv_net_desc* desc, const float* phi,
+                       const float* const w[3], const float* const b[3],
+                       void* stream, deepinv_net** out);
+
+/* Free everything the network owns.  Synchronises the device.  NULL is a no-op. */
+int deepinv_net_destroy(deepinv_net* net);
+
+/* Copy out the description the network was created with. */
+int deepinv_net_get_desc(const deepinv_net* net, deepinv_net_desc* desc);
+
+/* Make the network's workspace large enough for batches up to max_B so that
+ * later calls with B <= max_B allocate nothing.  Synchronises `stream`. */
+int deepinv_net_reserve(deepinv_net* net, int max_B, void* stream);
+
+/* y = Phi x with the network's own Phi (kept in the layout of its precision).
+ * x [B][N] -> y [B][M]. */
+int deepinv_net_measure(deepinv_net* net, const float* x, int B, float* y, void* stream);
+
+/* Bytes of the buffer deepinv_forward fills for deepinv_backward at batch B. */
+size_t deepinv_saved_bytes(const deepinv_net* net, int B);
+
+/* x^ = M(y, Omega) (Sec. 4): FC layer, reshape to n1 x n2, conv1 + ReLU,
+ * conv2 + ReLU, conv3 (+ ReLU when final_relu).
+ * y [B][M] -> xhat [B][N].  `saved` is NULL for inference, or a device buffer
+ * of deepinv_saved_bytes(net, B) bytes that receives the activations the
+ * backward pass needs.  Uses the network's workspace (grown if B exceeds the
+ * reserved batch, which synchronises); calls on one network must not overlap
+ * on different streams. */
+int deepinv_forward(deepinv_net* net, const float* y, int B, float* xhat, void* saved,
+                    void* stream);
+
+/* End to end on HOST memory: copy y_host [B][M] to the device, run
+ * deepinv_forward, copy x^ back to xhat_host [B][N], and wait for the copy.
+ * Host buffers should be page-locked for asynchronous copies. */
+int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xhat_host,
+                         void* stream);
+
+/* Sense and recover on HOST memory: x_host [B][N] -> y = Phi x on the device
+ * -> x^ -> xhat_host [B][N]; waits for the result. */
+int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, float* xhat_host,
+                               void* stream);
+
+/* Gradient of L(Omega) = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4) by
+ * backpropagation.  y [B][M] and x [B][N] are the batch; `saved` is the
+ * buffer a deepinv_forward of this same y filled.  Writes dW[l] (shape of
+ * w[l]), db[l] (shape of b[l]), dWfc [N][M] (only when train_fc; else pass
+ * NULL) and *loss (one device double).  All outputs are overwritten. */
+int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
+                     float* const dW[3], float* const db[3], float* dWfc, double* loss,
+                     void* stream);
+
+/* One SGD-with-momentum step on the float32 master weights:
+ * v <- mu v + g ; w <- w - lr v (momentum buffers live in the network, zero at
+ * creation), then refresh the kernel-layout copies.  dWfc is used only when
+ * train_fc. */
+int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float* const db[3],
+                         const float* dWfc, float lr, float mu, void* stream);
+
+/* Copy the float32 master weights out (any pointer may be NULL to skip it);
+ * wfc is [N][M] and is only available when train_fc. */
+int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEEPINV_H */

@@ -1,0 +1,635 @@
+// C ABI of libdeepinv (declared in include/deepinv.h): argument checks,
+// network objects (weights in float32 masters plus kernel layouts), workspace
+// management and the dispatch of the forward, backward and update passes.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace di {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static std::mutex g_status_mu;
+static std::vector<int*> g_status_words;
+
+int* device_status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if ((int)g_status_words.size() <= dev) g_status_words.resize(dev + 1, nullptr);
+    if (!g_status_words[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+        g_status_words[dev] = p;
+    }
+    return g_status_words[dev];
+}
+
+static int num_sms_current()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+// Round up to a multiple of 16 (the K granularity of one bf16 MMA).
+static inline int up16(int x) { return (x + 15) / 16 * 16; }
+
+// N tile of a GEMM whose N extent is n (16 .. 256, multiple of 16).
+static inline int gemm_nb(int n)
+{
+    const int tiles = cdiv(n, 256);
+    return up16(cdiv(n, tiles));
+}
+
+// Batch tile of the FC GEMM for batch B.
+static inline int fc_nb(int B) { return B >= 256 ? 256 : up16(B > 0 ? B : 1); }
+
+}  // namespace di
+
+using namespace di;
+
+struct deepinv_net {
+    deepinv_net_desc d;
+    int N = 0;
+    int num_sms = 1;
+    Geo geo{};
+    bool tc = false;   // bf16 tensor-core path
+    // float32 masters
+    float* phi = nullptr;
+    float* w[3] = {nullptr, nullptr, nullptr};
+    float* b[3] = {nullptr, nullptr, nullptr};
+    float* wfc = nullptr;
+    float* vw[3] = {nullptr, nullptr, nullptr};
+    float* vb[3] = {nullptr, nullptr, nullptr};
+    float* vfc = nullptr;
+    // bf16 kernel layouts
+    bf16* fcA = nullptr;    // FC: rows = pixel j, K = measurement i
+    int Kfc = 0;
+    bf16* msB = nullptr;    // measurement: rows = i, K = pixel j
+    int Kms = 0, NBms = 0;
+    bf16* w1p = nullptr;
+    bf16* w2p = nullptr;
+    bf16* w3p = nullptr;
+    // forward workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_B = 0;
+    // backward workspace
+    char* bws = nullptr;
+    size_t bws_bytes = 0;
+};
+
+namespace {
+
+struct Arena {
+    char* base;
+    size_t off;
+    template <typename T>
+    T* take(size_t n)
+    {
+        off = align_up(off, 256);
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+// Forward workspace carve-up for batch B (base == nullptr: size only).
+struct FwdWs {
+    bf16 *ypk, *xpk, *xt, *a1, *a2;
+    float *T;
+    float *fxt, *fa1, *fa2;
+    float *yd, *xd, *xhd;   // device staging of the host-memory entry points
+    size_t bytes;
+};
+
+FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
+{
+    Arena a{base, 0};
+    FwdWs w{};
+    const int N = n->N, M = n->d.M;
+    if (n->tc) {
+        const Geo& g = n->geo;
+        w.ypk = a.take<bf16>((align_up((size_t)B, 256) + 256) * n->Kfc);
+        w.xpk = a.take<bf16>(packed_elems(B, 128, n->Kms));
+        // zero-bordered planes: everything from here to `T` is cleared at allocation
+        w.xt = a.take<bf16>((size_t)B * g.plane);
+        w.a1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
+        w.a2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
+        w.T = a.take<float>(conv3_scratch_elems(g, B));
+    } else {
+        w.fxt = a.take<float>((size_t)B * N);
+        w.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
+        w.fa2 = a.take<float>((size_t)B * n->d.l2 * N);
+    }
+    w.yd = a.take<float>((size_t)B * M);
+    w.xd = a.take<float>((size_t)B * N);
+    w.xhd = a.take<float>((size_t)B * N);
+    w.bytes = align_up(a.off, 256);
+    return w;
+}
+
+// Layout of the caller's `saved` buffer at batch B.
+struct Saved {
+    bf16 *xt, *a1, *a2;      // bf16 path planes
+    float *fxt, *fa1, *fa2;  // float32 path NCHW
+    float* xhat;
+    size_t bytes;
+};
+
+Saved carve_saved(const deepinv_net* n, int B, char* base)
+{
+    Arena a{base, 0};
+    Saved s{};
+    const int N = n->N;
+    if (n->tc) {
+        const Geo& g = n->geo;
+        s.xt = a.take<bf16>((size_t)B * g.plane);
+        s.a1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
+        s.a2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
+    } else {
+        s.fxt = a.take<float>((size_t)B * N);
+        s.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
+        s.fa2 = a.take<float>((size_t)B * n->d.l2 * N);
+    }
+    s.xhat = a.take<float>((size_t)B * N);
+    s.bytes = align_up(a.off, 256);
+    return s;
+}
+
+int ensure_ws(deepinv_net* n, int B, cudaStream_t st)
+{
+    if (B <= n->ws_B && n->ws) return DEEPINV_OK;
+    const FwdWs need = carve_fwd(n, B, nullptr);
+    DI_CUDA(cudaStreamSynchronize(st));
+    if (n->ws) {
+        DI_CUDA(cudaFree(n->ws));
+        n->ws = nullptr;
+        n->ws_B = 0;
+        n->ws_bytes = 0;
+    }
+    char* p = nullptr;
+    if (cudaMalloc(&p, need.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("workspace of %zu bytes for batch %d: out of device memory", need.bytes, B);
+        return DEEPINV_ENOMEM;
+    }
+    DI_CUDA(cudaMemset(p, 0, need.bytes));
+    n->ws = p;
+    n->ws_bytes = need.bytes;
+    n->ws_B = B;
+    return DEEPINV_OK;
+}
+
+int check_desc(const deepinv_net_desc* d)
+{
+    DI_REQUIRE(d, "desc is NULL");
+    DI_REQUIRE(d->n1 >= 1 && d->n2 >= 1 && (long long)d->n1 * d->n2 <= (1 << 24),
+               "bad image size %d x %d", d->n1, d->n2);
+    DI_REQUIRE(d->M >= 1 && d->M <= d->n1 * d->n2, "bad M = %d for N = %d", d->M, d->n1 * d->n2);
+    DI_REQUIRE(d->l1 >= 1 && d->l2 >= 1 && d->l3 == 1, "filters (%d, %d, %d): need l1, l2 >= 1, l3 = 1",
+               d->l1, d->l2, d->l3);
+    DI_REQUIRE(d->k >= 1 && d->k <= 15 && d->k % 2 == 1, "kernel size %d must be odd and <= 15", d->k);
+    DI_REQUIRE(d->prec == DEEPINV_F32 || d->prec == DEEPINV_BF16, "unknown precision %d", d->prec);
+    if (d->prec == DEEPINV_BF16) {
+        if (d->l1 != 64 || d->l2 != 32 || d->k != 11) {
+            set_error("bf16 path is built for the paper network (64, 32, 1 filters of 11 x 11)");
+            return DEEPINV_EUNSUPPORTED;
+        }
+        if (!conv2_tc_supported(make_geo(d->n1, d->n2))) {
+            set_error("bf16 path: image width %d not supported yet", d->n2);
+            return DEEPINV_EUNSUPPORTED;
+        }
+    }
+    return DEEPINV_OK;
+}
+
+int repack(deepinv_net* n, cudaStream_t st)
+{
+    if (!n->tc) return DEEPINV_OK;
+    const int N = n->N, M = n->d.M;
+    DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[2], n->w1p, n->w2p, n->w3p, st));
+    // FC operand (rows = pixel j, K = measurement i): Phi^T or the trained copy.
+    if (n->wfc) DI_TRY(pack_kmajor(n->wfc, M, 1, N, M, 128, n->Kfc, n->fcA, st));
+    else DI_TRY(pack_kmajor(n->phi, 1, N, N, M, 128, n->Kfc, n->fcA, st));
+    return DEEPINV_OK;
+}
+
+void free_net(deepinv_net* n)
+{
+    if (!n) return;
+    cudaFree(n->phi);
+    for (int l = 0; l < 3; ++l) {
+        cudaFree(n->w[l]);
+        cudaFree(n->b[l]);
+        cudaFree(n->vw[l]);
+        cudaFree(n->vb[l]);
+    }
+    cudaFree(n->wfc);
+    cudaFree(n->vfc);
+    cudaFree(n->fcA);
+    cudaFree(n->msB);
+    cudaFree(n->w1p);
+    cudaFree(n->w2p);
+    cudaFree(n->w3p);
+    cudaFree(n->ws);
+    cudaFree(n->bws);
+    delete n;
+}
+
+size_t wsize(const deepinv_net* n, int l)
+{
+    const int cin = l == 0 ? 1 : (l == 1 ? n->d.l1 : n->d.l2);
+    const int cout = l == 0 ? n->d.l1 : (l == 1 ? n->d.l2 : n->d.l3);
+    return (size_t)cout * cin * n->d.k * n->d.k;
+}
+
+size_t bsize(const deepinv_net* n, int l) { return (size_t)(l == 0 ? n->d.l1 : (l == 1 ? n->d.l2 : n->d.l3)); }
+
+template <typename T>
+int dev_alloc(T** p, size_t n)
+{
+    if (n == 0) n = 1;
+    if (cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed", n * sizeof(T));
+        return DEEPINV_ENOMEM;
+    }
+    return DEEPINV_OK;
+}
+
+int measure_bf16_packed(const bf16* phiB, int Kp, int NB, const float* x, int N, int M, int B, float* y,
+                        bf16* xpk, cudaStream_t st)
+{
+    int* status = device_status_word();
+    DI_REQUIRE(status, "no device status word");
+    DI_TRY(pack_kmajor(x, N, 1, B, N, 128, Kp, xpk, st));
+    Geo dummy{};
+    return tc_gemm(xpk, phiB, Kp, B, M, NB, GEMM_OUT_F32, y, M, nullptr, dummy, status, st);
+}
+
+int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved, cudaStream_t st)
+{
+    if (B == 0) return DEEPINV_OK;
+    DI_TRY(ensure_ws(n, B, st));
+    // carve at the allocated batch so that plane offsets never move
+    const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
+    const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2, k = n->d.k;
+    Saved sv{};
+    if (saved) {
+        sv = carve_saved(n, B, static_cast<char*>(saved));
+        DI_CUDA(cudaMemsetAsync(saved, 0, sv.bytes, st));
+    }
+    if (n->tc) {
+        const Geo& g = n->geo;
+        int* status = device_status_word();
+        DI_REQUIRE(status, "no device status word");
+        bf16* xt = saved ? sv.xt : w.xt;
+        bf16* a1 = saved ? sv.a1 : w.a1;
+        bf16* a2 = saved ? sv.a2 : w.a2;
+        const int nb = fc_nb(B);
+        DI_TRY(pack_kmajor(y, M, 1, B, M, nb, n->Kfc, w.ypk, st));
+        DI_TRY(tc_gemm(n->fcA, w.ypk, n->Kfc, N, B, nb, GEMM_OUT_PLANE, nullptr, 0, xt, g, status, st));
+        DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, status, st));
+        DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], a2, n->num_sms, status, st));
+        DI_TRY(conv3_tc(a2, B, g, n->w3p, n->b[2], w.T, xhat, n->d.final_relu, status, st));
+    } else {
+        float* xt = saved ? sv.fxt : w.fxt;
+        float* a1 = saved ? sv.fa1 : w.fa1;
+        float* a2 = saved ? sv.fa2 : w.fa2;
+        if (n->wfc) DI_TRY(sgemm(B, N, M, y, M, 1, n->wfc, 1, M, xt, N, st));
+        else DI_TRY(sgemm(B, N, M, y, M, 1, n->phi, N, 1, xt, N, st));
+        DI_TRY(conv_f32(xt, B, 1, H, W, n->w[0], n->b[0], n->d.l1, k, a1, 1, st));
+        DI_TRY(conv_f32(a1, B, n->d.l1, H, W, n->w[1], n->b[1], n->d.l2, k, a2, 1, st));
+        DI_TRY(conv_f32(a2, B, n->d.l2, H, W, n->w[2], n->b[2], 1, k, xhat, n->d.final_relu, st));
+    }
+    if (saved) DI_CUDA(cudaMemcpyAsync(sv.xhat, xhat, (size_t)B * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return DEEPINV_OK;
+}
+
+int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream_t st)
+{
+    if (B == 0) return DEEPINV_OK;
+    const int N = n->N, M = n->d.M;
+    if (n->tc) {
+        DI_TRY(ensure_ws(n, B, st));
+        const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
+        return measure_bf16_packed(n->msB, n->Kms, n->NBms, x, N, M, B, y, w.xpk, st);
+    }
+    return sgemm(B, M, N, x, N, 1, n->phi, 1, N, y, M, st);
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* deepinv_last_error(void) { return di::g_err; }
+
+int deepinv_version(void) { return 100; }
+
+int deepinv_device_status(int reset)
+{
+    int* p = device_status_word();
+    DI_REQUIRE(p, "no CUDA device");
+    DI_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    DI_CUDA(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset) DI_CUDA(cudaMemset(p, 0, sizeof(int)));
+    if (v == DEV_TIMEOUT) {
+        set_error("a bounded wait inside a kernel ran out");
+        return DEEPINV_ETIMEOUT;
+    }
+    return DEEPINV_OK;
+}
+
+int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y, int prec, void* stream)
+{
+    DI_REQUIRE(M >= 1 && N >= 1 && B >= 0, "bad sizes M=%d N=%d B=%d", M, N, B);
+    DI_REQUIRE(B == 0 || (phi && x && y), "null pointer");
+    DI_REQUIRE(prec == DEEPINV_F32 || prec == DEEPINV_BF16, "unknown precision %d", prec);
+    if (B == 0) return DEEPINV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prec == DEEPINV_F32) return sgemm(B, M, N, x, N, 1, phi, 1, N, y, M, st);
+    const int Kp = up16(N), NB = gemm_nb(M);
+    bf16* phiB = nullptr;
+    bf16* xpk = nullptr;
+    const size_t nphi = packed_elems(M, NB, Kp), nx = packed_elems(B, 128, Kp);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&phiB), nphi * sizeof(bf16), st) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&xpk), nx * sizeof(bf16), st) != cudaSuccess) {
+        cudaGetLastError();
+        if (phiB) cudaFreeAsync(phiB, st);
+        set_error("deepinv_measure: out of device memory");
+        return DEEPINV_ENOMEM;
+    }
+    int rc = pack_kmajor(phi, N, 1, M, N, NB, Kp, phiB, st);
+    if (rc == DEEPINV_OK) rc = measure_bf16_packed(phiB, Kp, NB, x, N, M, B, y, xpk, st);
+    cudaFreeAsync(phiB, st);
+    cudaFreeAsync(xpk, st);
+    return rc;
+}
+
+int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const float* const w[3],
+                       const float* const b[3], void* stream, deepinv_net** out)
+{
+    DI_REQUIRE(out, "out is NULL");
+    DI_TRY(check_desc(desc));
+    DI_REQUIRE(phi && w && b, "null pointer");
+    for (int l = 0; l < 3; ++l) DI_REQUIRE(w[l] && b[l], "null weight pointer for layer %d", l + 1);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    deepinv_net* n = new (std::nothrow) deepinv_net();
+    DI_REQUIRE(n, "host allocation failed");
+    n->d = *desc;
+    n->N = desc->n1 * desc->n2;
+    n->tc = desc->prec == DEEPINV_BF16;
+    n->num_sms = num_sms_current();
+    const int N = n->N, M = desc->M;
+    int rc = DEEPINV_OK;
+#define DI_STEP(x) do { rc = (x); if (rc != DEEPINV_OK) { free_net(n); return rc; } } while (0)
+    DI_STEP(dev_alloc(&n->phi, (size_t)M * N));
+    DI_STEP(cudaMemcpyAsync(n->phi, phi, (size_t)M * N * sizeof(float), cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                ? DEEPINV_OK : DEEPINV_ECUDA);
+    for (int l = 0; l < 3; ++l) {
+        DI_STEP(dev_alloc(&n->w[l], wsize(n, l)));
+        DI_STEP(dev_alloc(&n->b[l], bsize(n, l)));
+        DI_STEP(dev_alloc(&n->vw[l], wsize(n, l)));
+        DI_STEP(dev_alloc(&n->vb[l], bsize(n, l)));
+        DI_STEP(cudaMemcpyAsync(n->w[l], w[l], wsize(n, l) * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                    ? DEEPINV_OK : DEEPINV_ECUDA);
+        DI_STEP(cudaMemcpyAsync(n->b[l], b[l], bsize(n, l) * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                    ? DEEPINV_OK : DEEPINV_ECUDA);
+        DI_STEP(cudaMemsetAsync(n->vw[l], 0, wsize(n, l) * 4, st) == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
+        DI_STEP(cudaMemsetAsync(n->vb[l], 0, bsize(n, l) * 4, st) == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
+    }
+    if (desc->train_fc) {
+        DI_STEP(dev_alloc(&n->wfc, (size_t)N * M));
+        DI_STEP(dev_alloc(&n->vfc, (size_t)N * M));
+        DI_STEP(cudaMemsetAsync(n->vfc, 0, (size_t)N * M * 4, st) == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
+    }
+    if (n->tc) {
+        n->geo = make_geo(desc->n1, desc->n2);
+        n->Kfc = up16(M);
+        n->Kms = up16(N);
+        n->NBms = gemm_nb(M);
+        DI_STEP(dev_alloc(&n->fcA, packed_elems(N, 128, n->Kfc)));
+        DI_STEP(dev_alloc(&n->msB, packed_elems(M, n->NBms, n->Kms)));
+        DI_STEP(dev_alloc(&n->w1p, kW1PackElems));
+        DI_STEP(dev_alloc(&n->w2p, kW2PackElems));
+        DI_STEP(dev_alloc(&n->w3p, kW3PackElems));
+        DI_STEP(pack_kmajor(n->phi, N, 1, M, N, n->NBms, n->Kms, n->msB, st));
+    }
+    if (desc->train_fc) DI_STEP(transpose_f32(n->phi, M, N, n->wfc, st));
+    DI_STEP(repack(n, st));
+    DI_STEP(cudaStreamSynchronize(st) == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
+#undef DI_STEP
+    *out = n;
+    return DEEPINV_OK;
+}
+
+int deepinv_net_destroy(deepinv_net* net)
+{
+    if (!net) return DEEPINV_OK;
+    cudaDeviceSynchronize();
+    free_net(net);
+    return DEEPINV_OK;
+}
+
+int deepinv_net_get_desc(const deepinv_net* net, deepinv_net_desc* desc)
+{
+    DI_REQUIRE(net && desc, "null pointer");
+    *desc = net->d;
+    return DEEPINV_OK;
+}
+
+int deepinv_net_reserve(deepinv_net* net, int max_B, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(max_B >= 0, "bad batch %d", max_B);
+    if (max_B == 0) return DEEPINV_OK;
+    return ensure_ws(net, max_B, static_cast<cudaStream_t>(stream));
+}
+
+int deepinv_net_measure(deepinv_net* net, const float* x, int B, float* y, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B == 0 || (x && y), "null pointer");
+    return net_measure_impl(net, x, B, y, static_cast<cudaStream_t>(stream));
+}
+
+size_t deepinv_saved_bytes(const deepinv_net* net, int B)
+{
+    if (!net || B <= 0) return 0;
+    return carve_saved(net, B, nullptr).bytes;
+}
+
+int deepinv_forward(deepinv_net* net, const float* y, int B, float* xhat, void* saved, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B == 0 || (y && xhat), "null pointer");
+    return forward_impl(net, y, B, xhat, saved, static_cast<cudaStream_t>(stream));
+}
+
+int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xhat_host, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B == 0 || (y_host && xhat_host), "null pointer");
+    if (B == 0) return DEEPINV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DI_TRY(ensure_ws(net, B, st));
+    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
+    DI_CUDA(cudaMemcpyAsync(w.yd, y_host, (size_t)B * net->d.M * sizeof(float), cudaMemcpyHostToDevice, st));
+    DI_TRY(forward_impl(net, w.yd, B, w.xhd, nullptr, st));
+    DI_CUDA(cudaMemcpyAsync(xhat_host, w.xhd, (size_t)B * net->N * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DI_CUDA(cudaStreamSynchronize(st));
+    return DEEPINV_OK;
+}
+
+int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, float* xhat_host, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B == 0 || (x_host && xhat_host), "null pointer");
+    if (B == 0) return DEEPINV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DI_TRY(ensure_ws(net, B, st));
+    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
+    DI_CUDA(cudaMemcpyAsync(w.xd, x_host, (size_t)B * net->N * sizeof(float), cudaMemcpyHostToDevice, st));
+    DI_TRY(net_measure_impl(net, w.xd, B, w.yd, st));
+    DI_TRY(forward_impl(net, w.yd, B, w.xhd, nullptr, st));
+    DI_CUDA(cudaMemcpyAsync(xhat_host, w.xhd, (size_t)B * net->N * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DI_CUDA(cudaStreamSynchronize(st));
+    return DEEPINV_OK;
+}
+
+int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
+                     float* const dW[3], float* const db[3], float* dWfc, double* loss, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(B >= 1, "bad batch %d", B);
+    DI_REQUIRE(y && x && saved && dW && db && loss, "null pointer");
+    for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
+    DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
+    const int l1 = net->d.l1, l2 = net->d.l2;
+    const Saved sv = carve_saved(net, B, static_cast<char*>(const_cast<void*>(saved)));
+
+    size_t maxw = 0;
+    for (int l = 0; l < 3; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;
+    auto carve_bwd = [&](char* base, float** g3, float** gA, float** gB, float** dxt, float** fxt, float** fa1,
+                         float** fa2, float** wt, double** wpart, double** lpart) {
+        Arena a{base, 0};
+        *g3 = a.take<float>((size_t)B * N);
+        *gA = a.take<float>((size_t)B * l2 * N);
+        *gB = a.take<float>((size_t)B * l1 * N);
+        *dxt = a.take<float>((size_t)B * N);
+        if (net->tc) {
+            *fxt = a.take<float>((size_t)B * N);
+            *fa1 = a.take<float>((size_t)B * l1 * N);
+            *fa2 = a.take<float>((size_t)B * l2 * N);
+        } else {
+            *fxt = sv.fxt;
+            *fa1 = sv.fa1;
+            *fa2 = sv.fa2;
+        }
+        *wt = a.take<float>(maxw);
+        *wpart = a.take<double>((size_t)kWgradChunks * maxw);
+        *lpart = a.take<double>(kLossBlocks);
+        return align_up(a.off, 256);
+    };
+    float *g3, *gA, *gB, *dxt, *fxt, *fa1, *fa2, *wt;
+    double *wpart, *lpart;
+    const size_t need = carve_bwd(nullptr, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+    if (need > net->bws_bytes) {
+        DI_CUDA(cudaStreamSynchronize(st));
+        cudaFree(net->bws);
+        net->bws = nullptr;
+        net->bws_bytes = 0;
+        if (cudaMalloc(&net->bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            net->bws = nullptr;
+            set_error("backward workspace of %zu bytes: out of device memory", need);
+            return DEEPINV_ENOMEM;
+        }
+        net->bws_bytes = need;
+    }
+    carve_bwd(net->bws, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+
+    if (net->tc) {
+        DI_TRY(plane_to_nchw(sv.xt, B, 1, net->geo, fxt, st));
+        DI_TRY(plane_to_nchw(sv.a1, B, l1, net->geo, fa1, st));
+        DI_TRY(plane_to_nchw(sv.a2, B, l2, net->geo, fa2, st));
+    }
+    // dL/dz3 = 2 (x^ - x) / B, and the loss in float64
+    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, B, net->d.final_relu, g3, lpart, loss, st));
+    // conv3
+    DI_TRY(conv_wgrad_f32(fa2, g3, B, l2, H, W, 1, k, wpart, dW[2], db[2], st));
+    DI_TRY(conv_dgrad_f32(g3, B, 1, H, W, net->w[2], l2, k, wt, gA, st));
+    DI_TRY(relu_mask_f32(gA, fa2, (long long)B * l2 * N, st));
+    // conv2
+    DI_TRY(conv_wgrad_f32(fa1, gA, B, l1, H, W, l2, k, wpart, dW[1], db[1], st));
+    DI_TRY(conv_dgrad_f32(gA, B, l2, H, W, net->w[1], l1, k, wt, gB, st));
+    DI_TRY(relu_mask_f32(gB, fa1, (long long)B * l1 * N, st));
+    // conv1
+    DI_TRY(conv_wgrad_f32(fxt, gB, B, 1, H, W, l1, k, wpart, dW[0], db[0], st));
+    if (net->d.train_fc) {
+        DI_TRY(conv_dgrad_f32(gB, B, l1, H, W, net->w[0], 1, k, wt, dxt, st));
+        // dWfc[j][i] = sum_b dx~[b][j] y[b][i]
+        DI_TRY(sgemm(N, M, B, dxt, 1, N, y, M, 1, dWfc, M, st));
+    }
+    return DEEPINV_OK;
+}
+
+int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float* const db[3], const float* dWfc,
+                         float lr, float mu, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(dW && db, "null pointer");
+    for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
+    DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int l = 0; l < 3; ++l) {
+        DI_TRY(sgd_momentum_f32(net->w[l], net->vw[l], dW[l], (long long)wsize(net, l), lr, mu, st));
+        DI_TRY(sgd_momentum_f32(net->b[l], net->vb[l], db[l], (long long)bsize(net, l), lr, mu, st));
+    }
+    if (net->d.train_fc)
+        DI_TRY(sgd_momentum_f32(net->wfc, net->vfc, dWfc, (long long)net->N * net->d.M, lr, mu, st));
+    return repack(net, st);
+}
+
+int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int l = 0; l < 3; ++l) {
+        if (w && w[l]) DI_CUDA(cudaMemcpyAsync(w[l], net->w[l], wsize(net, l) * 4, cudaMemcpyDeviceToDevice, st));
+        if (b && b[l]) DI_CUDA(cudaMemcpyAsync(b[l], net->b[l], bsize(net, l) * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    if (wfc) {
+        DI_REQUIRE(net->wfc, "network has no trainable FC weights");
+        DI_CUDA(cudaMemcpyAsync(wfc, net->wfc, (size_t)net->N * net->d.M * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return DEEPINV_OK;
+}
+
+}  // extern "C"

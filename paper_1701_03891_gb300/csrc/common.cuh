@@ -1,0 +1,104 @@
+// Shared host/device helpers of libdeepinv: status reporting, checks, and the
+// padded-plane geometry that the bfloat16 tensor-core path lays images out in.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "deepinv.h"
+
+namespace di {
+
+// Thread-local message for deepinv_last_error().
+void set_error(const char* fmt, ...);
+
+// Per-device sticky status word that kernels with bounded waits write into.
+int* device_status_word();
+
+#define DI_REQUIRE(cond, ...)                 \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::di::set_error(__VA_ARGS__);     \
+            return DEEPINV_EINVAL;            \
+        }                                     \
+    } while (0)
+
+#define DI_CUDA(call)                                                               \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::di::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                            __FILE__, __LINE__);                                    \
+            return DEEPINV_ECUDA;                                                   \
+        }                                                                           \
+    } while (0)
+
+#define DI_LAUNCH_CHECK() DI_CUDA(cudaGetLastError())
+
+#define DI_TRY(expr)                  \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != DEEPINV_OK) return rc_; \
+    } while (0)
+
+// Device-side status codes written to the status word.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+// Time limit of one bounded wait inside a kernel, in nanoseconds.
+constexpr unsigned long long kWaitLimitNs = 1000ull * 1000ull * 1000ull;  // 1 s
+
+static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Geometry of the padded image planes used by the bfloat16 path.
+//
+// An n1 x n2 image is stored with a row pitch P = n2 + 5: every row carries
+// its n2 pixels followed by five zeros.  With a half-width of five (11 x 11
+// kernels) those five zeros serve both as the right border of a row and the
+// left border of the next one, so that every tap (dy, dx) of output position
+// q = r * P + c reads input position q + dy * P + dx of the plane (the crop S
+// of Eq. 1 is then the 'same' zero padding).  Pixel (r, c) lives at plane
+// index q + 5 P + 5; the first 5 P + 5 entries and everything after the last
+// row are zero.  Output positions with c >= n2 are computed and discarded.
+struct Geo {
+    int H, W, P;   // rows, columns, pitch
+    int HP;        // H * P output positions per image
+    int t1;        // conv1 tiles (128 positions) per image
+    int t2;        // conv2 tiles (kConv2Valid positions) per image
+    int t3;        // conv3 row-sum blocks (128 positions) per image
+    int nslab;     // conv2 window slabs of kSlabPx positions
+    int plane;     // positions per image plane (multiple of 8)
+};
+
+constexpr int kPad = 5;            // (k - 1) / 2 for k = 11
+constexpr int kConv2N = 256;       // MMA N of conv2 (positions per tile)
+constexpr int kConv2Valid = 253;   // outputs a conv2 tile completes (256 - 3)
+constexpr int kSlabPx = 128;       // conv2 window slab
+constexpr int kConv2Reach = 10;    // rows of halo below an output row (k - 1)
+
+static inline Geo make_geo(int H, int W)
+{
+    Geo g;
+    g.H = H;
+    g.W = W;
+    g.P = W + kPad;
+    g.HP = H * g.P;
+    g.t1 = cdiv(g.HP, 128);
+    g.t2 = cdiv(g.HP, kConv2Valid);
+    // conv3 computes row partial sums T[p] for p in [0, (H + 10) P).
+    g.t3 = cdiv((H + kConv2Reach) * g.P, 128);
+    const int win2 = kConv2Reach * g.P + 8 + kConv2N;    // positions one conv2 tile reads
+    g.nslab = cdiv(win2, kSlabPx);
+    size_t need = 0;
+    auto upd = [&](size_t v) { if (v > need) need = v; };
+    upd((size_t)(g.t2 - 1) * kConv2Valid + (size_t)g.nslab * kSlabPx);     // conv2 window
+    upd((size_t)g.t1 * 128 + (size_t)kConv2Reach * g.P + 16);              // conv1 im2col window
+    upd((size_t)g.t3 * 128 + 16);                                          // conv3 window
+    upd((size_t)(H + 2 * kPad) * g.P + 2 * kPad);                          // data + borders
+    g.plane = (int)align_up(need, 8);
+    return g;
+}
+
+}  // namespace di

@@ -1,0 +1,70 @@
+// Host-side launchers of the libdeepinv kernels (declarations).
+#pragma once
+
+#include "common.cuh"
+
+namespace di {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------- float32 path (f32_kernels.cu)
+constexpr int kWgradChunks = 64;   // pixel chunks of the float32 weight-gradient reduction
+constexpr int kLossBlocks = 256;   // partial sums of the loss reduction
+
+int sgemm(int Mr, int Nc, int K, const float* A, long long sam, long long sak, const float* B,
+          long long sbk, long long sbn, float* C, long long ldc, cudaStream_t st);
+int conv_f32(const float* in, int B, int Cin, int H, int W, const float* w, const float* bias,
+             int Cout, int k, float* out, int relu, cudaStream_t st);
+int conv_dgrad_f32(const float* g, int B, int Cout, int H, int W, const float* w, int Cin, int k,
+                   float* wt_scratch, float* din, cudaStream_t st);
+size_t wgrad_scratch_bytes(int Cout, int Cin, int k);
+int conv_wgrad_f32(const float* in, const float* g, int B, int Cin, int H, int W, int Cout, int k,
+                   double* scratch, float* dw, float* db, cudaStream_t st);
+int relu_mask_f32(float* g, const float* a, long long n, cudaStream_t st);
+int mse_loss_grad(const float* xhat, const float* x, long long n, int B, int final_relu, float* g,
+                  double* part, double* loss, cudaStream_t st);
+int transpose_f32(const float* src, int R, int C, float* dst, cudaStream_t st);
+int sgd_momentum_f32(float* w, float* v, const float* g, long long n, float lr, float mu,
+                     cudaStream_t st);
+
+// ---------------------------------------------------------------- bfloat16 tensor-core path (tc_kernels.cu)
+// Packed K-major operand: dst holds ceil(R / TR) row tiles, each Kp / 8
+// chunks of TR rows x 8 bf16 (16 bytes per row), i.e. element (r, k) at
+// ((r / TR * (Kp / 8) + k / 8) * TR + r % TR) * 8 + k % 8.  Source element
+// (r, k) = src[r * rs + k * cs]; zero outside R x K.
+size_t packed_elems(int R, int TR, int Kp);
+int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int TR, int Kp,
+                bf16* dst, cudaStream_t st);
+
+// Weight layouts of the paper network (l1 = 64, l2 = 32, l3 = 1, k = 11).
+constexpr size_t kW1PackElems = 16 * 64 * 8;             // [16 chunks][64 rows][8]
+constexpr size_t kW2PackElems = 11 * 3 * 4 * 2 * 128 * 8;  // [dy][s][kk][2][128][8]
+constexpr size_t kW3PackElems = 11 * 2 * 2 * 16 * 8;     // [dx][kk][2][16][8]
+int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p,
+                      bf16* w3p, cudaStream_t st);
+
+enum GemmOut { GEMM_OUT_F32 = 0, GEMM_OUT_PLANE = 1 };
+
+// D[m][n] = sum_k A[m][k] B[n][k] over packed operands (A: TR = 128, B: TR =
+// NB).  GEMM_OUT_F32 writes out_f32[m * ldo + n] for m < Mr, n < Nc;
+// GEMM_OUT_PLANE treats m as pixel j of an n1 x n2 image and n as the image
+// index, writing bf16 to plane[n * geo.plane + L(j)].
+int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mode, float* out_f32,
+            long long ldo, bf16* plane, const Geo& geo, int* status, cudaStream_t st);
+
+// conv1: x~ plane [B][plane] -> a1 [B][8][plane][8] (bias, ReLU, zero pad columns).
+int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, bf16* a1,
+             int* status, cudaStream_t st);
+// conv2: a1 -> a2 [B][4][plane][8] (bias, ReLU, zero pad columns).
+int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* b2, bf16* a2,
+             int num_sms, int* status, cudaStream_t st);
+bool conv2_tc_supported(const Geo& g);
+// conv3: a2 -> row partial sums T [B][11][t3 * 128] -> xhat [B][n1 * n2] float32.
+size_t conv3_scratch_elems(const Geo& g, int B);
+int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* b3, float* T,
+             float* xhat, int final_relu, int* status, cudaStream_t st);
+
+// Layout conversions for the backward pass (bf16 planes -> float32 NCHW).
+int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st);
+
+}  // namespace di

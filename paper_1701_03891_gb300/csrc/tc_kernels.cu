@@ -1,0 +1,801 @@
+// bfloat16 tcgen05 tensor-core kernels of libdeepinv (sm_103a).
+//
+//  * tc_gemm   -- y = Phi x (Sec. 1) and the FC layer x~ = Phi^T y (Sec. 4).
+//  * conv1_tc  -- Eq. (1), layer 1 (1 -> 64 filters of 11 x 11) as an
+//                 im2col GEMM: M = 128 positions, N = 64 filters, K = 121 taps.
+//  * conv2_tc  -- layer 2 (64 -> 32), 95 % of the network's flops, as a
+//                 tap-stacked implicit GEMM (below).
+//  * conv3_tc  -- layer 3 (32 -> 1): per-row partial sums T by GEMM
+//                 (M = 128 positions, N = 11 kernel rows, K = 11 columns x 32
+//                 channels), then a sum over the 11 kernel rows.
+//
+// All operands are K-major without swizzle (see tc.cuh), moved by the TMA
+// engine with 1-D bulk copies; accumulators live in TMEM.
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace di {
+
+using namespace tc;
+
+namespace {
+
+__device__ __forceinline__ uint4 pack8_bf16(const float* v)
+{
+    uint4 r;
+    uint32_t* u = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        u[i] = *reinterpret_cast<uint32_t*>(&p);
+    }
+    return r;
+}
+
+// Wait that ignores the abort flag: used on exit to let copies in flight land.
+__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > 1000000000ull) return;
+    }
+}
+
+// ---------------------------------------------------------------- packing
+__global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, long long cs, int R,
+                                   int K, int TR, int Kp, long long nchunks, bf16* __restrict__ dst)
+{
+    const int kcs = Kp / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nchunks;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int rr = (int)(i % TR);
+        const int kc = (int)((i / TR) % kcs);
+        const long long rt = i / ((long long)TR * kcs);
+        const long long r = rt * TR + rr;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = kc * 8 + e;
+            v[e] = (r < R && k < K) ? src[r * rs + (long long)k * cs] : 0.f;
+        }
+        reinterpret_cast<uint4*>(dst)[i] = pack8_bf16(v);
+    }
+}
+
+// conv1 B operand: (n = filter co, k = tap t = 11 dy + dx), t >= 121 zero.
+// conv2 A operand: block (dy, s, kk) holds rows m = 4 co + g (g = tap slot),
+//   K = input channels 16 kk .. 16 kk + 15, weight W2[co][ci][dy][4 s + g]
+//   (zero when 4 s + g = 11).
+// conv3 B operand: block (dx, kk) holds rows n = dy (zero for dy >= 11),
+//   K = channels 16 kk .. 16 kk + 15, weight W3[0][ci][dy][dx].
+__global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const float* __restrict__ w2,
+                                         const float* __restrict__ w3, bf16* __restrict__ w1p,
+                                         bf16* __restrict__ w2p, bf16* __restrict__ w3p)
+{
+    const long long n1 = kW1PackElems, n2 = kW2PackElems, n3 = kW3PackElems;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n1 + n2 + n3;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < n1) {
+            const int e = (int)(i % 8), co = (int)((i / 8) % 64), kc = (int)(i / (8 * 64));
+            const int t = kc * 8 + e;
+            const float v = t < 121 ? w1[co * 121 + t] : 0.f;
+            w1p[i] = __float2bfloat16_rn(v);
+        } else if (i < n1 + n2) {
+            const long long j = i - n1;
+            const int e = (int)(j % 8);
+            const int m = (int)((j / 8) % 128);
+            const int half = (int)((j / (8 * 128)) % 2);
+            const int kk = (int)((j / (8 * 128 * 2)) % 4);
+            const int s = (int)((j / (8 * 128 * 2 * 4)) % 3);
+            const int dy = (int)(j / (8 * 128 * 2 * 4 * 3));
+            const int co = m / 4, g = m % 4, dx = 4 * s + g, ci = kk * 16 + half * 8 + e;
+            const float v = dx < 11 ? w2[((co * 64 + ci) * 11 + dy) * 11 + dx] : 0.f;
+            w2p[j] = __float2bfloat16_rn(v);
+        } else {
+            const long long j = i - n1 - n2;
+            const int e = (int)(j % 8);
+            const int n = (int)((j / 8) % 16);
+            const int half = (int)((j / (8 * 16)) % 2);
+            const int kk = (int)((j / (8 * 16 * 2)) % 2);
+            const int dx = (int)(j / (8 * 16 * 2 * 2));
+            const int ci = kk * 16 + half * 8 + e;
+            const float v = n < 11 ? w3[(ci * 11 + n) * 11 + dx] : 0.f;
+            w3p[j] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- GEMM
+// One 128 x NB output tile per CTA; K in stages of kGemmKS MMA steps (16 each).
+// Warp 0 lane 0: producer (bulk copies).  Warp 1: TMEM owner and MMA issuer.
+// Warps 2..5: epilogue (TMEM lane quarter = warp % 4).
+constexpr int kGemmKS = 4;
+constexpr int kGemmNS = 3;
+
+struct GemmSmem {
+    uint64_t full[kGemmNS], empty[kGemmNS], acc_full, drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ int plane_index(int j, int W, int P) { return (j / W) * P + (j % W) + kPad * P + kPad; }
+
+template <int MODE>
+__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict__ A, const bf16* __restrict__ Bm,
+                                                         int Kp, int Mr, int Nc, int NB, uint32_t tmem_cols,
+                                                         float* __restrict__ out_f32, long long ldo,
+                                                         bf16* __restrict__ plane, int H, int W, int P,
+                                                         int plane_len, int* status)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = smem_raw;
+    const uint32_t a_stage = kGemmKS * 4096;
+    const uint32_t b_stage = (uint32_t)kGemmKS * NB * 32;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kGemmNS * a_stage;
+    GemmSmem* ss = reinterpret_cast<GemmSmem*>(sB + kGemmNS * b_stage);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    const int nsteps = Kp / 16;
+    const int nstages = (nsteps + kGemmKS - 1) / kGemmKS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGemmNS; ++s) {
+            mbar_init(smem_u32(&ss->full[s]), 1);
+            mbar_init(smem_u32(&ss->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&ss->acc_full), 1);
+        mbar_init(smem_u32(&ss->drain), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&ss->tmem_base), tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        const bf16* Ablk = A + (size_t)mt * (Kp / 8) * 128 * 8;
+        const bf16* Bblk = Bm + (size_t)nt * (Kp / 8) * NB * 8;
+        int armed_parity[kGemmNS];
+        for (int s = 0; s < kGemmNS; ++s) armed_parity[s] = -1;
+        for (int st = 0; st < nstages; ++st) {
+            const int slot = st % kGemmNS, n = st / kGemmNS;
+            if (!mbar_wait(smem_u32(&ss->empty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) break;
+            const int k0 = st * kGemmKS;
+            const int ks = min(kGemmKS, nsteps - k0);
+            const uint32_t abytes = ks * 4096, bbytes = ks * NB * 32;
+            mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), abytes + bbytes);
+            armed_parity[slot] = n & 1;
+            bulk_g2s(smem_u32(sA + slot * a_stage), Ablk + (size_t)k0 * 2 * 128 * 8, abytes,
+                     smem_u32(&ss->full[slot]));
+            bulk_g2s(smem_u32(sB + slot * b_stage), Bblk + (size_t)k0 * 2 * NB * 8, bbytes,
+                     smem_u32(&ss->full[slot]));
+        }
+        for (int s = 0; s < kGemmNS; ++s)
+            if (armed_parity[s] >= 0) mbar_wait_drain(smem_u32(&ss->full[s]), armed_parity[s]);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_bf16(128, NB);
+        bool ok = true;
+        for (int st = 0; st < nstages && ok; ++st) {
+            const int slot = st % kGemmNS, n = st / kGemmNS;
+            if (!mbar_wait(smem_u32(&ss->full[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const int k0 = st * kGemmKS;
+            const int ks = min(kGemmKS, nsteps - k0);
+            for (int j = 0; j < ks; ++j) {
+                const uint64_t ad = sdesc(smem_u32(sA + slot * a_stage + j * 4096), 2048, 128);
+                const uint64_t bd = sdesc(smem_u32(sB + slot * b_stage + j * NB * 32), NB * 16, 128);
+                mma_bf16(tbase, ad, bd, idesc, (k0 + j) > 0 ? 1u : 0u);
+            }
+            mma_commit(smem_u32(&ss->empty[slot]));
+        }
+        mma_commit(smem_u32(&ss->acc_full));
+        mma_commit(smem_u32(&ss->drain));
+        mbar_wait_drain(smem_u32(&ss->drain), 0);
+    } else if (warp >= 2) {
+        // epilogue
+        const int q = warp % 4;
+        bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        tc_fence_after();
+        if (ok) {
+            const int m = mt * 128 + q * 32 + lane;
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+                float v[16];
+                tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (m >= Mr) continue;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int n = nt * NB + c0 + i;
+                    if (n >= Nc) break;
+                    if (MODE == GEMM_OUT_F32) {
+                        out_f32[(long long)m * ldo + n] = v[i];
+                    } else {
+                        plane[(size_t)n * plane_len + plane_index(m, W, P)] = __float2bfloat16_rn(v[i]);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, tmem_cols);
+    }
+}
+
+// ---------------------------------------------------------------- conv1
+// One CTA per 128 output positions of one image; 4 warps.  The im2col A
+// operand (128 positions x 128 taps, taps >= 121 zero) is built in shared
+// memory from the proxy window; B = the 64 filters (resident, 16 KB).
+struct Conv1Smem {
+    uint64_t wbar, mbar;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt, int H, int W, int P,
+                                                    int plane_len, int t1, const bf16* __restrict__ w1p,
+                                                    const float* __restrict__ b1, bf16* __restrict__ a1,
+                                                    int* status)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sB = smem_raw;                 // 16 KB
+    uint8_t* sA = smem_raw + 16384;         // 32 KB
+    bf16* sWin = reinterpret_cast<bf16*>(smem_raw + 16384 + 32768);
+    const int winx = (128 + kConv2Reach * P + 10 + 7) / 8 * 8;
+    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + 16384 + 32768 + winx * 2);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int b = blockIdx.x / t1, t = blockIdx.x % t1;
+    const int q0 = t * 128;
+    const int HP = H * P;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&ss->wbar), 1);
+        mbar_init(smem_u32(&ss->mbar), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 64);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(smem_u32(&ss->wbar), 16384);
+        bulk_g2s(smem_u32(sB), w1p, 16384, smem_u32(&ss->wbar));
+    }
+    // proxy window -> shared memory (16-byte vectors; the plane is 16-byte aligned)
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(xt + (size_t)b * plane_len + q0);
+        uint4* dst = reinterpret_cast<uint4*>(sWin);
+        for (int i = threadIdx.x; i < winx / 8; i += 128) dst[i] = src[i];
+    }
+    __syncthreads();
+    // im2col: chunk (kc, m) holds taps 8 kc .. 8 kc + 7 of position q0 + m
+    for (int i = threadIdx.x; i < 16 * 128; i += 128) {
+        const int kc = i / 128, m = i % 128;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int tap = kc * 8 + e;
+            const int dy = tap / 11, dx = tap % 11;
+            v[e] = tap < 121 ? __bfloat162float(sWin[m + dy * P + dx]) : 0.f;
+        }
+        reinterpret_cast<uint4*>(sA)[i] = pack8_bf16(v);
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    if (threadIdx.x == 0) {
+        if (mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag)) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16(128, 64);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint64_t ad = sdesc(smem_u32(sA + kk * 4096), 2048, 128);
+                const uint64_t bd = sdesc(smem_u32(sB + kk * 2048), 1024, 128);
+                mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            }
+        } else {
+            mbar_wait_drain(smem_u32(&ss->wbar), 0);
+        }
+        mma_commit(smem_u32(&ss->mbar));
+    }
+    bool ok = mbar_wait(smem_u32(&ss->mbar), 0, status, &ss->abort_flag);
+    ok = __all_sync(0xffffffffu, ok && !ss->abort_flag);
+    tc_fence_after();
+    if (ok) {
+        const int m = warp * 32 + lane;
+        const int qq = q0 + m;
+        const bool valid = qq < HP;
+        const bool data = valid && (qq % P) < W;
+        bf16* dst = a1 + ((size_t)b * 8 * plane_len + (size_t)(qq + kPad * P + kPad)) * 8;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + __ldg(&b1[c0 + i]), 0.f) : 0.f;
+            if (valid) {
+                *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8) * plane_len * 8) = pack8_bf16(v);
+                *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8 + 1) * plane_len * 8) = pack8_bf16(v + 8);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 64);
+    }
+}
+
+// ---------------------------------------------------------------- conv2
+// Tap-stacked implicit GEMM.  For kernel row dy and column group s (taps
+// dx = 4 s + g, g = 0..3), one MMA with M = 128 rows (row 4 co + g: filter co,
+// tap slot g), N = 256 positions and K = 16 channels computes
+//   D_g[co][n] += sum_ci W2[co][ci][dy][4 s + g] a1[q0 + n + dy P + 4 s][ci],
+// so that output q0 + j = sum_g D_g[co][j + g]: the four slots of one filter
+// are four adjacent TMEM lanes and are summed with two warp shuffles in the
+// epilogue.  33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253
+// valid outputs per tile (the last 3 columns lack their slot-3 partner).
+//
+// Persistent CTAs, 6 warps: warp 0 lane 0 streams the input window (slabs of
+// 128 positions x 64 channels, freed as soon as the last kernel row reading
+// them has been multiplied) and the weights ((dy, s) blocks of 16 KB through a
+// ring); warp 1 owns TMEM (2 accumulators x 256 columns) and issues MMAs;
+// warps 2..5 drain the accumulator of the previous tile.
+constexpr int kW2Stages = 4;
+constexpr int kMaxSlabs = 10;
+
+struct Conv2Smem {
+    uint64_t full[kMaxSlabs], empty[kMaxSlabs];
+    uint64_t wfull[kW2Stages], wempty[kW2Stages];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__host__ __device__ inline int conv2_dylast(int j, int P)
+{
+    const int d = (j * kSlabPx + kSlabPx - 1) / P;
+    return d < 10 ? d : 10;
+}
+
+__global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ a1, int B, int H, int W, int P,
+                                                       int plane_len, int t2, int nslab,
+                                                       const bf16* __restrict__ w2p,
+                                                       const float* __restrict__ b2, bf16* __restrict__ a2,
+                                                       int* status)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const int win_px = nslab * kSlabPx;
+    const uint32_t CH = (uint32_t)win_px * 16;     // bytes per 8-channel chunk plane of the window
+    uint8_t* sWin = smem_raw;                       // [8][win_px][8] bf16
+    uint8_t* sW = smem_raw + 8 * CH;                // [kW2Stages][16 KB]
+    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * 16384);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int HP = H * P;
+    const int ntiles = B * t2;
+
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < nslab; ++j) {
+            mbar_init(smem_u32(&ss->full[j]), 1);
+            mbar_init(smem_u32(&ss->empty[j]), 1);
+        }
+        for (int s = 0; s < kW2Stages; ++s) {
+            mbar_init(smem_u32(&ss->wfull[s]), 1);
+            mbar_init(smem_u32(&ss->wempty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&ss->acc_full[s]), 1);
+            mbar_init(smem_u32(&ss->acc_empty[s]), 4);
+        }
+        mbar_init(smem_u32(&ss->drain), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ producer
+        int slab_parity[kMaxSlabs];
+        int w_parity[kW2Stages];
+        for (int j = 0; j < kMaxSlabs; ++j) slab_parity[j] = -1;
+        for (int s = 0; s < kW2Stages; ++s) w_parity[s] = -1;
+        int it = 0, wst = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
+            const uint8_t* src_img = reinterpret_cast<const uint8_t*>(a1) + (size_t)b * 8 * plane_len * 16;
+            int next_slab = 0;
+            for (int dy = 0; dy < 11 && ok; ++dy) {
+                const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                while (next_slab <= last) {
+                    const int j = next_slab++;
+                    if (!mbar_wait(smem_u32(&ss->empty[j]), (it & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
+                    mbar_arrive_expect_tx(smem_u32(&ss->full[j]), 8 * kSlabPx * 16);
+                    slab_parity[j] = it & 1;
+                    for (int c = 0; c < 8; ++c)
+                        bulk_g2s(smem_u32(sWin + c * CH + j * kSlabPx * 16),
+                                 src_img + ((size_t)c * plane_len + q0 + j * kSlabPx) * 16, kSlabPx * 16,
+                                 smem_u32(&ss->full[j]));
+                }
+                for (int s = 0; s < 3 && ok; ++s, ++wst) {
+                    const int slot = wst % kW2Stages, n = wst / kW2Stages;
+                    if (!mbar_wait(smem_u32(&ss->wempty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
+                    mbar_arrive_expect_tx(smem_u32(&ss->wfull[slot]), 16384);
+                    w_parity[slot] = n & 1;
+                    bulk_g2s(smem_u32(sW + slot * 16384),
+                             reinterpret_cast<const uint8_t*>(w2p) + (size_t)(dy * 3 + s) * 16384, 16384,
+                             smem_u32(&ss->wfull[slot]));
+                }
+            }
+        }
+        for (int j = 0; j < nslab; ++j)
+            if (slab_parity[j] >= 0) mbar_wait_drain(smem_u32(&ss->full[j]), slab_parity[j]);
+        for (int s = 0; s < kW2Stages; ++s)
+            if (w_parity[s] >= 0) mbar_wait_drain(smem_u32(&ss->wfull[s]), w_parity[s]);
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16(128, kConv2N);
+        int it = 0, wst = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            const int buf = it & 1, use = it >> 1;
+            if (!mbar_wait(smem_u32(&ss->acc_empty[buf]), (use & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d = tbase + (uint32_t)buf * kConv2N;
+            int next_wait = 0, next_free = 0;
+            for (int dy = 0; dy < 11 && ok; ++dy) {
+                const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                while (next_wait <= last) {
+                    if (!mbar_wait(smem_u32(&ss->full[next_wait]), it & 1, status, &ss->abort_flag)) { ok = false; break; }
+                    ++next_wait;
+                }
+                if (!ok) break;
+                tc_fence_after();
+                for (int s = 0; s < 3; ++s, ++wst) {
+                    const int slot = wst % kW2Stages, n = wst / kW2Stages;
+                    if (!mbar_wait(smem_u32(&ss->wfull[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t off = (uint32_t)(dy * P + 4 * s) * 16;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = sdesc(smem_u32(sW + slot * 16384 + kk * 4096), 2048, 128);
+                        const uint64_t bd = sdesc(smem_u32(sWin + (2 * kk) * CH) + off, CH, 128);
+                        mma_bf16(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&ss->wempty[slot]));
+                }
+                if (!ok) break;
+                while (next_free < nslab && conv2_dylast(next_free, P) == dy) {
+                    mma_commit(smem_u32(&ss->empty[next_free]));
+                    ++next_free;
+                }
+            }
+            if (!ok) break;
+            mma_commit(smem_u32(&ss->acc_full[buf]));
+        }
+        mma_commit(smem_u32(&ss->drain));
+        mbar_wait_drain(smem_u32(&ss->drain), 0);
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int q = warp % 4;               // TMEM lane quarter = filters 8 q .. 8 q + 7
+        const int g = lane & 3;               // tap slot of this lane
+        const int co = q * 8 + (lane >> 2);
+        const float bias = __ldg(&b2[co]);
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int buf = it & 1, use = it >> 1;
+            bool ok = mbar_wait(smem_u32(&ss->acc_full[buf]), use & 1, status, &ss->abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
+            bf16* dst = a2 + ((size_t)b * 4 + q) * plane_len * 8 + (lane >> 2);
+            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kConv2N;
+            for (int cc = 0; cc < kConv2N / 32; ++cc) {
+                float v[36];
+                tmem_ld32(lane_addr + cc * 32, v);
+                if (cc < kConv2N / 32 - 1) {
+                    tmem_ld4(lane_addr + cc * 32 + 32, v + 32);
+                } else {
+                    v[32] = v[33] = v[34] = v[35] = 0.f;
+                }
+                float res[8];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float t = g == 0 ? v[j] : g == 1 ? v[j + 1] : g == 2 ? v[j + 2] : v[j + 3];
+                    t += __shfl_xor_sync(0xffffffffu, t, 1);
+                    t += __shfl_xor_sync(0xffffffffu, t, 2);
+                    if ((j & 3) == g) res[j >> 2] = t;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int jcol = cc * 32 + jj * 4 + g;
+                    const int qq = q0 + jcol;
+                    if (jcol < kConv2Valid && qq < HP) {
+                        const float val = (qq % P) < W ? fmaxf(res[jj] + bias, 0.f) : 0.f;
+                        dst[(size_t)(qq + kPad * P + kPad) * 8] = __float2bfloat16_rn(val);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ss->acc_empty[buf]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
+// ---------------------------------------------------------------- conv3
+// Row partial sums T[p][dy] = sum_{dx, ci} W3[ci][dy][dx] a2[p + dx][ci] for
+// 128 positions p per CTA: 11 columns x 2 channel chunks = 22 MMAs with
+// M = 128, N = 16 (rows dy >= 11 zero), K = 16.  Then
+// xhat[q] = b3 + sum_dy T[q + dy P][dy].
+struct Conv3Smem {
+    uint64_t bar, mbar;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+constexpr int kConv3Win = 144;      // 128 + 10 positions, rounded up to 16
+
+__global__ void __launch_bounds__(128) conv3_rows_kernel(const bf16* __restrict__ a2, int plane_len, int t3,
+                                                         int tlen, const bf16* __restrict__ w3p,
+                                                         float* __restrict__ T, int* status)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sWin = smem_raw;                         // [4][144][8] bf16 = 9216 B
+    uint8_t* sW = smem_raw + 4 * kConv3Win * 16;      // 11264 B
+    Conv3Smem* ss = reinterpret_cast<Conv3Smem*>(sW + 11264);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int b = blockIdx.x / t3, u = blockIdx.x % t3;
+    const int p0 = u * 128;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&ss->bar), 1);
+        mbar_init(smem_u32(&ss->mbar), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 32);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (threadIdx.x == 0) {
+        const uint32_t bar = smem_u32(&ss->bar);
+        mbar_arrive_expect_tx(bar, 4 * kConv3Win * 16 + 11264);
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(a2) + (size_t)b * 4 * plane_len * 16;
+        for (int c = 0; c < 4; ++c)
+            bulk_g2s(smem_u32(sWin + c * kConv3Win * 16), src + ((size_t)c * plane_len + p0) * 16,
+                     kConv3Win * 16, bar);
+        bulk_g2s(smem_u32(sW), w3p, 11264, bar);
+        if (mbar_wait(bar, 0, status, &ss->abort_flag)) {
+            tc_fence_after();
+            const uint32_t idesc = idesc_bf16(128, 16);
+            for (int dx = 0; dx < 11; ++dx)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t ad = sdesc(smem_u32(sWin + (2 * kk) * kConv3Win * 16 + dx * 16),
+                                              kConv3Win * 16, 128);
+                    const uint64_t bd = sdesc(smem_u32(sW + (dx * 2 + kk) * 512), 256, 128);
+                    mma_bf16(tbase, ad, bd, idesc, (dx | kk) ? 1u : 0u);
+                }
+        } else {
+            mbar_wait_drain(bar, 0);
+        }
+        mma_commit(smem_u32(&ss->mbar));
+    }
+    bool ok = mbar_wait(smem_u32(&ss->mbar), 0, status, &ss->abort_flag);
+    ok = __all_sync(0xffffffffu, ok && !ss->abort_flag);
+    tc_fence_after();
+    if (ok) {
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
+        const int p = p0 + warp * 32 + lane;
+        float* dst = T + (size_t)b * 11 * tlen + p;
+#pragma unroll
+        for (int dy = 0; dy < 11; ++dy) dst[(size_t)dy * tlen] = v[dy];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 32);
+    }
+}
+
+__global__ void conv3_sum_kernel(const float* __restrict__ T, int B, int H, int W, int P, int tlen,
+                                 const float* __restrict__ b3, int final_relu, float* __restrict__ xhat)
+{
+    const long long n = (long long)B * H * W;
+    const float bias = __ldg(b3);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % W);
+        const int r = (int)((i / W) % H);
+        const long long b = i / ((long long)W * H);
+        const float* t = T + (size_t)b * 11 * tlen + (size_t)r * P + c;
+        float s = bias;
+#pragma unroll
+        for (int dy = 0; dy < 11; ++dy) s += t[(size_t)dy * tlen + (size_t)dy * P];
+        xhat[i] = final_relu ? fmaxf(s, 0.f) : s;
+    }
+}
+
+// bf16 planes -> float32 NCHW (C == 1: [B][plane]; C % 8 == 0: [B][C/8][plane][8]).
+__global__ void plane_to_nchw_kernel(const bf16* __restrict__ src, int B, int C, int H, int W, int P,
+                                     int plane_len, float* __restrict__ dst)
+{
+    const long long n = (long long)B * C * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % W);
+        const int r = (int)((i / W) % H);
+        const int ch = (int)((i / ((long long)W * H)) % C);
+        const long long b = i / ((long long)W * H * C);
+        const long long pos = (long long)r * P + c + kPad * P + kPad;
+        size_t off;
+        if (C == 1) off = (size_t)b * plane_len + pos;
+        else off = (((size_t)b * (C / 8) + ch / 8) * plane_len + pos) * 8 + (ch % 8);
+        dst[i] = __bfloat162float(src[off]);
+    }
+}
+
+inline int grid1d(long long n, int threads = 256)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// ================================================================ launchers
+size_t packed_elems(int R, int TR, int Kp) { return (size_t)cdiv(R, TR) * TR * Kp; }
+
+int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int TR, int Kp, bf16* dst,
+                cudaStream_t st)
+{
+    const long long nchunks = (long long)cdiv(R, TR) * TR * (Kp / 8);
+    if (nchunks <= 0) return DEEPINV_OK;
+    pack_kmajor_kernel<<<grid1d(nchunks), 256, 0, st>>>(src, rs, cs, R, K, TR, Kp, nchunks, dst);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p, bf16* w3p,
+                      cudaStream_t st)
+{
+    const long long n = (long long)(kW1PackElems + kW2PackElems + kW3PackElems);
+    pack_conv_weights_kernel<<<grid1d(n), 256, 0, st>>>(w1, w2, w3, w1p, w2p, w3p);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mode, float* out_f32,
+            long long ldo, bf16* plane, const Geo& geo, int* status, cudaStream_t st)
+{
+    if (Mr <= 0 || Nc <= 0) return DEEPINV_OK;
+    if (NB < 16 || NB > 256 || NB % 16 || Kp % 16 || Kp <= 0) {
+        set_error("tc_gemm: bad tile N=%d or K=%d", NB, Kp);
+        return DEEPINV_EINVAL;
+    }
+    uint32_t cols = 32;
+    while (cols < (uint32_t)NB) cols <<= 1;
+    const size_t smem = (size_t)kGemmNS * (kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
+    dim3 grid(cdiv(Mr, 128), cdiv(Nc, NB));
+    if (mode == GEMM_OUT_F32) {
+        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc_gemm_kernel<GEMM_OUT_F32><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane,
+                                                              geo.H, geo.W, geo.P, geo.plane, status);
+    } else {
+        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_PLANE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc_gemm_kernel<GEMM_OUT_PLANE><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane,
+                                                                geo.H, geo.W, geo.P, geo.plane, status);
+    }
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, bf16* a1, int* status,
+             cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
+    const size_t smem = 16384 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(conv1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv1_kernel<<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, status);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+static size_t conv2_smem_bytes(const Geo& g)
+{
+    return (size_t)8 * g.nslab * kSlabPx * 16 + (size_t)kW2Stages * 16384 + sizeof(Conv2Smem);
+}
+
+bool conv2_tc_supported(const Geo& g)
+{
+    return g.nslab <= kMaxSlabs && conv2_smem_bytes(g) <= 227 * 1024;
+}
+
+int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* b2, bf16* a2, int num_sms,
+             int* status, cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    if (!conv2_tc_supported(g)) {
+        set_error("conv2_tc: image width %d needs %d window slabs (max %d)", g.W, g.nslab, kMaxSlabs);
+        return DEEPINV_EUNSUPPORTED;
+    }
+    const size_t smem = conv2_smem_bytes(g);
+    DI_CUDA(cudaFuncSetAttribute(conv2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ntiles = B * g.t2;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    conv2_kernel<<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, g.nslab, w2p, b2, a2, status);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+size_t conv3_scratch_elems(const Geo& g, int B) { return (size_t)B * 11 * g.t3 * 128; }
+
+int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* b3, float* T, float* xhat,
+             int final_relu, int* status, cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    const size_t smem = 4 * kConv3Win * 16 + 11264 + sizeof(Conv3Smem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int tlen = g.t3 * 128;
+    conv3_rows_kernel<<<B * g.t3, 128, smem, st>>>(a2, g.plane, g.t3, tlen, w3p, T, status);
+    DI_LAUNCH_CHECK();
+    const long long n = (long long)B * g.H * g.W;
+    conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, B, g.H, g.W, g.P, tlen, b3, final_relu, xhat);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st)
+{
+    const long long n = (long long)B * C * g.H * g.W;
+    if (n <= 0) return DEEPINV_OK;
+    plane_to_nchw_kernel<<<grid1d(n), 256, 0, st>>>(src, B, C, g.H, g.W, g.P, g.plane, dst);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+}  // namespace di

@@ -1,0 +1,303 @@
+"""Thin Python binding of libdeepinv.so (C ABI in include/deepinv.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams; tensors are passed
+as raw device pointers.  There is no fallback: if the library is missing or
+a call fails, a ``DeepInvError`` is raised.
+
+Paper: Mousavi & Baraniuk, "Learning to Invert: Signal Recovery via Deep
+Convolutional Networks", arXiv 1701.03891 -- y = Phi x (Sec. 1), the network
+x^ = M(y, Omega) of Sec. 4 with the layer sizes of Sec. 5, and its MSE loss.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdeepinv.so")
+
+F32 = 0
+BF16 = 1
+PRECISIONS = {"f32": F32, "fp32": F32, "bf16": BF16}
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
+_STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EUNSUPPORTED: "EUNSUPPORTED",
+                 ETIMEOUT: "ETIMEOUT", EBUSY: "EBUSY"}
+
+
+class DeepInvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (_STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("M", ctypes.c_int),
+                ("l1", ctypes.c_int), ("l2", ctypes.c_int), ("l3", ctypes.c_int),
+                ("k", ctypes.c_int), ("final_relu", ctypes.c_int), ("train_fc", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); mirrors include/deepinv.h
+SIGNATURES = {
+    "deepinv_last_error": (ctypes.c_char_p, []),
+    "deepinv_version": (_I, []),
+    "deepinv_device_status": (_I, [_I]),
+    "deepinv_measure": (_I, [_P, _I, _I, _P, _I, _P, _I, _P]),
+    "deepinv_net_create": (_I, [ctypes.POINTER(NetDesc), _P, _PP, _PP, _P, ctypes.POINTER(_P)]),
+    "deepinv_net_destroy": (_I, [_P]),
+    "deepinv_net_get_desc": (_I, [_P, ctypes.POINTER(NetDesc)]),
+    "deepinv_net_reserve": (_I, [_P, _I, _P]),
+    "deepinv_net_measure": (_I, [_P, _P, _I, _P, _P]),
+    "deepinv_saved_bytes": (ctypes.c_size_t, [_P, _I]),
+    "deepinv_forward": (_I, [_P, _P, _I, _P, _P, _P]),
+    "deepinv_forward_host": (_I, [_P, _P, _I, _P, _P]),
+    "deepinv_sense_recover_host": (_I, [_P, _P, _I, _P, _P]),
+    "deepinv_backward": (_I, [_P, _P, _P, _I, _P, _PP, _PP, _P, _P, _P]),
+    "deepinv_sgd_momentum": (_I, [_P, _PP, _PP, _P, ctypes.c_float, ctypes.c_float, _P]),
+    "deepinv_get_params": (_I, [_P, _PP, _PP, _P, _P]),
+}
+
+
+def lib():
+    """Load libdeepinv.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise DeepInvError(ECUDA, "libdeepinv.so not built (run __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        msg = lib().deepinv_last_error()
+        raise DeepInvError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_f32_cuda(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise DeepInvError(EINVAL, "%s must be a contiguous float32 CUDA tensor" % name)
+
+
+def _arr(ptrs):
+    a = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    return ctypes.cast(a, _PP), a
+
+
+def device_status(reset: bool = False) -> int:
+    return lib().deepinv_device_status(1 if reset else 0)
+
+
+def measure(phi, x, prec="f32", out=None, stream=None):
+    """y = Phi x (Sec. 1).  phi [M][N], x [B][N] float32 CUDA -> y [B][M]."""
+    import torch
+    _need_f32_cuda(phi, "phi")
+    _need_f32_cuda(x, "x")
+    M, N = phi.shape
+    B = x.shape[0]
+    y = out if out is not None else torch.empty((B, M), device=x.device, dtype=torch.float32)
+    _check(lib().deepinv_measure(_ptr(phi), M, N, _ptr(x), B, _ptr(y), PRECISIONS.get(prec, prec),
+                                 _stream(stream)))
+    return y
+
+
+class Net:
+    """A DeepInverse network (Sec. 4) held by the library: FC = Phi^T, then
+    three conv layers (Eq. 1).  ``params`` maps w1,b1,w2,b2,w3,b3 to float32
+    tensors (CUDA or CPU; copied)."""
+
+    def __init__(self, phi, params: dict, n1: int, n2: int, *, prec="bf16", final_relu=False,
+                 train_fc=False, device="cuda"):
+        import torch
+        dev = torch.device(device)
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(dev).contiguous()
+        phi_t = t(phi)
+        M, N = phi_t.shape
+        assert N == n1 * n2, "phi must be M x (n1*n2)"
+        ws = [t(params["w%d" % i]) for i in (1, 2, 3)]
+        bs = [t(params["b%d" % i]) for i in (1, 2, 3)]
+        self.desc = NetDesc(n1, n2, M, ws[0].shape[0], ws[1].shape[0], ws[2].shape[0], ws[0].shape[-1],
+                            int(final_relu), int(train_fc), PRECISIONS.get(prec, prec))
+        self.n1, self.n2, self.M, self.N = n1, n2, M, N
+        self.prec = prec
+        self.device = dev
+        self._h = ctypes.c_void_p()
+        wp, _k1 = _arr([w.data_ptr() for w in ws])
+        bp, _k2 = _arr([b.data_ptr() for b in bs])
+        _check(lib().deepinv_net_create(ctypes.byref(self.desc), phi_t.data_ptr(), wp, bp,
+                                        _stream(), ctypes.byref(self._h)))
+        self.shapes = [tuple(w.shape) for w in ws]
+
+    def close(self):
+        if self._h:
+            lib().deepinv_net_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, max_B: int, stream=None):
+        _check(lib().deepinv_net_reserve(self._h, max_B, _stream(stream)))
+
+    def measure(self, x, out=None, stream=None):
+        import torch
+        _need_f32_cuda(x, "x")
+        B = x.shape[0]
+        y = out if out is not None else torch.empty((B, self.M), device=x.device, dtype=torch.float32)
+        _check(lib().deepinv_net_measure(self._h, _ptr(x), B, _ptr(y), _stream(stream)))
+        return y
+
+    def saved_bytes(self, B: int) -> int:
+        return int(lib().deepinv_saved_bytes(self._h, B))
+
+    def forward(self, y, out=None, saved=None, stream=None):
+        """x^ = M(y, Omega).  y [B][M] -> x^ [B][N]."""
+        import torch
+        _need_f32_cuda(y, "y")
+        B = y.shape[0]
+        xh = out if out is not None else torch.empty((B, self.N), device=y.device, dtype=torch.float32)
+        _check(lib().deepinv_forward(self._h, _ptr(y), B, _ptr(xh), _ptr(saved), _stream(stream)))
+        return xh
+
+    __call__ = forward
+
+    def forward_host(self, y_host, out_host=None, stream=None):
+        """End to end from host memory (pinned for async copies); returns a CPU tensor."""
+        import torch
+        B = y_host.shape[0]
+        xh = out_host if out_host is not None else torch.empty((B, self.N), dtype=torch.float32)
+        _check(lib().deepinv_forward_host(self._h, y_host.data_ptr(), B, xh.data_ptr(), _stream(stream)))
+        return xh
+
+    def sense_recover_host(self, x_host, out_host=None, stream=None):
+        import torch
+        B = x_host.shape[0]
+        xh = out_host if out_host is not None else torch.empty((B, self.N), dtype=torch.float32)
+        _check(lib().deepinv_sense_recover_host(self._h, x_host.data_ptr(), B, xh.data_ptr(),
+                                                _stream(stream)))
+        return xh
+
+    def new_saved(self, B: int):
+        import torch
+        return torch.empty(self.saved_bytes(B), dtype=torch.uint8, device=self.device)
+
+    def grad_buffers(self):
+        import torch
+        dW = [torch.empty(s, device=self.device, dtype=torch.float32) for s in self.shapes]
+        db = [torch.empty(s[0], device=self.device, dtype=torch.float32) for s in self.shapes]
+        dWfc = (torch.empty((self.N, self.M), device=self.device, dtype=torch.float32)
+                if self.desc.train_fc else None)
+        return dW, db, dWfc
+
+    def backward(self, y, x, saved, grads=None, stream=None):
+        """Gradient of L = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4).  Returns (loss tensor, dW, db, dWfc)."""
+        import torch
+        _need_f32_cuda(y, "y")
+        _need_f32_cuda(x, "x")
+        B = y.shape[0]
+        dW, db, dWfc = grads if grads is not None else self.grad_buffers()
+        loss = torch.empty((), device=self.device, dtype=torch.float64)
+        wp, _k1 = _arr([t.data_ptr() for t in dW])
+        bp, _k2 = _arr([t.data_ptr() for t in db])
+        _check(lib().deepinv_backward(self._h, _ptr(y), _ptr(x), B, _ptr(saved), wp, bp, _ptr(dWfc),
+                                      _ptr(loss), _stream(stream)))
+        return loss, dW, db, dWfc
+
+    def sgd_momentum(self, dW, db, dWfc=None, lr=1e-3, mu=0.9, stream=None):
+        wp, _k1 = _arr([t.data_ptr() for t in dW])
+        bp, _k2 = _arr([t.data_ptr() for t in db])
+        _check(lib().deepinv_sgd_momentum(self._h, wp, bp, _ptr(dWfc), float(lr), float(mu),
+                                          _stream(stream)))
+
+    def get_params(self, stream=None) -> dict:
+        import torch
+        W = [torch.empty(s, device=self.device, dtype=torch.float32) for s in self.shapes]
+        Bv = [torch.empty(s[0], device=self.device, dtype=torch.float32) for s in self.shapes]
+        wfc = (torch.empty((self.N, self.M), device=self.device, dtype=torch.float32)
+               if self.desc.train_fc else None)
+        wp, _k1 = _arr([t.data_ptr() for t in W])
+        bp, _k2 = _arr([t.data_ptr() for t in Bv])
+        _check(lib().deepinv_get_params(self._h, wp, bp, _ptr(wfc), _stream(stream)))
+        out = {"w1": W[0], "w2": W[1], "w3": W[2], "b1": Bv[0], "b2": Bv[1], "b3": Bv[2]}
+        if wfc is not None:
+            out["wfc"] = wfc
+        return out
+
+
+def _make_autograd():
+    import torch
+
+    class DeepInverseMSE(torch.autograd.Function):
+        """L(Omega) of Sec. 4 as an autograd node over the network's parameters.
+
+        forward(net, y, x, *params) runs the library's forward (saving the
+        activations) and its hand-written backward in one go and returns the
+        loss; backward hands the stored parameter gradients, scaled by the
+        incoming gradient, to autograd.  ``params`` are placeholders that
+        carry requires_grad (the library holds the weights themselves)."""
+
+        @staticmethod
+        def forward(ctx, net, y, x, *params):
+            B = y.shape[0]
+            saved = net.new_saved(B)
+            net.forward(y, saved=saved)
+            loss, dW, db, dWfc = net.backward(y, x, saved)
+            grads = [dW[0], db[0], dW[1], db[1], dW[2], db[2]]
+            if dWfc is not None:
+                grads.append(dWfc)
+            ctx.grads = grads
+            return loss.to(torch.float32)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g = [t * gout for t in ctx.grads]
+            return (None, None, None, *g[:len(ctx.needs_input_grad) - 3])
+
+    return DeepInverseMSE
+
+
+_autograd_cls = None
+
+
+def mse_loss(net: Net, y, x, params):
+    """Differentiable L(Omega); ``params`` is the list [w1, b1, w2, b2, w3, b3(, wfc)]."""
+    global _autograd_cls
+    if _autograd_cls is None:
+        _autograd_cls = _make_autograd()
+    return _autograd_cls.apply(net, y, x, *params)

@@ -1,0 +1,82 @@
+"""The C ABI library loads, exports every symbol include/*.h declares, and
+rejects bad arguments on the host before touching a GPU (no compute calls)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(deepinv_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1701_03891_gb300 import build, deepinv
+    build.build()
+    return deepinv.lib()
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for n in ("deepinv_measure", "deepinv_forward", "deepinv_backward", "deepinv_net_create"):
+        assert n in d
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_1701_03891_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (deepinv_\w+)", out))
+    missing = _declared() - exported
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1701_03891_gb300 import deepinv
+    assert _declared() <= set(deepinv.SIGNATURES)
+
+
+def test_version(L):
+    assert L.deepinv_version() == 100
+
+
+def test_null_pointers_rejected_on_host(L):
+    from paper_1701_03891_gb300 import deepinv
+    rc = L.deepinv_measure(None, 4, 8, None, 2, None, 0, None)
+    assert rc == deepinv.EINVAL
+    assert b"null" in L.deepinv_last_error()
+    assert L.deepinv_forward(None, None, 1, None, None, None) == deepinv.EINVAL
+    assert L.deepinv_net_reserve(None, 4, None) == deepinv.EINVAL
+
+
+def test_bad_descriptions_rejected_on_host(L):
+    from paper_1701_03891_gb300 import deepinv
+    out = ctypes.c_void_p()
+    bad = [
+        deepinv.NetDesc(0, 8, 4, 64, 32, 1, 11, 0, 0, 0),      # empty image
+        deepinv.NetDesc(8, 8, 65, 64, 32, 1, 11, 0, 0, 0),     # M > N
+        deepinv.NetDesc(8, 8, 4, 64, 32, 1, 10, 0, 0, 0),      # even kernel
+        deepinv.NetDesc(8, 8, 4, 64, 32, 2, 11, 0, 0, 0),      # l3 != 1
+        deepinv.NetDesc(8, 8, 4, 64, 32, 1, 11, 0, 0, 7),      # unknown precision
+    ]
+    for d in bad:
+        rc = L.deepinv_net_create(ctypes.byref(d), ctypes.c_void_p(16), None, None, None, ctypes.byref(out))
+        assert rc == deepinv.EINVAL, (d.n1, d.M, d.k, rc)
+    d = deepinv.NetDesc(8, 8, 4, 16, 32, 1, 11, 0, 0, deepinv.BF16)  # bf16 needs 64/32/1
+    rc = L.deepinv_net_create(ctypes.byref(d), ctypes.c_void_p(16), None, None, None, ctypes.byref(out))
+    assert rc == deepinv.EUNSUPPORTED
+
+
+def test_saved_bytes_null_net(L):
+    assert L.deepinv_saved_bytes(None, 4) == 0

@@ -1,0 +1,239 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative L2 per image, max over the batch):
+  float32 path  <= 1e-5   (float32 products, float32 accumulation)
+  bfloat16 path <= 1e-2   (bfloat16 operands, float32 accumulation)
+The oracle sees the float32 master weights and inputs, so the bfloat16
+tolerance includes the rounding of weights, inputs and activations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_03891_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def di():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_03891_gb300 import build, deepinv
+    build.build()
+    deepinv.lib()
+    return deepinv
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _maxrel(got, ref):
+    return float(np.max(oracle.rel_l2(got, ref)))
+
+
+# ------------------------------------------------------------------ y = Phi x
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("M,N,B", [(13, 37, 5), (102, 1024, 4), (410, 4096, 130), (1, 16, 1), (300, 300, 257)])
+def test_measure(di, prec, M, N, B):
+    rng = np.random.default_rng(M * 7 + N)
+    phi = synth.gaussian_phi(M, N, seed=M)
+    x = rng.uniform(0, 1, (B, N)).astype(np.float32)
+    y = di.measure(_cuda(phi), _cuda(x), prec=prec).cpu().numpy()
+    ref = oracle.measure(phi, x)
+    assert _maxrel(y, ref) <= TOL[prec]
+
+
+def test_measure_empty_batch(di):
+    import torch
+    phi = _cuda(synth.gaussian_phi(8, 32))
+    x = torch.empty((0, 32), device="cuda")
+    assert di.measure(phi, x, prec="bf16").shape == (0, 8)
+
+
+# ------------------------------------------------------------------ forward
+def _case(n1, n2, ratio, B, seed=0, images="dct", bias_std=0.01):
+    N = n1 * n2
+    M = synth.m_for_ratio(ratio, N)
+    phi = synth.gaussian_phi(M, N, seed=seed)
+    params = synth.he_params(seed=seed + 1, bias_std=bias_std)
+    if images == "dct":
+        x = synth.dct_sparse_images(B, n1, n2, K=max(1, N // 20), seed=seed + 2)
+    else:
+        x = synth.voronoi_images(B, n1, n2, seed=seed + 3)
+    return phi, params, x
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("n1,n2,ratio,B", [
+    (32, 32, 0.10, 4),      # the 32 x 32 float32 parity workload
+    (64, 64, 0.25, 3),
+    (64, 64, 0.10, 3),
+    (64, 64, 0.05, 3),
+    (16, 16, 0.125, 2),
+    (24, 40, 0.10, 3),      # non-square
+    (20, 37, 0.20, 2),      # ragged width
+    (7, 9, 0.5, 5),         # tiny image: one tile, most of it padding
+])
+def test_forward(di, prec, n1, n2, ratio, B):
+    phi, params, x = _case(n1, n2, ratio, B)
+    net = di.Net(phi, params, n1, n2, prec=prec)
+    xd = _cuda(x)
+    y = net.measure(xd)
+    xhat = net.forward(y).cpu().numpy()
+    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
+    err = _maxrel(xhat, ref)
+    assert np.all(np.isfinite(xhat))
+    assert err <= TOL[prec], err
+    net.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_forward_final_relu(di, prec):
+    phi, params, x = _case(32, 32, 0.1, 3)
+    net = di.Net(phi, params, 32, 32, prec=prec, final_relu=True)
+    y = _cuda(oracle.measure(phi, x))
+    xhat = net.forward(y).cpu().numpy()
+    ref = oracle.forward(y.cpu().numpy(), params, 32, 32, phi=phi, final_relu=True)
+    assert np.all(xhat >= 0)
+    assert float(np.linalg.norm(xhat - ref) / np.linalg.norm(ref)) <= TOL[prec]
+
+
+def test_forward_f32_reduced_net(di):
+    """The float32 path takes any filter counts and odd kernel sizes."""
+    n1, n2, M, B = 13, 19, 30, 3
+    phi = synth.gaussian_phi(M, n1 * n2, seed=5)
+    params = synth.he_params(5, 3, 1, 5, seed=6, bias_std=0.1)
+    x = synth.dct_sparse_images(B, n1, n2, K=12, seed=7)
+    net = di.Net(phi, params, n1, n2, prec="f32")
+    y = _cuda(oracle.measure(phi, x))
+    got = net.forward(y).cpu().numpy()
+    ref = oracle.forward(y.cpu().numpy(), params, n1, n2, phi=phi)
+    assert _maxrel(got, ref) <= TOL["f32"]
+
+
+def test_forward_bf16_full_batch_sampled(di):
+    """64 x 64, M/N = 0.1, batch 1024 (the benchmark workload): sampled images against the oracle."""
+    n1 = n2 = 64
+    B = 1024
+    phi, params, x = _case(n1, n2, 0.10, B, images="voronoi", bias_std=0.0)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
+    xd = _cuda(x)
+    y = net.measure(xd)
+    xhat = net.forward(y).cpu().numpy()
+    assert np.all(np.isfinite(xhat))
+    idx = [0, 1, 511, 777, 1023]
+    ref = oracle.forward(oracle.measure(phi, x[idx]), params, n1, n2, phi=phi)
+    assert _maxrel(xhat[idx], ref) <= TOL["bf16"]
+    # batch invariance: the same images alone give the same result
+    alone = net.forward(y[idx].contiguous()).cpu().numpy()
+    np.testing.assert_allclose(alone, xhat[idx], rtol=0, atol=1e-6 * np.abs(xhat[idx]).max())
+    net.close()
+
+
+def test_forward_batch_sizes_reuse_workspace(di):
+    """Growing and shrinking the batch on one network keeps results exact (zero borders preserved)."""
+    phi, params, x = _case(32, 32, 0.1, 40)
+    net = di.Net(phi, params, 32, 32, prec="bf16")
+    y = _cuda(oracle.measure(phi, x))
+    full = net.forward(y).cpu().numpy()
+    for b in (1, 7, 40, 3):
+        part = net.forward(y[:b].contiguous()).cpu().numpy()
+        np.testing.assert_array_equal(part, full[:b])
+
+
+def test_forward_empty_batch(di):
+    import torch
+    phi, params, _ = _case(16, 16, 0.125, 1)
+    net = di.Net(phi, params, 16, 16, prec="bf16")
+    out = net.forward(torch.empty((0, phi.shape[0]), device="cuda"))
+    assert out.shape == (0, 256)
+
+
+def test_host_entry_points(di):
+    import torch
+    phi, params, x = _case(32, 32, 0.1, 6)
+    for prec in ("f32", "bf16"):
+        net = di.Net(phi, params, 32, 32, prec=prec)
+        xd = _cuda(x)
+        y = net.measure(xd)
+        dev = net.forward(y).cpu()
+        yh = y.cpu().pin_memory()
+        host = net.forward_host(yh, torch.empty((6, 1024)).pin_memory())
+        assert torch.equal(host, dev)
+        sr = net.sense_recover_host(torch.from_numpy(x).pin_memory(), torch.empty((6, 1024)).pin_memory())
+        assert torch.equal(sr, dev)
+
+
+# ------------------------------------------------------------------ backward
+def _train_case(train_fc):
+    n1 = n2 = 16
+    M, B = 32, 2
+    phi = synth.gaussian_phi(M, n1 * n2, seed=0)
+    params = synth.he_params(seed=1, bias_std=0.05)
+    x = synth.dct_sparse_images(B, n1, n2, K=10, seed=2)
+    y = oracle.measure(phi, x).astype(np.float32)
+    return n1, n2, phi, params, x, y
+
+
+@pytest.mark.parametrize("prec,train_fc", [("f32", False), ("f32", True), ("bf16", False), ("bf16", True)])
+def test_backward_matches_oracle(di, prec, train_fc):
+    n1, n2, phi, params, x, y = _train_case(train_fc)
+    loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi, train_fc=train_fc)
+    net = di.Net(phi, params, n1, n2, prec=prec, train_fc=train_fc)
+    yd, xd = _cuda(y), _cuda(x)
+    saved = net.new_saved(2)
+    net.forward(yd, saved=saved)
+    loss, dW, db, dWfc = net.backward(yd, xd, saved)
+    tol = {"f32": 1e-4, "bf16": 5e-2}[prec]
+    assert abs(float(loss) - loss_ref) <= (1e-6 if prec == "f32" else 2e-2) * abs(loss_ref)
+    for i in range(3):
+        for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
+            ref = g[name]
+            err = float(np.linalg.norm(got.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30))
+            assert err <= tol, (name, err)
+    if train_fc:
+        err = float(np.linalg.norm(dWfc.cpu().numpy() - g["wfc"]) / np.linalg.norm(g["wfc"]))
+        assert err <= tol, ("wfc", err)
+
+
+def test_sgd_momentum_step(di):
+    n1, n2, phi, params, x, y = _train_case(False)
+    net = di.Net(phi, params, n1, n2, prec="f32")
+    yd, xd = _cuda(y), _cuda(x)
+    saved = net.new_saved(2)
+    p = {k: v.astype(np.float64) for k, v in params.items()}
+    v = {k: np.zeros_like(a) for k, a in p.items()}
+    for step in range(2):
+        net.forward(yd, saved=saved)
+        loss, dW, db, _ = net.backward(yd, xd, saved)
+        net.sgd_momentum(dW, db, lr=1e-2, mu=0.9)
+        for i in range(3):
+            for name, gg in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
+                p[name], v[name] = oracle.sgd_momentum(p[name], v[name], gg.cpu().numpy(), 1e-2, 0.9)
+    got = net.get_params()
+    for k in p:
+        np.testing.assert_allclose(got[k].cpu().numpy(), p[k], rtol=1e-5, atol=1e-7)
+
+
+def test_autograd_function(di):
+    import torch
+    n1, n2, phi, params, x, y = _train_case(False)
+    net = di.Net(phi, params, n1, n2, prec="f32")
+    ps = [torch.tensor(params[k], requires_grad=True, device="cuda")
+          for k in ("w1", "b1", "w2", "b2", "w3", "b3")]
+    loss = di.mse_loss(net, _cuda(y), _cuda(x), ps)
+    loss.backward()
+    loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi)
+    assert abs(float(loss.detach()) - loss_ref) <= 1e-5 * loss_ref
+    err = np.linalg.norm(ps[2].grad.cpu().numpy() - g["w2"]) / np.linalg.norm(g["w2"])
+    assert err <= 1e-4
+
+
+def test_device_status_clean(di):
+    assert di.device_status() == 0
