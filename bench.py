@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""DeepInverse recovery throughput on GB300 (images/s), one JSON line.
+
+Workload: 64 x 64 images (N = 4096), M/N = 0.1 (M = 410), batch 1024 per GPU,
+the paper's network (FC = Phi^T, then 64 / 32 / 1 filters of 11 x 11, Sec. 4-5),
+seeded synthetic piecewise-smooth images standing in for the 64 x 64 ImageNet
+crops of Sec. 5.  One step = sense and recover one batch: y = Phi x, then
+x^ = M(y, Omega), on the bfloat16 tensor-core path (float32 accumulation).
+
+Also reported: the float32 CUDA-core path on the same batch (images/s and the
+rel-L2 between the two paths), the end-to-end rate through the host-memory
+entry point, the conv2 roofline fraction, the clocks seen during the timed
+region, and the FP64 CPU oracle's rate on a bounded sample of the batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank recovers its own batch (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "images/s at 64x64, M/N=0.1: BF16 vs FP32 at rel-L2<=1e-2; serving p50/p99 ms"
+CONV2_MAC_PER_PX = 64 * 32 * 121
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--size", type=int, default=64)
+    ap.add_argument("--ratio", type=float, default=0.10)
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sust=float(d["bf16_tflops_sustained"]), src="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback")
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) around the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(args, rank=0):
+    from paper_1701_03891_gb300 import synth
+    n = args.size
+    N = n * n
+    M = synth.m_for_ratio(args.ratio, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    params = synth.he_params(seed=1)
+    x = synth.voronoi_images(args.batch, n, n, seed=3 + rank)
+    return n, N, M, phi, params, x
+
+
+def config(args, n, M, world):
+    return {"workload": "DeepInverse sense+recover %dx%d, M/N=%.2f (M=%d), batch %d per GPU, "
+                        "FC=Phi^T + conv 64/32/1 @ 11x11" % (n, n, args.ratio, M, args.batch),
+            "image_size": n, "M": M, "global_batch": args.batch * world,
+            "parallelism": "replicas (dp%d, no collective)" % world,
+            "l2": "flushed (%d MiB write) before every timed step, outside its events" % (L2_FLUSH_BYTES >> 20)}
+
+
+def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the batch."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    errs = []
+    chunk = 4
+    while done < x.shape[0] and (time.perf_counter() - t0) < args.cpu_seconds:
+        xs = x[done:done + chunk]
+        ref = oracle.forward(oracle.measure(phi, xs), params, n, n, phi=phi)
+        if gpu_xhat is not None:
+            errs.append(oracle.rel_l2(gpu_xhat[done:done + chunk], ref))
+        done += xs.shape[0]
+    dt = time.perf_counter() - t0
+    out = {"value": done / dt, "unit": "images/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "%d of the %d batch images (FP64 oracle, OpenMP over output channels, %.1f s)"
+                     % (done, x.shape[0], dt)}
+    if errs:
+        out["bf16_vs_oracle_max_rel_l2"] = float(np.max(np.concatenate(errs)))
+    return out
+
+
+def traffic_record():
+    """ncu DRAM bytes per conv2 image from profiles/, valid only for the current kernel source."""
+    src = os.path.join(ROOT, "paper_1701_03891_gb300", "csrc", "tc_kernels.cu")
+    rec = os.path.join(ROOT, "profiles", "conv2_traffic.json")
+    try:
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(rec) as f:
+            d = json.load(f)
+        if d.get("kernel_sha") == h:
+            return float(d["dram_bytes_per_image"])
+    except Exception:
+        pass
+    return None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1701_03891_gb300 import synth
+    oracle.build()
+    n = args.size
+    N = n * n
+    M = synth.m_for_ratio(args.ratio, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    params = synth.he_params(seed=1)
+    x = synth.voronoi_images(max(1, args.steps + args.warmup), n, n, seed=3)
+    for i in range(args.warmup):
+        oracle.forward(oracle.measure(phi, x[i:i + 1]), params, n, n, phi=phi)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = args.warmup + i
+        oracle.forward(oracle.measure(phi, x[j:j + 1]), params, n, n, phi=phi)
+    dt = time.perf_counter() - t0
+    val = args.steps / dt
+    cfg = config(args, n, M, 1)
+    cfg["workload"] += "; reference = FP64 CPU oracle, one image per step"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "images/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Voronoi images standing in for ImageNet 64x64 crops)",
+            "config": cfg,
+            "cpu_baseline": {"value": val, "unit": "images/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "one image of the batch per step, %d steps" % args.steps},
+            "e2e": {"value": val, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1701_03891_gb300 import build as libbuild, deepinv
+    libbuild.build()
+    n, N, M, phi, params, x = workload(args, rank)
+    B = args.batch
+    pk = peaks()
+
+    net = deepinv.Net(phi, params, n, n, prec="bf16")
+    net.reserve(B)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty((B, M), device="cuda")
+    xh = torch.empty((B, N), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        net.measure(xd, out=yd)
+        net.forward(yd, out=xh)
+
+    clocks = Clocks(local)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
+    time.sleep(0.25)
+    net.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    stages = net.profile_read()
+    net.profile(False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms = float(t.item())
+    value = world * B * args.steps / (dev_ms / 1000.0)
+    ms_per_step = dev_ms / args.steps
+
+    conv2_ms = stages["conv2"][0] / max(1, stages["conv2"][1])
+    conv2_flop = 2.0 * CONV2_MAC_PER_PX * B * n * n
+    achieved = conv2_flop / (conv2_ms / 1000.0) / 1e12
+    dram = traffic_record()
+    roof = {"bound": "tensor", "kernel": "conv2 (tap-stacked tcgen05 implicit GEMM)",
+            "achieved": achieved, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
+            "frac": achieved / pk["bf16_sust"],
+            "peak_note": "bf16 sustained of %s (MEASURED_PEAKS.json)" % pk["src"] if pk["src"] == "measured"
+            else "bf16 sustained of fallback",
+            "traffic": (dram * B) if dram is not None else None,
+            "algorithmic_flop_per_launch": conv2_flop}
+    stage_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items()}
+
+    bf16_out = xh.cpu().numpy()
+    # float32 CUDA-core path on the same batch
+    netf = deepinv.Net(phi, params, n, n, prec="f32")
+    netf.reserve(B)
+    yf = torch.empty((B, M), device="cuda")
+    xf = torch.empty((B, N), device="cuda")
+    netf.measure(xd, out=yf)
+    netf.forward(yf, out=xf)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.fp32_steps):
+        netf.measure(xd, out=yf)
+        netf.forward(yf, out=xf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f32_ms = e0.elapsed_time(e1) / args.fp32_steps
+    f32_out = xf.cpu().numpy()
+    rel = np.linalg.norm(bf16_out - f32_out, axis=1) / np.linalg.norm(f32_out, axis=1)
+    del netf, yf, xf
+
+    # end to end through the host-memory entry point
+    xh_host = torch.from_numpy(x).pin_memory()
+    out_host = torch.empty((B, N), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        net.sense_recover_host(xh_host, out_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        net.sense_recover_host(xh_host, out_host)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * B * args.e2e_steps / e2e_s, "unit": "images/s",
+           "h2d_bytes_per_step": B * N * 4, "d2h_bytes_per_step": B * N * 4,
+           "call": "deepinv_sense_recover_host (pinned x in, pinned x^ out, synchronous)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, phi, params, x, n, gpu_xhat=bf16_out)
+
+    status = deepinv.device_status()
+    line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded Voronoi images standing in for ImageNet 64x64 crops; He-init weights)",
+            "config": config(args, n, M, world),
+            "roofline": roof, "stage_ms": stage_ms,
+            "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
+                     "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
+                     "bf16_vs_fp32_max_rel_l2": float(rel.max())},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -153,6 +153,28 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float
 int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc,
                        void* stream);
 
+/* Stages of the forward pass timed by the profiler. */
+#define DEEPINV_NSTAGES 5
+enum {
+    DEEPINV_STAGE_MEASURE = 0, /* y = Phi x (deepinv_net_measure) */
+    DEEPINV_STAGE_FC = 1,      /* x~ = Phi^T y, written in the conv1 input layout */
+    DEEPINV_STAGE_CONV1 = 2,
+    DEEPINV_STAGE_CONV2 = 3,
+    DEEPINV_STAGE_CONV3 = 4
+};
+
+/* Profiling of the network's calls by CUDA events.  While enabled,
+ * deepinv_net_measure and deepinv_forward record an event before and after
+ * each stage on the caller's stream (no synchronisation).  Enabling or
+ * disabling clears what was recorded. */
+int deepinv_profile_enable(deepinv_net* net, int enable);
+
+/* Wait for the recorded events and return, per stage, the summed device
+ * milliseconds and the number of recorded executions (either array may be
+ * NULL); then clear the record. */
+int deepinv_profile_read(deepinv_net* net, float stage_ms[DEEPINV_NSTAGES],
+                         int stage_count[DEEPINV_NSTAGES]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,7 @@ using namespace di;
 
 struct deepinv_net {
     deepinv_net_desc d;
+    int dev = 0;       // CUDA device the network lives on
     int N = 0;
     int num_sms = 1;
     Geo geo{};
@@ -94,9 +95,73 @@ struct deepinv_net {
     // backward workspace
     char* bws = nullptr;
     size_t bws_bytes = 0;
+    // profiler: event pool and (stage, start event, end event) spans
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> spans;
 };
 
 namespace {
+
+// Makes `dev` current for this library's runtime for the duration of a call
+// (the library's CUDA runtime state is separate from the caller's).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int device_of(const void* p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ? a.device : -1;
+}
+
+// Record an event from the pool on `st`; returns its index or -1.
+int prof_event(deepinv_net* n, cudaStream_t st)
+{
+    if (n->ev_used == n->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return -1; }
+        n->ev_pool.push_back(e);
+    }
+    const int i = (int)n->ev_used++;
+    if (cudaEventRecord(n->ev_pool[i], st) != cudaSuccess) { cudaGetLastError(); return -1; }
+    return i;
+}
+
+// Marks the start of a stage; its destructor records the end and the span.
+struct StageTimer {
+    deepinv_net* n;
+    cudaStream_t st;
+    int stage, e0;
+    StageTimer(deepinv_net* n_, cudaStream_t st_, int stage_) : n(n_), st(st_), stage(stage_), e0(-1)
+    {
+        if (n->prof) e0 = prof_event(n, st);
+    }
+    ~StageTimer()
+    {
+        if (!n->prof || e0 < 0) return;
+        const int e1 = prof_event(n, st);
+        if (e1 < 0) return;
+        n->spans.push_back(stage);
+        n->spans.push_back(e0);
+        n->spans.push_back(e1);
+    }
+};
 
 struct Arena {
     char* base;
@@ -251,6 +316,7 @@ void free_net(deepinv_net* n)
     cudaFree(n->w3p);
     cudaFree(n->ws);
     cudaFree(n->bws);
+    for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
     delete n;
 }
 
@@ -305,20 +371,44 @@ int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved
         bf16* a1 = saved ? sv.a1 : w.a1;
         bf16* a2 = saved ? sv.a2 : w.a2;
         const int nb = fc_nb(B);
-        DI_TRY(pack_kmajor(y, M, 1, B, M, nb, n->Kfc, w.ypk, st));
-        DI_TRY(tc_gemm(n->fcA, w.ypk, n->Kfc, N, B, nb, GEMM_OUT_PLANE, nullptr, 0, xt, g, status, st));
-        DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, status, st));
-        DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], a2, n->num_sms, status, st));
-        DI_TRY(conv3_tc(a2, B, g, n->w3p, n->b[2], w.T, xhat, n->d.final_relu, status, st));
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_FC);
+            DI_TRY(pack_kmajor(y, M, 1, B, M, nb, n->Kfc, w.ypk, st));
+            DI_TRY(tc_gemm(n->fcA, w.ypk, n->Kfc, N, B, nb, GEMM_OUT_PLANE, nullptr, 0, xt, g, status, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV1);
+            DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, status, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV2);
+            DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], a2, n->num_sms, status, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV3);
+            DI_TRY(conv3_tc(a2, B, g, n->w3p, n->b[2], w.T, xhat, n->d.final_relu, status, st));
+        }
     } else {
         float* xt = saved ? sv.fxt : w.fxt;
         float* a1 = saved ? sv.fa1 : w.fa1;
         float* a2 = saved ? sv.fa2 : w.fa2;
-        if (n->wfc) DI_TRY(sgemm(B, N, M, y, M, 1, n->wfc, 1, M, xt, N, st));
-        else DI_TRY(sgemm(B, N, M, y, M, 1, n->phi, N, 1, xt, N, st));
-        DI_TRY(conv_f32(xt, B, 1, H, W, n->w[0], n->b[0], n->d.l1, k, a1, 1, st));
-        DI_TRY(conv_f32(a1, B, n->d.l1, H, W, n->w[1], n->b[1], n->d.l2, k, a2, 1, st));
-        DI_TRY(conv_f32(a2, B, n->d.l2, H, W, n->w[2], n->b[2], 1, k, xhat, n->d.final_relu, st));
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_FC);
+            if (n->wfc) DI_TRY(sgemm(B, N, M, y, M, 1, n->wfc, 1, M, xt, N, st));
+            else DI_TRY(sgemm(B, N, M, y, M, 1, n->phi, N, 1, xt, N, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV1);
+            DI_TRY(conv_f32(xt, B, 1, H, W, n->w[0], n->b[0], n->d.l1, k, a1, 1, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV2);
+            DI_TRY(conv_f32(a1, B, n->d.l1, H, W, n->w[1], n->b[1], n->d.l2, k, a2, 1, st));
+        }
+        {
+            StageTimer t(n, st, DEEPINV_STAGE_CONV3);
+            DI_TRY(conv_f32(a2, B, n->d.l2, H, W, n->w[2], n->b[2], 1, k, xhat, n->d.final_relu, st));
+        }
     }
     if (saved) DI_CUDA(cudaMemcpyAsync(sv.xhat, xhat, (size_t)B * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return DEEPINV_OK;
@@ -328,8 +418,9 @@ int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream
 {
     if (B == 0) return DEEPINV_OK;
     const int N = n->N, M = n->d.M;
+    DI_TRY(ensure_ws(n, B, st));
+    StageTimer t(n, st, DEEPINV_STAGE_MEASURE);
     if (n->tc) {
-        DI_TRY(ensure_ws(n, B, st));
         const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
         return measure_bf16_packed(n->msB, n->Kms, n->NBms, x, N, M, B, y, w.xpk, st);
     }
@@ -347,12 +438,21 @@ int deepinv_version(void) { return 100; }
 
 int deepinv_device_status(int reset)
 {
-    int* p = device_status_word();
-    DI_REQUIRE(p, "no CUDA device");
-    DI_CUDA(cudaDeviceSynchronize());
+    std::vector<int*> words;
+    {
+        std::lock_guard<std::mutex> lk(g_status_mu);
+        words = g_status_words;
+    }
     int v = 0;
-    DI_CUDA(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (reset) DI_CUDA(cudaMemset(p, 0, sizeof(int)));
+    for (int dev = 0; dev < (int)words.size(); ++dev) {
+        if (!words[dev]) continue;
+        DeviceGuard g(dev);
+        DI_CUDA(cudaDeviceSynchronize());
+        int w = 0;
+        DI_CUDA(cudaMemcpy(&w, words[dev], sizeof(int), cudaMemcpyDeviceToHost));
+        if (reset) DI_CUDA(cudaMemset(words[dev], 0, sizeof(int)));
+        if (w) v = w;
+    }
     if (v == DEV_TIMEOUT) {
         set_error("a bounded wait inside a kernel ran out");
         return DEEPINV_ETIMEOUT;
@@ -366,6 +466,7 @@ int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float
     DI_REQUIRE(B == 0 || (phi && x && y), "null pointer");
     DI_REQUIRE(prec == DEEPINV_F32 || prec == DEEPINV_BF16, "unknown precision %d", prec);
     if (B == 0) return DEEPINV_OK;
+    DeviceGuard dg(device_of(phi));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (prec == DEEPINV_F32) return sgemm(B, M, N, x, N, 1, phi, 1, N, y, M, st);
     const int Kp = up16(N), NB = gemm_nb(M);
@@ -393,10 +494,14 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
     DI_TRY(check_desc(desc));
     DI_REQUIRE(phi && w && b, "null pointer");
     for (int l = 0; l < 3; ++l) DI_REQUIRE(w[l] && b[l], "null weight pointer for layer %d", l + 1);
+    const int dev = device_of(phi);
+    DI_REQUIRE(dev >= 0, "phi is not device memory");
+    DeviceGuard dg(dev);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     deepinv_net* n = new (std::nothrow) deepinv_net();
     DI_REQUIRE(n, "host allocation failed");
     n->d = *desc;
+    n->dev = dev;
     n->N = desc->n1 * desc->n2;
     n->tc = desc->prec == DEEPINV_BF16;
     n->num_sms = num_sms_current();
@@ -446,6 +551,7 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
 int deepinv_net_destroy(deepinv_net* net)
 {
     if (!net) return DEEPINV_OK;
+    DeviceGuard dg(net->dev);
     cudaDeviceSynchronize();
     free_net(net);
     return DEEPINV_OK;
@@ -461,6 +567,7 @@ int deepinv_net_get_desc(const deepinv_net* net, deepinv_net_desc* desc)
 int deepinv_net_reserve(deepinv_net* net, int max_B, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(max_B >= 0, "bad batch %d", max_B);
     if (max_B == 0) return DEEPINV_OK;
     return ensure_ws(net, max_B, static_cast<cudaStream_t>(stream));
@@ -469,6 +576,7 @@ int deepinv_net_reserve(deepinv_net* net, int max_B, void* stream)
 int deepinv_net_measure(deepinv_net* net, const float* x, int B, float* y, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (x && y), "null pointer");
     return net_measure_impl(net, x, B, y, static_cast<cudaStream_t>(stream));
@@ -483,6 +591,7 @@ size_t deepinv_saved_bytes(const deepinv_net* net, int B)
 int deepinv_forward(deepinv_net* net, const float* y, int B, float* xhat, void* saved, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (y && xhat), "null pointer");
     return forward_impl(net, y, B, xhat, saved, static_cast<cudaStream_t>(stream));
@@ -491,6 +600,7 @@ int deepinv_forward(deepinv_net* net, const float* y, int B, float* xhat, void* 
 int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xhat_host, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (y_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
@@ -507,6 +617,7 @@ int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xh
 int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, float* xhat_host, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (x_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
@@ -525,6 +636,7 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
                      float* const dW[3], float* const db[3], float* dWfc, double* loss, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 1, "bad batch %d", B);
     DI_REQUIRE(y && x && saved && dW && db && loss, "null pointer");
     for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
@@ -604,6 +716,7 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float
                          float lr, float mu, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     DI_REQUIRE(dW && db, "null pointer");
     for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
@@ -620,6 +733,7 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float
 int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int l = 0; l < 3; ++l) {
         if (w && w[l]) DI_CUDA(cudaMemcpyAsync(w[l], net->w[l], wsize(net, l) * 4, cudaMemcpyDeviceToDevice, st));
@@ -628,6 +742,41 @@ int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b
     if (wfc) {
         DI_REQUIRE(net->wfc, "network has no trainable FC weights");
         DI_CUDA(cudaMemcpyAsync(wfc, net->wfc, (size_t)net->N * net->d.M * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return DEEPINV_OK;
+}
+
+int deepinv_profile_enable(deepinv_net* net, int enable)
+{
+    DI_REQUIRE(net, "net is NULL");
+    net->prof = enable != 0;
+    net->spans.clear();
+    net->ev_used = 0;
+    return DEEPINV_OK;
+}
+
+int deepinv_profile_read(deepinv_net* net, float stage_ms[DEEPINV_NSTAGES], int stage_count[DEEPINV_NSTAGES])
+{
+    DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
+    float ms[DEEPINV_NSTAGES] = {0};
+    int cnt[DEEPINV_NSTAGES] = {0};
+    for (size_t i = 0; i + 2 < net->spans.size(); i += 3) {
+        const int stg = net->spans[i];
+        cudaEvent_t e0 = net->ev_pool[net->spans[i + 1]], e1 = net->ev_pool[net->spans[i + 2]];
+        DI_CUDA(cudaEventSynchronize(e1));
+        float t = 0.f;
+        DI_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        if (stg >= 0 && stg < DEEPINV_NSTAGES) {
+            ms[stg] += t;
+            cnt[stg] += 1;
+        }
+    }
+    net->spans.clear();
+    net->ev_used = 0;
+    for (int s = 0; s < DEEPINV_NSTAGES; ++s) {
+        if (stage_ms) stage_ms[s] = ms[s];
+        if (stage_count) stage_count[s] = cnt[s];
     }
     return DEEPINV_OK;
 }

@@ -65,7 +65,12 @@ SIGNATURES = {
     "deepinv_backward": (_I, [_P, _P, _P, _I, _P, _PP, _PP, _P, _P, _P]),
     "deepinv_sgd_momentum": (_I, [_P, _PP, _PP, _P, ctypes.c_float, ctypes.c_float, _P]),
     "deepinv_get_params": (_I, [_P, _PP, _PP, _P, _P]),
+    "deepinv_profile_enable": (_I, [_P, _I]),
+    "deepinv_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
 }
+
+NSTAGES = 5
+STAGES = ("measure", "fc", "conv1", "conv2", "conv3")
 
 
 def lib():
@@ -244,6 +249,17 @@ class Net:
         bp, _k2 = _arr([t.data_ptr() for t in db])
         _check(lib().deepinv_sgd_momentum(self._h, wp, bp, _ptr(dWfc), float(lr), float(mu),
                                           _stream(stream)))
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) recording CUDA events around each stage of measure/forward."""
+        _check(lib().deepinv_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{stage: (total device ms, count)} since profile(True); clears the record."""
+        ms = (ctypes.c_float * NSTAGES)()
+        cnt = (ctypes.c_int * NSTAGES)()
+        _check(lib().deepinv_profile_read(self._h, ms, cnt))
+        return {STAGES[i]: (float(ms[i]), int(cnt[i])) for i in range(NSTAGES)}
 
     def get_params(self, stream=None) -> dict:
         import torch
