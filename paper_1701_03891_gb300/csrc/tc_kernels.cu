@@ -63,7 +63,7 @@ __global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, 
 }
 
 // conv1 B operand: (n = filter co, k = tap t = 11 dy + dx), t >= 121 zero.
-// conv2 A operand: block (dy, s, kk) holds rows m = 4 co + g (g = tap slot),
+// conv2 A operand: block (dy, s, kk) holds rows m = 32 g + co (g = tap slot),
 //   K = input channels 16 kk .. 16 kk + 15, weight W2[co][ci][dy][4 s + g]
 //   (zero when 4 s + g = 11).
 // conv3 B operand: block (dx, kk) holds rows n = dy (zero for dy >= 11),
@@ -88,7 +88,7 @@ __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const flo
             const int kk = (int)((j / (8 * 128 * 2)) % 4);
             const int s = (int)((j / (8 * 128 * 2 * 4)) % 3);
             const int dy = (int)(j / (8 * 128 * 2 * 4 * 3));
-            const int co = m / 4, g = m % 4, dx = 4 * s + g, ci = kk * 16 + half * 8 + e;
+            const int co = m % 32, g = m / 32, dx = 4 * s + g, ci = kk * 16 + half * 8 + e;
             const float v = dx < 11 ? w2[((co * 64 + ci) * 11 + dy) * 11 + dx] : 0.f;
             w2p[j] = __float2bfloat16_rn(v);
         } else {
@@ -241,6 +241,7 @@ struct Conv1Smem {
     uint64_t wbar, mbar;
     uint32_t tmem_base;
     int abort_flag;
+    float bias[64];
 };
 
 __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt, int H, int W, int P,
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
         ss->abort_flag = 0;
         fence_mbar_init();
     }
+    if (threadIdx.x < 64) ss->bias[threadIdx.x] = __ldg(&b1[threadIdx.x]);
     if (warp == 0) {
         tmem_alloc(smem_u32(&ss->tmem_base), 64);
         tmem_relinquish();
@@ -286,17 +288,24 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
         for (int i = threadIdx.x; i < winx / 8; i += 128) dst[i] = src[i];
     }
     __syncthreads();
-    // im2col: chunk (kc, m) holds taps 8 kc .. 8 kc + 7 of position q0 + m
-    for (int i = threadIdx.x; i < 16 * 128; i += 128) {
-        const int kc = i / 128, m = i % 128;
-        float v[8];
+    // im2col: thread m builds row m (position q0 + m) of all 16 chunks; chunk kc
+    // holds taps 8 kc .. 8 kc + 7 (tap t = 11 dy + dx, taps >= 121 zero),
+    // copied as raw bf16 bits.
+    {
+        const int m = threadIdx.x;
+        const unsigned short* w16 = reinterpret_cast<const unsigned short*>(sWin) + m;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int tap = kc * 8 + e;
-            const int dy = tap / 11, dx = tap % 11;
-            v[e] = tap < 121 ? __bfloat162float(sWin[m + dy * P + dx]) : 0.f;
+        for (int kc = 0; kc < 16; ++kc) {
+            uint32_t u[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+                const int t0 = kc * 8 + 2 * e2, t1 = t0 + 1;
+                const uint32_t lo = t0 < 121 ? w16[(t0 / 11) * P + t0 % 11] : 0u;
+                const uint32_t hi = t1 < 121 ? w16[(t1 / 11) * P + t1 % 11] : 0u;
+                u[e2] = lo | (hi << 16);
+            }
+            reinterpret_cast<uint4*>(sA)[kc * 128 + m] = make_uint4(u[0], u[1], u[2], u[3]);
         }
-        reinterpret_cast<uint4*>(sA)[i] = pack8_bf16(v);
     }
     fence_proxy_async();
     __syncthreads();
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
             float v[16];
             tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + __ldg(&b1[c0 + i]), 0.f) : 0.f;
+            for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + ss->bias[c0 + i], 0.f) : 0.f;
             if (valid) {
                 *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8) * plane_len * 8) = pack8_bf16(v);
                 *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8 + 1) * plane_len * 8) = pack8_bf16(v + 8);
@@ -347,13 +356,15 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
 
 // ---------------------------------------------------------------- conv2
 // Tap-stacked implicit GEMM.  For kernel row dy and column group s (taps
-// dx = 4 s + g, g = 0..3), one MMA with M = 128 rows (row 4 co + g: filter co,
-// tap slot g), N = 256 positions and K = 16 channels computes
+// dx = 4 s + g, g = 0..3), one MMA with M = 128 rows (row 32 g + co: tap slot
+// g, filter co), N = 256 positions and K = 16 channels computes
 //   D_g[co][n] += sum_ci W2[co][ci][dy][4 s + g] a1[q0 + n + dy P + 4 s][ci],
-// so that output q0 + j = sum_g D_g[co][j + g]: the four slots of one filter
-// are four adjacent TMEM lanes and are summed with two warp shuffles in the
-// epilogue.  33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253
-// valid outputs per tile (the last 3 columns lack their slot-3 partner).
+// so that output q0 + j = sum_g D_g[co][j + g].  Slot g is TMEM lane quarter
+// g, i.e. epilogue warp g: each warp reads its slot shifted by g columns, the
+// four slots are added through a small shared-memory exchange, and each
+// thread then stores 8 channels of one position as one 16-byte vector.
+// 33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253 valid outputs
+// per tile (the last 3 columns lack their slot-3 partner).
 //
 // Persistent CTAs, 6 warps: warp 0 lane 0 streams the input window (slabs of
 // 128 positions x 64 channels, freed as soon as the last kernel row reading
@@ -363,6 +374,9 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
 constexpr int kW2Stages = 4;
 constexpr int kMaxSlabs = 10;
 
+constexpr int kXStride = 36;          // floats per row of the slot exchange (32 + 4 pad)
+constexpr int kXBytes = 4 * 32 * kXStride * 4;
+
 struct Conv2Smem {
     uint64_t full[kMaxSlabs], empty[kMaxSlabs];
     uint64_t wfull[kW2Stages], wempty[kW2Stages];
@@ -370,7 +384,19 @@ struct Conv2Smem {
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
+    int vote[2][4];
 };
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Row of the slot exchange: x[j] = v[j + G] (the slot-G contribution to column j).
+template <int G>
+__device__ __forceinline__ void put_shifted(float* x, const float* v)
+{
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(x + j) = make_float4(v[j + G], v[j + G + 1], v[j + G + 2], v[j + G + 3]);
+}
 
 __host__ __device__ inline int conv2_dylast(int j, int P)
 {
@@ -389,7 +415,8 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
     const uint32_t CH = (uint32_t)win_px * 16;     // bytes per 8-channel chunk plane of the window
     uint8_t* sWin = smem_raw;                       // [8][win_px][8] bf16
     uint8_t* sW = smem_raw + 8 * CH;                // [kW2Stages][16 KB]
-    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * 16384);
+    float* sX = reinterpret_cast<float*>(sW + kW2Stages * 16384);   // [4 slots][32 filters][kXStride]
+    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * 16384 + kXBytes);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int HP = H * P;
@@ -505,44 +532,58 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
         mbar_wait_drain(smem_u32(&ss->drain), 0);
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
-        const int q = warp % 4;               // TMEM lane quarter = filters 8 q .. 8 q + 7
-        const int g = lane & 3;               // tap slot of this lane
-        const int co = q * 8 + (lane >> 2);
-        const float bias = __ldg(&b2[co]);
+        const int g = warp % 4;                   // TMEM lane quarter = tap slot; lane = filter
+        const int le = threadIdx.x - 64;          // 0..127
+        const int c8 = le / 32, jl = le % 32;     // sum phase: filters 8 c8 .. 8 c8 + 7, column jl
+        float bias8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) bias8[e] = __ldg(&b2[c8 * 8 + e]);
+        float* xrow = sX + (g * 32 + lane) * kXStride;
+        const float* xsum = sX + c8 * 8 * kXStride + jl;
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int buf = it & 1, use = it >> 1;
             bool ok = mbar_wait(smem_u32(&ss->acc_full[buf]), use & 1, status, &ss->abort_flag);
-            if (!__all_sync(0xffffffffu, ok)) break;
+            ok = __all_sync(0xffffffffu, ok);
+            if (lane == 0) ss->vote[buf][g] = ok ? 1 : 0;
+            epi_bar();
+            ok = ss->vote[buf][0] && ss->vote[buf][1] && ss->vote[buf][2] && ss->vote[buf][3];
+            if (!ok) break;
             tc_fence_after();
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
-            bf16* dst = a2 + ((size_t)b * 4 + q) * plane_len * 8 + (lane >> 2);
-            const uint32_t lane_addr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kConv2N;
-            for (int cc = 0; cc < kConv2N / 32; ++cc) {
+            bf16* dst = a2 + ((size_t)b * 4 + c8) * plane_len * 8;
+            const uint32_t lane_addr = tbase + ((uint32_t)(g * 32) << 16) + (uint32_t)buf * kConv2N;
+            for (int cc = 0; cc < kConv2N; cc += 32) {
                 float v[36];
-                tmem_ld32(lane_addr + cc * 32, v);
-                if (cc < kConv2N / 32 - 1) {
-                    tmem_ld4(lane_addr + cc * 32 + 32, v + 32);
+                tmem_ld32(lane_addr + cc, v);
+                if (cc + 32 < kConv2N) {
+                    tmem_ld4(lane_addr + cc + 32, v + 32);
                 } else {
                     v[32] = v[33] = v[34] = v[35] = 0.f;
                 }
-                float res[8];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    float t = g == 0 ? v[j] : g == 1 ? v[j + 1] : g == 2 ? v[j + 2] : v[j + 3];
-                    t += __shfl_xor_sync(0xffffffffu, t, 1);
-                    t += __shfl_xor_sync(0xffffffffu, t, 2);
-                    if ((j & 3) == g) res[j >> 2] = t;
+                switch (g) {
+                    case 0: put_shifted<0>(xrow, v); break;
+                    case 1: put_shifted<1>(xrow, v); break;
+                    case 2: put_shifted<2>(xrow, v); break;
+                    default: put_shifted<3>(xrow, v); break;
                 }
+                epi_bar();
+                float acc[8];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int jcol = cc * 32 + jj * 4 + g;
-                    const int qq = q0 + jcol;
-                    if (jcol < kConv2Valid && qq < HP) {
-                        const float val = (qq % P) < W ? fmaxf(res[jj] + bias, 0.f) : 0.f;
-                        dst[(size_t)(qq + kPad * P + kPad) * 8] = __float2bfloat16_rn(val);
-                    }
+                for (int e = 0; e < 8; ++e) {
+                    float t = bias8[e];
+#pragma unroll
+                    for (int gg = 0; gg < 4; ++gg) t += xsum[(gg * 32 + e) * kXStride];
+                    acc[e] = t;
                 }
+                const int jcol = cc + jl, qq = q0 + jcol;
+                if (jcol < kConv2Valid && qq < HP) {
+                    const bool data = (qq % P) < W;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[e] = data ? fmaxf(acc[e], 0.f) : 0.f;
+                    *reinterpret_cast<uint4*>(dst + (size_t)(qq + kPad * P + kPad) * 8) = pack8_bf16(acc);
+                }
+                epi_bar();
             }
             tc_fence_before();
             __syncwarp();
@@ -747,7 +788,7 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
 
 static size_t conv2_smem_bytes(const Geo& g)
 {
-    return (size_t)8 * g.nslab * kSlabPx * 16 + (size_t)kW2Stages * 16384 + sizeof(Conv2Smem);
+    return (size_t)8 * g.nslab * kSlabPx * 16 + (size_t)kW2Stages * 16384 + kXBytes + sizeof(Conv2Smem);
 }
 
 bool conv2_tc_supported(const Geo& g)
