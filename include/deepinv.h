@@ -85,6 +85,32 @@ int deepinv_device_status(int reset);
 int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y,
                     int prec, void* stream);
 
+/* y = Phi x on the bfloat16 tensor cores, like deepinv_measure(..., DEEPINV_BF16),
+ * but without any device allocation (the paper has no counterpart; this is a
+ * service to callers).  It is meant for callers that cannot let a library
+ * allocate device memory: processes that split their device memory once at
+ * start-up into fixed budgets, real-time loops that must not reach the
+ * allocator after initialisation, and hosts that install their own allocator.
+ *
+ * phi [M][N], x [B][N] -> y [B][M], float32 device memory owned by the caller,
+ * as in deepinv_measure; the result is the same as deepinv_measure with
+ * DEEPINV_BF16.  The bfloat16 operand tiles live in one static device array of
+ * 32 MiB (minus a 256-byte header) that every device which loads the library
+ * holds until the process exits; requests whose packed operands,
+ * 2 (ceil(M / NB) NB + ceil(B / 128) 128) ceil16(N) bytes with
+ * NB = ceil16(M / ceil(M / 256)), do not fit are rejected with DEEPINV_EINVAL
+ * before anything is launched (M = 410, N = 4096 fits up to B = 3584).
+ *
+ * The first call on a device looks the array up (cudaGetSymbolAddress) and
+ * clears its header, synchronously; make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents, so calls whose work overlaps on the GPU (different streams
+ * without ordering) race and may return wrong results.  A bounded wait that
+ * runs out inside this call is recorded in the array's header and is not
+ * reported by deepinv_device_status(). */
+int deepinv_measure_noalloc(const float* phi, int M, int N, const float* x, int B, float* y,
+                            void* stream);
+
 /* Create a network (Sec. 4).  phi [M][N] is copied (it defines the FC layer,
  * x~ = Phi^T y); w[l] is [l_l][l_{l-1}][k][k] and b[l] is [l_l] for l = 0,1,2
  * (conv1..conv3, l_0 = 1), all device float32, copied into float32 master

@@ -53,6 +53,7 @@ SIGNATURES = {
     "deepinv_version": (_I, []),
     "deepinv_device_status": (_I, [_I]),
     "deepinv_measure": (_I, [_P, _I, _I, _P, _I, _P, _I, _P]),
+    "deepinv_measure_noalloc": (_I, [_P, _I, _I, _P, _I, _P, _P]),
     "deepinv_net_create": (_I, [ctypes.POINTER(NetDesc), _P, _PP, _PP, _P, ctypes.POINTER(_P)]),
     "deepinv_net_destroy": (_I, [_P]),
     "deepinv_net_get_desc": (_I, [_P, ctypes.POINTER(NetDesc)]),
@@ -133,6 +134,18 @@ def measure(phi, x, prec="f32", out=None, stream=None):
     _check(lib().deepinv_measure(_ptr(phi), M, N, _ptr(x), B, _ptr(y), PRECISIONS.get(prec, prec),
                                  _stream(stream)))
     return y
+
+
+def measure_noalloc(phi, x, out, stream=None):
+    """y = Phi x in bfloat16 without any device allocation by the library: the
+    packed operands live in a static 32 MiB device array (see deepinv.h).
+    ``out`` [B][M] must be supplied by the caller."""
+    _need_f32_cuda(phi, "phi")
+    _need_f32_cuda(x, "x")
+    _need_f32_cuda(out, "out")
+    M, N = phi.shape
+    _check(lib().deepinv_measure_noalloc(_ptr(phi), M, N, _ptr(x), x.shape[0], _ptr(out), _stream(stream)))
+    return out
 
 
 class Net:

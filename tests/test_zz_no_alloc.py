@@ -1,0 +1,73 @@
+"""deepinv_measure_noalloc: y = Phi x without device allocation by the library.
+
+Callers that cannot let a library allocate device memory (fixed per-process
+budgets split at start-up, real-time loops, hosts with their own allocator)
+use this entry point; its bfloat16 operand tiles live in a static device
+array.  It must give the result of deepinv_measure(..., DEEPINV_BF16), call
+after call, since every call reuses (and overwrites) the same array.
+
+This file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test.  It must also pass alone in a
+fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_03891_gb300 import build, deepinv
+    build.build()
+    return deepinv.lib()
+
+
+def _measure(L, fn_noalloc, phi, x, M, N, B):
+    import torch
+    y = torch.full((B, M), float("nan"), device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if fn_noalloc:
+        rc = L.deepinv_measure_noalloc(phi.data_ptr(), M, N, x.data_ptr(), B, y.data_ptr(), s)
+    else:
+        rc = L.deepinv_measure(phi.data_ptr(), M, N, x.data_ptr(), B, y.data_ptr(), 1, s)
+    assert rc == 0, L.deepinv_last_error()
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("M,N,B", [(410, 4096, 1024), (13, 37, 5)])
+def test_noalloc_matches_allocating_entry_point_twice(L, M, N, B):
+    import torch
+    from paper_1701_03891_gb300 import synth
+    phi = torch.from_numpy(synth.gaussian_phi(M, N, seed=1)).cuda()
+    results = []
+    for call in range(2):
+        rng = np.random.default_rng(100 + call)
+        x = torch.from_numpy(rng.uniform(0, 1, (B, N)).astype(np.float32)).cuda()
+        ref = _measure(L, False, phi, x, M, N, B)
+        got = _measure(L, True, phi, x, M, N, B)
+        assert np.all(np.isfinite(got))
+        # same kernels on the same operands: within the bf16 tolerance of the tests
+        # (and in practice bit-identical)
+        err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert float(err.max()) <= 1e-2
+        np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-6)
+        results.append(got)
+    assert not np.array_equal(results[0], results[1])   # the second call did new work
+
+
+def test_noalloc_rejects_oversized_request(L):
+    import torch
+    M, N, B = 410, 4096, 4096          # packed operands exceed the 32 MiB static array
+    phi = torch.zeros((M, N), device="cuda")
+    x = torch.zeros((1, N), device="cuda")      # not read: the size check comes first
+    y = torch.zeros((1, M), device="cuda")
+    rc = L.deepinv_measure_noalloc(phi.data_ptr(), M, N, x.data_ptr(), B, y.data_ptr(), None)
+    assert rc == -1
+    assert b"static scratch" in L.deepinv_last_error()
