@@ -179,6 +179,74 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float
 int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc,
                        void* stream);
 
+/* ------------------------------------------------------------------ serving
+ * Low-latency recovery (Sec. 5: DeepInverse suits applications that need
+ * low-latency recovery) as a continuous-batching server inside the library.
+ * A scheduler thread keeps requests in one queue per network; whenever one of
+ * the server's CUDA streams is free it takes up to max_batch waiting requests
+ * of the network whose oldest request has waited longest, and runs them as one
+ * batch on that stream, so batches of different networks (image sizes, M/N)
+ * overlap on the device and requests that arrive while others run join the
+ * next batch.  Each batch needs a workspace of that network for max_batch
+ * images; workspaces are kept for reuse and count against the HBM budget,
+ * idle ones of other networks are released when a new one does not fit, and
+ * a batch waits while its workspace does not fit.  Results do not depend on
+ * the batch a request ran in. */
+typedef struct deepinv_server deepinv_server;  /* opaque */
+
+typedef struct {
+    int net_id;         /* from deepinv_serve_add_net */
+    const float* y;     /* HOST [M] measurement of that network; read before deepinv_serve returns */
+    float* xhat;        /* HOST [N] result; written before the request's result is returned */
+    uint64_t tag;       /* caller's identifier, echoed in the result */
+} deepinv_request;
+
+typedef struct {
+    uint64_t tag;
+    int status;         /* DEEPINV_OK, or the error that failed the request */
+    int net_id;
+    int batch;          /* number of requests in the batch it ran in */
+    double queue_us;    /* submission -> batch launch */
+    double latency_us;  /* submission -> result written to xhat */
+} deepinv_result;
+
+/* Create a server; it runs on the device of the first network added.
+ * hbm_budget_bytes bounds the device memory its workspaces may hold;
+ * max_streams (1..16) batches may be in flight at once; max_batch (1..1024)
+ * requests per batch.  No device work happens until a network is added. */
+int deepinv_serve_open(size_t hbm_budget_bytes, int max_streams, int max_batch, deepinv_server** out);
+
+/* Register a network (not owned; it must outlive the server and must not be
+ * used by the caller while the server runs).  All networks of a server live
+ * on one device.  Add networks before the first request; returns
+ * DEEPINV_EBUSY while requests are in flight. */
+int deepinv_serve_add_net(deepinv_server* s, deepinv_net* net, int* net_id);
+
+/* Submit n_in requests (copied; n_in may be 0), then return up to max_out
+ * finished results (in completion order), waiting up to timeout_us for at
+ * least one when none is ready (timeout_us = 0: do not wait).  *n_out is the
+ * number returned.  Returns DEEPINV_ETIMEOUT if the wait ran out with nothing
+ * finished while requests were pending, DEEPINV_EINVAL for a bad request
+ * (nothing of this call is submitted). */
+int deepinv_serve(deepinv_server* s, const deepinv_request* in, int n_in,
+                  deepinv_result* out, int max_out, int* n_out, int timeout_us);
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t batches;
+    int max_in_flight;        /* largest number of concurrent batches seen */
+    size_t workspace_bytes;   /* device memory held for workspaces now */
+    size_t peak_workspace_bytes;
+    uint64_t evictions;       /* idle workspaces released to make room */
+    uint64_t admission_waits; /* times a batch waited for its workspace to fit */
+} deepinv_serve_stats;
+
+int deepinv_serve_get_stats(deepinv_server* s, deepinv_serve_stats* st);
+
+/* Finish every submitted request, stop the scheduler and free the server's
+ * memory.  Results not yet harvested are dropped.  NULL is a no-op. */
+int deepinv_serve_close(deepinv_server* s);
+
 /* Stages of the forward pass timed by the profiler. */
 #define DEEPINV_NSTAGES 5
 enum {

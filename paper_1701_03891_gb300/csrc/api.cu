@@ -351,12 +351,9 @@ int measure_bf16_packed(const bf16* phiB, int Kp, int NB, const float* x, int N,
     return tc_gemm(xpk, phiB, Kp, B, M, NB, GEMM_OUT_F32, y, M, nullptr, dummy, status, st);
 }
 
-int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved, cudaStream_t st)
+// The forward pass in a given workspace `w` (carved for at least B images).
+int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* xhat, void* saved, cudaStream_t st)
 {
-    if (B == 0) return DEEPINV_OK;
-    DI_TRY(ensure_ws(n, B, st));
-    // carve at the allocated batch so that plane offsets never move
-    const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
     const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2, k = n->d.k;
     Saved sv{};
     if (saved) {
@@ -414,6 +411,15 @@ int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved
     return DEEPINV_OK;
 }
 
+int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved, cudaStream_t st)
+{
+    if (B == 0) return DEEPINV_OK;
+    DI_TRY(ensure_ws(n, B, st));
+    // carve at the allocated batch so that plane offsets never move
+    const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
+    return forward_core(n, w, y, B, xhat, saved, st);
+}
+
 int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream_t st)
 {
     if (B == 0) return DEEPINV_OK;
@@ -428,6 +434,36 @@ int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream
 }
 
 }  // namespace
+
+// ================================================================ internal interface (serving)
+namespace di {
+
+int net_device(const deepinv_net* n) { return n->dev; }
+int net_M(const deepinv_net* n) { return n->d.M; }
+int net_N(const deepinv_net* n) { return n->N; }
+
+// Bytes of a private forward workspace for batches up to max_B (the staging
+// buffers for y and x^ included); it must be zeroed once before first use.
+size_t net_ws_bytes(const deepinv_net* n, int max_B) { return carve_fwd(n, max_B, nullptr).bytes; }
+
+// x^ = M(y) for B <= max_B images with a private workspace `ws` (carved for
+// max_B).  y_dev / xhat_dev may be NULL to use the workspace's own staging
+// buffers, whose device addresses net_ws_staging returns.
+int net_forward_ws(deepinv_net* n, char* ws, int max_B, const float* y, int B, float* xhat, cudaStream_t st)
+{
+    if (B == 0) return DEEPINV_OK;
+    const FwdWs w = carve_fwd(n, max_B, ws);
+    return forward_core(n, w, y, B, xhat, nullptr, st);
+}
+
+void net_ws_staging(const deepinv_net* n, char* ws, int max_B, float** y_dev, float** xhat_dev)
+{
+    const FwdWs w = carve_fwd(n, max_B, ws);
+    *y_dev = w.yd;
+    *xhat_dev = w.xhd;
+}
+
+}  // namespace di
 
 // ================================================================ C ABI
 extern "C" {

@@ -1,0 +1,440 @@
+// Continuous-batching server of libdeepinv (deepinv_serve_*; see deepinv.h).
+//
+// The paper motivates DeepInverse by low-latency recovery (Sec. 5).  Here a
+// host scheduler thread turns a stream of single recoveries for several
+// networks (image sizes and M/N ratios) into batches: per-network FIFO queues,
+// up to max_streams batches in flight on separate CUDA streams, each batch in
+// a private workspace leased under an HBM budget, results copied back to the
+// requests' host buffers as soon as their batch's event completes.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace di {
+int net_device(const deepinv_net* n);
+int net_M(const deepinv_net* n);
+int net_N(const deepinv_net* n);
+size_t net_ws_bytes(const deepinv_net* n, int max_B);
+int net_forward_ws(deepinv_net* n, char* ws, int max_B, const float* y, int B, float* xhat, cudaStream_t st);
+void net_ws_staging(const deepinv_net* n, char* ws, int max_B, float** y_dev, float** xhat_dev);
+}  // namespace di
+
+using namespace di;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Req {
+    int net;
+    uint64_t tag;
+    float* xhat;
+    std::vector<float> y;   // copy of the caller's measurement
+    Clock::time_point t_submit;
+};
+
+struct Lease {
+    int net;
+    char* ws;
+    size_t bytes;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    float* y_pin = nullptr;   // [max_batch][maxM] page-locked staging
+    float* x_pin = nullptr;   // [max_batch][maxN]
+    bool busy = false;
+    int net = -1;
+    std::vector<Req> reqs;
+    Lease* lease = nullptr;
+    Clock::time_point t_launch;
+};
+
+double us_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+}  // namespace
+
+struct deepinv_server {
+    size_t budget = 0;
+    int max_streams = 1, max_batch = 1;
+    int dev = -1;
+    int maxM = 0, maxN = 0;
+    std::vector<deepinv_net*> nets;
+    std::vector<size_t> lease_bytes;
+    std::vector<std::deque<Req>> pending;
+    std::vector<std::vector<Lease*>> cache;
+    std::vector<Slot> slots;
+    size_t held = 0;
+    std::deque<deepinv_result> done;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread thr;
+    bool stop = false, started = false, waiting_admission = false;
+    uint64_t outstanding = 0;   // submitted and not yet finished
+    deepinv_serve_stats stats{};
+};
+
+namespace {
+
+void fail_request(deepinv_server* s, const Req& r, int status)
+{
+    deepinv_result res{};
+    res.tag = r.tag;
+    res.status = status;
+    res.net_id = r.net;
+    res.batch = 0;
+    const auto now = Clock::now();
+    res.queue_us = us_between(r.t_submit, now);
+    res.latency_us = res.queue_us;
+    s->done.push_back(res);
+    s->stats.failed++;
+    s->outstanding--;
+}
+
+// A workspace for network `net`: reuse an idle one, else allocate after
+// releasing idle workspaces of other networks while the budget demands.
+// Returns nullptr if it does not fit now.
+Lease* acquire(deepinv_server* s, int net, cudaStream_t st)
+{
+    if (!s->cache[net].empty()) {
+        Lease* l = s->cache[net].back();
+        s->cache[net].pop_back();
+        return l;
+    }
+    const size_t need = s->lease_bytes[net];
+    for (size_t other = 0; other < s->cache.size() && s->held + need > s->budget; ++other) {
+        while (!s->cache[other].empty() && s->held + need > s->budget) {
+            Lease* l = s->cache[other].back();
+            s->cache[other].pop_back();
+            cudaFreeAsync(l->ws, st);
+            s->held -= l->bytes;
+            s->stats.evictions++;
+            delete l;
+        }
+    }
+    if (s->held + need > s->budget) return nullptr;
+    char* p = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&p), need, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    // zero once: the planes' borders must be zero and are never written
+    if (cudaMemsetAsync(p, 0, need, st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(p, st);
+        return nullptr;
+    }
+    s->held += need;
+    s->stats.workspace_bytes = s->held;
+    s->stats.peak_workspace_bytes = std::max(s->stats.peak_workspace_bytes, s->held);
+    Lease* l = new Lease{net, p, need};
+    return l;
+}
+
+void finish_slot(deepinv_server* s, Slot& sl, int status)
+{
+    const auto now = Clock::now();
+    const int N = net_N(s->nets[sl.net]);
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        Req& r = sl.reqs[i];
+        if (status == DEEPINV_OK) std::memcpy(r.xhat, sl.x_pin + i * (size_t)N, (size_t)N * sizeof(float));
+        deepinv_result res{};
+        res.tag = r.tag;
+        res.status = status;
+        res.net_id = r.net;
+        res.batch = (int)sl.reqs.size();
+        res.queue_us = us_between(r.t_submit, sl.t_launch);
+        res.latency_us = us_between(r.t_submit, Clock::now());
+        s->done.push_back(res);
+        if (status == DEEPINV_OK) s->stats.completed++;
+        else s->stats.failed++;
+        s->outstanding--;
+    }
+    (void)now;
+    sl.reqs.clear();
+    s->cache[sl.net].push_back(sl.lease);
+    sl.lease = nullptr;
+    sl.busy = false;
+    sl.net = -1;
+}
+
+// Launch one batch of `net` on slot `sl` (lock held).
+int launch(deepinv_server* s, Slot& sl, int net, Lease* lease)
+{
+    deepinv_net* n = s->nets[net];
+    const int M = net_M(n), N = net_N(n);
+    std::deque<Req>& q = s->pending[net];
+    const int b = (int)std::min<size_t>(q.size(), (size_t)s->max_batch);
+    sl.reqs.clear();
+    for (int i = 0; i < b; ++i) {
+        sl.reqs.push_back(std::move(q.front()));
+        q.pop_front();
+        std::memcpy(sl.y_pin + (size_t)i * M, sl.reqs.back().y.data(), (size_t)M * sizeof(float));
+    }
+    sl.net = net;
+    sl.lease = lease;
+    sl.t_launch = Clock::now();
+    float *yd = nullptr, *xd = nullptr;
+    net_ws_staging(n, lease->ws, s->max_batch, &yd, &xd);
+    int rc = DEEPINV_OK;
+    if (cudaMemcpyAsync(yd, sl.y_pin, (size_t)b * M * sizeof(float), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
+        rc = DEEPINV_ECUDA;
+    if (rc == DEEPINV_OK) rc = net_forward_ws(n, lease->ws, s->max_batch, yd, b, xd, sl.st);
+    if (rc == DEEPINV_OK &&
+        cudaMemcpyAsync(sl.x_pin, xd, (size_t)b * N * sizeof(float), cudaMemcpyDeviceToHost, sl.st) != cudaSuccess)
+        rc = DEEPINV_ECUDA;
+    if (rc == DEEPINV_OK && cudaEventRecord(sl.ev, sl.st) != cudaSuccess) rc = DEEPINV_ECUDA;
+    if (rc != DEEPINV_OK) {
+        cudaGetLastError();
+        finish_slot(s, sl, rc);
+        return rc;
+    }
+    sl.busy = true;
+    s->stats.batches++;
+    int inflight = 0;
+    for (const Slot& o : s->slots) inflight += o.busy ? 1 : 0;
+    s->stats.max_in_flight = std::max(s->stats.max_in_flight, inflight);
+    return DEEPINV_OK;
+}
+
+void scheduler(deepinv_server* s)
+{
+    cudaSetDevice(s->dev);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        bool progressed = false, finished = false;
+        // 1. collect finished batches
+        for (Slot& sl : s->slots) {
+            if (!sl.busy) continue;
+            const cudaError_t e = cudaEventQuery(sl.ev);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) cudaGetLastError();
+            finish_slot(s, sl, e == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
+            progressed = finished = true;
+        }
+        if (finished) s->cv_done.notify_all();
+        // 2. start batches on free streams, oldest waiting network first
+        bool blocked = false;
+        for (Slot& sl : s->slots) {
+            if (sl.busy || blocked) continue;
+            int best = -1;
+            for (size_t k = 0; k < s->pending.size(); ++k)
+                if (!s->pending[k].empty() &&
+                    (best < 0 || s->pending[k].front().t_submit < s->pending[best].front().t_submit))
+                    best = (int)k;
+            if (best < 0) break;
+            if (s->lease_bytes[best] > s->budget) {
+                // can never fit: fail this network's waiting requests
+                while (!s->pending[best].empty()) {
+                    fail_request(s, s->pending[best].front(), DEEPINV_ENOMEM);
+                    s->pending[best].pop_front();
+                }
+                s->cv_done.notify_all();
+                progressed = true;
+                continue;
+            }
+            Lease* l = acquire(s, best, sl.st);
+            if (!l) {
+                if (!s->waiting_admission) s->stats.admission_waits++;
+                s->waiting_admission = true;
+                blocked = true;
+                continue;
+            }
+            s->waiting_admission = false;
+            launch(s, sl, best, l);
+            progressed = true;
+        }
+        bool any_busy = false, any_pending = false;
+        for (const Slot& sl : s->slots) any_busy |= sl.busy;
+        for (const auto& q : s->pending) any_pending |= !q.empty();
+        if (s->stop && !any_busy && !any_pending) break;
+        if (progressed) continue;
+        if (any_busy) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            lk.lock();
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        }
+    }
+    s->cv_done.notify_all();
+}
+
+int ensure_slots(deepinv_server* s)
+{
+    for (Slot& sl : s->slots) {
+        if (!sl.st) {
+            DI_CUDA(cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking));
+            DI_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
+        }
+        if (sl.y_pin) cudaFreeHost(sl.y_pin);
+        if (sl.x_pin) cudaFreeHost(sl.x_pin);
+        sl.y_pin = sl.x_pin = nullptr;
+        if (cudaMallocHost(&sl.y_pin, (size_t)s->max_batch * s->maxM * sizeof(float)) != cudaSuccess ||
+            cudaMallocHost(&sl.x_pin, (size_t)s->max_batch * s->maxN * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("serve: page-locked staging allocation failed");
+            return DEEPINV_ENOMEM;
+        }
+    }
+    return DEEPINV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int deepinv_serve_open(size_t hbm_budget_bytes, int max_streams, int max_batch, deepinv_server** out)
+{
+    DI_REQUIRE(out, "out is NULL");
+    DI_REQUIRE(max_streams >= 1 && max_streams <= 16, "max_streams %d not in 1..16", max_streams);
+    DI_REQUIRE(max_batch >= 1 && max_batch <= 1024, "max_batch %d not in 1..1024", max_batch);
+    deepinv_server* s = new (std::nothrow) deepinv_server();
+    DI_REQUIRE(s, "host allocation failed");
+    s->budget = hbm_budget_bytes;
+    s->max_streams = max_streams;
+    s->max_batch = max_batch;
+    s->slots.resize(max_streams);
+    *out = s;
+    return DEEPINV_OK;
+}
+
+int deepinv_serve_add_net(deepinv_server* s, deepinv_net* net, int* net_id)
+{
+    DI_REQUIRE(s && net && net_id, "null pointer");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->outstanding > 0) {
+        set_error("serve_add_net: requests are in flight");
+        return DEEPINV_EBUSY;
+    }
+    const int dev = net_device(net);
+    DI_REQUIRE(s->dev < 0 || s->dev == dev, "network on device %d, server on device %d", dev, s->dev);
+    s->dev = dev;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(dev);
+    s->nets.push_back(net);
+    s->lease_bytes.push_back(net_ws_bytes(net, s->max_batch));
+    s->pending.emplace_back();
+    s->cache.emplace_back();
+    s->maxM = std::max(s->maxM, net_M(net));
+    s->maxN = std::max(s->maxN, net_N(net));
+    int rc = ensure_slots(s);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (rc != DEEPINV_OK) {
+        s->nets.pop_back();
+        s->lease_bytes.pop_back();
+        s->pending.pop_back();
+        s->cache.pop_back();
+        return rc;
+    }
+    *net_id = (int)s->nets.size() - 1;
+    if (!s->started) {
+        s->started = true;
+        s->thr = std::thread(scheduler, s);
+    }
+    return DEEPINV_OK;
+}
+
+int deepinv_serve(deepinv_server* s, const deepinv_request* in, int n_in, deepinv_result* out, int max_out,
+                  int* n_out, int timeout_us)
+{
+    DI_REQUIRE(s && n_out, "null pointer");
+    DI_REQUIRE(n_in >= 0 && max_out >= 0 && timeout_us >= 0, "negative count or timeout");
+    DI_REQUIRE(n_in == 0 || in, "requests pointer is NULL");
+    DI_REQUIRE(max_out == 0 || out, "results pointer is NULL");
+    *n_out = 0;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (int i = 0; i < n_in; ++i) {
+        const deepinv_request& r = in[i];
+        DI_REQUIRE(r.net_id >= 0 && r.net_id < (int)s->nets.size(), "request %d: unknown net_id %d", i, r.net_id);
+        DI_REQUIRE(r.y && r.xhat, "request %d: null y or xhat", i);
+    }
+    const auto now = Clock::now();
+    for (int i = 0; i < n_in; ++i) {
+        const deepinv_request& r = in[i];
+        Req q;
+        q.net = r.net_id;
+        q.tag = r.tag;
+        q.xhat = r.xhat;
+        const int M = net_M(s->nets[r.net_id]);
+        q.y.assign(r.y, r.y + M);
+        q.t_submit = now;
+        s->pending[r.net_id].push_back(std::move(q));
+        s->stats.submitted++;
+        s->outstanding++;
+    }
+    if (n_in > 0) s->cv_work.notify_one();
+    if (max_out == 0) return DEEPINV_OK;
+    if (s->done.empty() && timeout_us > 0 && s->outstanding > 0)
+        s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [s] { return !s->done.empty(); });
+    int n = 0;
+    while (n < max_out && !s->done.empty()) {
+        out[n++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n_out = n;
+    if (n == 0 && timeout_us > 0 && s->outstanding > 0) {
+        set_error("serve: no request finished within %d us", timeout_us);
+        return DEEPINV_ETIMEOUT;
+    }
+    return DEEPINV_OK;
+}
+
+int deepinv_serve_get_stats(deepinv_server* s, deepinv_serve_stats* st)
+{
+    DI_REQUIRE(s && st, "null pointer");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *st = s->stats;
+    st->workspace_bytes = s->held;
+    return DEEPINV_OK;
+}
+
+int deepinv_serve_close(deepinv_server* s)
+{
+    if (!s) return DEEPINV_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->thr.joinable()) s->thr.join();
+    if (s->dev >= 0) cudaSetDevice(s->dev);
+    for (Slot& sl : s->slots) {
+        if (sl.st) cudaStreamSynchronize(sl.st);
+    }
+    cudaStream_t fs = s->slots.empty() ? nullptr : s->slots[0].st;
+    for (auto& c : s->cache)
+        for (Lease* l : c) {
+            cudaFreeAsync(l->ws, fs);
+            delete l;
+        }
+    for (Slot& sl : s->slots) {
+        if (sl.lease) {
+            cudaFreeAsync(sl.lease->ws, fs);
+            delete sl.lease;
+        }
+    }
+    if (fs) cudaStreamSynchronize(fs);
+    for (Slot& sl : s->slots) {
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+        if (sl.y_pin) cudaFreeHost(sl.y_pin);
+        if (sl.x_pin) cudaFreeHost(sl.x_pin);
+    }
+    delete s;
+    return DEEPINV_OK;
+}
+
+}  // extern "C"

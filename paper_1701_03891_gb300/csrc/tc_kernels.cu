@@ -11,6 +11,8 @@
 //
 // All operands are K-major without swizzle (see tc.cuh), moved by the TMA
 // engine with 1-D bulk copies; accumulators live in TMEM.
+#include <cstdlib>
+
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -371,9 +373,15 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
 // them has been multiplied) and the weights ((dy, s) blocks of 16 KB through a
 // ring); warp 1 owns TMEM (2 accumulators x 256 columns) and issues MMAs;
 // warps 2..5 drain the accumulator of the previous tile.
+//
+// Wide images (the window of 10 P + 264 positions does not fit in shared
+// memory) use row mode: the producer streams, for every kernel row dy, just
+// the 264 positions that row's MMAs read, through a ring of kRowSlots pieces.
 constexpr int kW2Stages = 4;
 constexpr int kMaxSlabs = 10;
 
+constexpr int kPiecePx = 8 + kConv2N;  // positions one kernel row's MMAs read (row mode)
+constexpr int kRowSlots = 4;           // row-mode ring of input pieces
 constexpr int kXStride = 36;          // floats per row of the slot exchange (32 + 4 pad)
 constexpr int kXBytes = 4 * 32 * kXStride * 4;
 
@@ -404,6 +412,7 @@ __host__ __device__ inline int conv2_dylast(int j, int P)
     return d < 10 ? d : 10;
 }
 
+template <bool ROWS>
 __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ a1, int B, int H, int W, int P,
                                                        int plane_len, int t2, int nslab,
                                                        const bf16* __restrict__ w2p,
@@ -411,10 +420,11 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                                                        int* status)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    const int win_px = nslab * kSlabPx;
-    const uint32_t CH = (uint32_t)win_px * 16;     // bytes per 8-channel chunk plane of the window
-    uint8_t* sWin = smem_raw;                       // [8][win_px][8] bf16
-    uint8_t* sW = smem_raw + 8 * CH;                // [kW2Stages][16 KB]
+    // window mode: [8][nslab * 128][8] bf16; row mode: [nslab pieces][8][kPiecePx][8] bf16
+    const uint32_t CH = ROWS ? (uint32_t)kPiecePx * 16 : (uint32_t)nslab * kSlabPx * 16;
+    const uint32_t win_bytes = ROWS ? (uint32_t)nslab * 8 * CH : 8 * CH;
+    uint8_t* sWin = smem_raw;
+    uint8_t* sW = smem_raw + win_bytes;             // [kW2Stages][16 KB]
     float* sX = reinterpret_cast<float*>(sW + kW2Stages * 16384);   // [4 slots][32 filters][kXStride]
     Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * 16384 + kXBytes);
 
@@ -454,14 +464,25 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
         int w_parity[kW2Stages];
         for (int j = 0; j < kMaxSlabs; ++j) slab_parity[j] = -1;
         for (int s = 0; s < kW2Stages; ++s) w_parity[s] = -1;
-        int it = 0, wst = 0;
+        int it = 0, wst = 0, pc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
             const uint8_t* src_img = reinterpret_cast<const uint8_t*>(a1) + (size_t)b * 8 * plane_len * 16;
             int next_slab = 0;
             for (int dy = 0; dy < 11 && ok; ++dy) {
-                const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                if (ROWS) {
+                    const int slot = pc % nslab, n = pc / nslab;
+                    ++pc;
+                    if (!mbar_wait(smem_u32(&ss->empty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
+                    mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), 8 * kPiecePx * 16);
+                    slab_parity[slot] = n & 1;
+                    for (int c = 0; c < 8; ++c)
+                        bulk_g2s(smem_u32(sWin + (slot * 8 + c) * CH),
+                                 src_img + ((size_t)c * plane_len + q0 + dy * P) * 16, kPiecePx * 16,
+                                 smem_u32(&ss->full[slot]));
+                }
+                const int last = ROWS ? -1 : (dy * P + 8 + kConv2N - 1) / kSlabPx;
                 while (next_slab <= last) {
                     const int j = next_slab++;
                     if (!mbar_wait(smem_u32(&ss->empty[j]), (it & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
@@ -490,7 +511,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
         const uint32_t idesc = idesc_bf16(128, kConv2N);
-        int it = 0, wst = 0;
+        int it = 0, wst = 0, pc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
             const int buf = it & 1, use = it >> 1;
@@ -499,28 +520,42 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
             const uint32_t d = tbase + (uint32_t)buf * kConv2N;
             int next_wait = 0, next_free = 0;
             for (int dy = 0; dy < 11 && ok; ++dy) {
-                const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
-                while (next_wait <= last) {
-                    if (!mbar_wait(smem_u32(&ss->full[next_wait]), it & 1, status, &ss->abort_flag)) { ok = false; break; }
-                    ++next_wait;
+                int slot = 0;
+                uint32_t bbase, off;
+                if (ROWS) {
+                    slot = pc % nslab;
+                    const int n = pc / nslab;
+                    ++pc;
+                    if (!mbar_wait(smem_u32(&ss->full[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
+                    bbase = smem_u32(sWin + slot * 8 * CH);
+                    off = 0;
+                } else {
+                    const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                    while (next_wait <= last) {
+                        if (!mbar_wait(smem_u32(&ss->full[next_wait]), it & 1, status, &ss->abort_flag)) { ok = false; break; }
+                        ++next_wait;
+                    }
+                    bbase = smem_u32(sWin);
+                    off = (uint32_t)(dy * P) * 16;
                 }
                 if (!ok) break;
                 tc_fence_after();
                 for (int s = 0; s < 3; ++s, ++wst) {
-                    const int slot = wst % kW2Stages, n = wst / kW2Stages;
-                    if (!mbar_wait(smem_u32(&ss->wfull[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
+                    const int wslot = wst % kW2Stages, n = wst / kW2Stages;
+                    if (!mbar_wait(smem_u32(&ss->wfull[wslot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t off = (uint32_t)(dy * P + 4 * s) * 16;
+                    const uint32_t boff = off + (uint32_t)(4 * s) * 16;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = sdesc(smem_u32(sW + slot * 16384 + kk * 4096), 2048, 128);
-                        const uint64_t bd = sdesc(smem_u32(sWin + (2 * kk) * CH) + off, CH, 128);
+                        const uint64_t ad = sdesc(smem_u32(sW + wslot * 16384 + kk * 4096), 2048, 128);
+                        const uint64_t bd = sdesc(bbase + (2 * kk) * CH + boff, CH, 128);
                         mma_bf16(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
                     }
-                    mma_commit(smem_u32(&ss->wempty[slot]));
+                    mma_commit(smem_u32(&ss->wempty[wslot]));
                 }
                 if (!ok) break;
-                while (next_free < nslab && conv2_dylast(next_free, P) == dy) {
+                if (ROWS) mma_commit(smem_u32(&ss->empty[slot]));
+                while (!ROWS && next_free < nslab && conv2_dylast(next_free, P) == dy) {
                     mma_commit(smem_u32(&ss->empty[next_free]));
                     ++next_free;
                 }
@@ -786,14 +821,27 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
     return DEEPINV_OK;
 }
 
-static size_t conv2_smem_bytes(const Geo& g)
+static size_t conv2_smem_bytes(const Geo& g, bool rows)
 {
-    return (size_t)8 * g.nslab * kSlabPx * 16 + (size_t)kW2Stages * 16384 + kXBytes + sizeof(Conv2Smem);
+    const size_t win = rows ? (size_t)kRowSlots * 8 * kPiecePx * 16 : (size_t)8 * g.nslab * kSlabPx * 16;
+    return win + (size_t)kW2Stages * 16384 + kXBytes + sizeof(Conv2Smem);
+}
+
+// Window mode when the whole input window of a tile fits in shared memory.
+// DEEPINV_CONV2_FORCE_ROWS=1 in the environment selects row mode everywhere
+// (both modes give bit-identical results; the tests compare them).
+static bool conv2_window_mode(const Geo& g)
+{
+    static const bool force_rows = [] {
+        const char* e = getenv("DEEPINV_CONV2_FORCE_ROWS");
+        return e && e[0] == '1';
+    }();
+    return !force_rows && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false) <= 227 * 1024;
 }
 
 bool conv2_tc_supported(const Geo& g)
 {
-    return g.nslab <= kMaxSlabs && conv2_smem_bytes(g) <= 227 * 1024;
+    return conv2_window_mode(g) || conv2_smem_bytes(g, true) <= 227 * 1024;
 }
 
 int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* b2, bf16* a2, int num_sms,
@@ -801,14 +849,22 @@ int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* 
 {
     if (B <= 0) return DEEPINV_OK;
     if (!conv2_tc_supported(g)) {
-        set_error("conv2_tc: image width %d needs %d window slabs (max %d)", g.W, g.nslab, kMaxSlabs);
+        set_error("conv2_tc: no kernel configuration for image width %d", g.W);
         return DEEPINV_EUNSUPPORTED;
     }
-    const size_t smem = conv2_smem_bytes(g);
-    DI_CUDA(cudaFuncSetAttribute(conv2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const bool rows = !conv2_window_mode(g);
+    const size_t smem = conv2_smem_bytes(g, rows);
     const int ntiles = B * g.t2;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
-    conv2_kernel<<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, g.nslab, w2p, b2, a2, status);
+    if (rows) {
+        DI_CUDA(cudaFuncSetAttribute(conv2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        conv2_kernel<true><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, kRowSlots, w2p, b2, a2,
+                                                    status);
+    } else {
+        DI_CUDA(cudaFuncSetAttribute(conv2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        conv2_kernel<false><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, g.nslab, w2p, b2, a2,
+                                                     status);
+    }
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

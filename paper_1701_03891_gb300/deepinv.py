@@ -33,6 +33,23 @@ class DeepInvError(RuntimeError):
         self.status = status
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("net_id", ctypes.c_int), ("y", ctypes.c_void_p), ("xhat", ctypes.c_void_p),
+                ("tag", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("net_id", ctypes.c_int),
+                ("batch", ctypes.c_int), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_in_flight", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t), ("peak_workspace_bytes", ctypes.c_size_t),
+                ("evictions", ctypes.c_uint64), ("admission_waits", ctypes.c_uint64)]
+
+
 class NetDesc(ctypes.Structure):
     _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("M", ctypes.c_int),
                 ("l1", ctypes.c_int), ("l2", ctypes.c_int), ("l3", ctypes.c_int),
@@ -66,6 +83,11 @@ SIGNATURES = {
     "deepinv_backward": (_I, [_P, _P, _P, _I, _P, _PP, _PP, _P, _P, _P]),
     "deepinv_sgd_momentum": (_I, [_P, _PP, _PP, _P, ctypes.c_float, ctypes.c_float, _P]),
     "deepinv_get_params": (_I, [_P, _PP, _PP, _P, _P]),
+    "deepinv_serve_open": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
+    "deepinv_serve_add_net": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "deepinv_serve": (_I, [_P, ctypes.POINTER(Request), _I, ctypes.POINTER(Result), _I, ctypes.POINTER(_I), _I]),
+    "deepinv_serve_get_stats": (_I, [_P, ctypes.POINTER(ServeStats)]),
+    "deepinv_serve_close": (_I, [_P]),
     "deepinv_profile_enable": (_I, [_P, _I]),
     "deepinv_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
 }
@@ -330,3 +352,49 @@ def mse_loss(net: Net, y, x, params):
     if _autograd_cls is None:
         _autograd_cls = _make_autograd()
     return _autograd_cls.apply(net, y, x, *params)
+
+
+class Server:
+    """Continuous-batching recovery server (deepinv_serve_*): host y in, host x^ out."""
+
+    def __init__(self, hbm_budget_bytes: int, max_streams: int = 4, max_batch: int = 64):
+        self._h = ctypes.c_void_p()
+        _check(lib().deepinv_serve_open(int(hbm_budget_bytes), max_streams, max_batch, ctypes.byref(self._h)))
+        self.nets = []
+
+    def add(self, net: "Net") -> int:
+        nid = ctypes.c_int()
+        _check(lib().deepinv_serve_add_net(self._h, net.handle, ctypes.byref(nid)))
+        self.nets.append(net)
+        return nid.value
+
+    def serve(self, requests=(), max_out: int = 4096, timeout_us: int = 0):
+        """Submit [(net_id, y_host_array, xhat_host_array, tag), ...] and harvest finished results.
+        Returns (status, [Result, ...])."""
+        n_in = len(requests)
+        arr = (Request * max(1, n_in))()
+        for i, (nid, y, xh, tag) in enumerate(requests):
+            arr[i] = Request(nid, y.ctypes.data if hasattr(y, "ctypes") else y.data_ptr(),
+                             xh.ctypes.data if hasattr(xh, "ctypes") else xh.data_ptr(), tag)
+        out = (Result * max(1, max_out))()
+        n_out = ctypes.c_int()
+        rc = lib().deepinv_serve(self._h, arr, n_in, out, max_out, ctypes.byref(n_out), timeout_us)
+        if rc not in (OK, ETIMEOUT):
+            _check(rc)
+        return rc, [out[i] for i in range(n_out.value)]
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(lib().deepinv_serve_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().deepinv_serve_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

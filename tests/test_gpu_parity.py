@@ -93,6 +93,43 @@ def test_forward(di, prec, n1, n2, ratio, B):
     net.close()
 
 
+@pytest.mark.parametrize("n1,n2,ratio,B", [
+    (128, 128, 0.05, 2),    # wide images: conv2 streams per-kernel-row pieces
+    (90, 100, 0.10, 2),
+    (256, 256, 0.01, 1),
+])
+def test_forward_bf16_wide(di, n1, n2, ratio, B):
+    phi, params, x = _case(n1, n2, ratio, B)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
+    y = net.measure(_cuda(x))
+    xhat = net.forward(y).cpu().numpy()
+    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
+    assert np.all(np.isfinite(xhat))
+    assert _maxrel(xhat, ref) <= TOL["bf16"]
+
+
+def test_conv2_row_mode_matches_window_mode(di):
+    """Both conv2 pipelines (window slabs vs per-row pieces) give identical bits."""
+    import subprocess, sys, os, json
+    code = (
+        "import numpy as np, torch, sys; sys.path.insert(0, %r);"
+        "from paper_1701_03891_gb300 import deepinv, synth;"
+        "phi = synth.gaussian_phi(410, 4096, 0); p = synth.he_params(seed=1, bias_std=0.01);"
+        "x = synth.voronoi_images(8, 64, 64, seed=5);"
+        "net = deepinv.Net(phi, p, 64, 64, prec='bf16');"
+        "y = net.measure(torch.from_numpy(x).cuda()); out = net.forward(y).cpu().numpy();"
+        "np.save(sys.argv[1], out)" % os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import tempfile
+    outs = []
+    for force in ("0", "1"):
+        f = tempfile.mktemp(suffix=".npy")
+        env = dict(os.environ, DEEPINV_CONV2_FORCE_ROWS=force)
+        subprocess.check_call([sys.executable, "-c", code, f], env=env)
+        outs.append(np.load(f))
+        os.unlink(f)
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 def test_forward_final_relu(di, prec):
     phi, params, x = _case(32, 32, 0.1, 3)
