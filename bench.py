@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rates", default="20000,80000,200000",
+                    help="offered request rates (requests/s) of the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window per rate")
     return ap.parse_args()
 
 
@@ -169,6 +173,84 @@ def traffic_record():
     except Exception:
         pass
     return None
+
+
+SERVE_SIZES = (32, 64, 128)
+SERVE_RATIOS = (0.05, 0.10, 0.25)
+
+
+def serving_bench(args):
+    """Mixed-size serving: 9 resident bf16 networks (32/64/128 squared x M/N 0.05/0.10/0.25),
+    Poisson arrivals (seed 4) of single recoveries drawn uniformly over the 9 classes,
+    a continuous-batching server (4 streams, batches <= 64, 40 GB budget); per offered
+    rate: latency p50/p99 (scheduled arrival -> result in host memory) and images/s."""
+    import ctypes
+    import numpy as np
+    from paper_1701_03891_gb300 import deepinv, synth
+    nets, pools = [], []
+    for si, n in enumerate(SERVE_SIZES):
+        N = n * n
+        for ri, r in enumerate(SERVE_RATIOS):
+            M = synth.m_for_ratio(r, N)
+            phi = synth.gaussian_phi(M, N, seed=100 + 3 * si + ri)
+            net = deepinv.Net(phi, synth.he_params(seed=1), n, n, prec="bf16")
+            x = synth.voronoi_images(16, n, n, seed=200 + 3 * si + ri)
+            y = (x.astype(np.float64) @ phi.astype(np.float64).T).astype(np.float32)
+            nets.append(net)
+            pools.append((np.ascontiguousarray(y), N))
+    srv = deepinv.Server(hbm_budget_bytes=40 << 30, max_streams=4, max_batch=64)
+    for net in nets:
+        srv.add(net)
+    rng = np.random.default_rng(4)
+    points = []
+    for rate in [float(v) for v in args.serve_rates.split(",") if v]:
+        n_req = int(min(100000, max(500, rate * args.serve_seconds)))
+        cls = rng.integers(0, len(nets), n_req)
+        arrive = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        # results land in a ring of 64 host buffers per class (values are not checked here)
+        ring = [np.empty((64, pools[c][1]), np.float32) for c in range(len(nets))]
+        reqs = (deepinv.Request * n_req)()
+        for i, c in enumerate(cls):
+            y, _ = pools[c]
+            reqs[i] = deepinv.Request(int(c), y[i % y.shape[0]].ctypes.data, ring[c][i % 64].ctypes.data, i)
+        res = (deepinv.Result * 4096)()
+        lag = np.zeros(n_req)
+        lat = np.zeros(n_req)
+        batch = np.zeros(n_req)
+        done = 0
+        sent = 0
+        t0 = time.perf_counter()
+        while done < n_req:
+            now = time.perf_counter() - t0
+            k = int(np.searchsorted(arrive, now, side="right")) - sent
+            if k > 0:
+                lag[sent:sent + k] = now - arrive[sent:sent + k]
+            rc, n_out = srv.serve_raw(reqs, sent, max(0, k), res, 4096, 0)
+            sent += max(0, k)
+            for j in range(n_out):
+                r = res[j]
+                lat[r.tag] = r.latency_us * 1e-6
+                batch[r.tag] = r.batch
+            done += n_out
+            if n_out == 0 and sent == n_req:
+                time.sleep(20e-6)
+        t_end = time.perf_counter() - t0
+        total = lat + lag
+        points.append({"offered_rps": rate, "requests": n_req,
+                       "images_per_s": n_req / t_end,
+                       "p50_ms": float(np.percentile(total, 50) * 1e3),
+                       "p99_ms": float(np.percentile(total, 99) * 1e3),
+                       "mean_batch": float(batch.mean())})
+    st = srv.stats()
+    srv.close()
+    for net in nets:
+        net.close()
+    return {"workload": "9 bf16 networks: %s x M/N %s; Poisson arrivals, uniform over classes; "
+                        "4 streams, batches <= 64, 40 GB budget" % ("/".join("%d^2" % n for n in SERVE_SIZES),
+                                                                   "/".join(str(r) for r in SERVE_RATIOS)),
+            "latency": "scheduled arrival -> result in the request's host buffer",
+            "points": points, "max_in_flight": st["max_in_flight"],
+            "peak_workspace_gb": st["peak_workspace_bytes"] / 2**30}
 
 
 def run_reference(args):
@@ -316,6 +398,10 @@ def run_native(args):
            "h2d_bytes_per_step": B * N * 4, "d2h_bytes_per_step": B * N * 4,
            "call": "deepinv_sense_recover_host (pinned x in, pinned x^ out, synchronous)"}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, phi, params, x, n, gpu_xhat=bf16_out)
@@ -330,7 +416,7 @@ def run_native(args):
             "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "serving": serving, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -383,6 +383,16 @@ class Server:
             _check(rc)
         return rc, [out[i] for i in range(n_out.value)]
 
+    def serve_raw(self, reqs, offset: int, count: int, results, max_out: int, timeout_us: int = 0):
+        """Low-overhead form: ``reqs`` and ``results`` are preallocated ctypes arrays of
+        Request / Result; submits reqs[offset:offset+count]; returns (rc, n_out)."""
+        n_out = ctypes.c_int()
+        base = ctypes.cast(ctypes.byref(reqs, offset * ctypes.sizeof(Request)), ctypes.POINTER(Request))
+        rc = lib().deepinv_serve(self._h, base, count, results, max_out, ctypes.byref(n_out), timeout_us)
+        if rc not in (OK, ETIMEOUT):
+            _check(rc)
+        return rc, n_out.value
+
     def stats(self) -> dict:
         st = ServeStats()
         _check(lib().deepinv_serve_get_stats(self._h, ctypes.byref(st)))
