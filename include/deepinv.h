@@ -25,7 +25,10 @@
  *  - Precision: DEEPINV_F32 runs every product in float32 on CUDA cores;
  *    DEEPINV_BF16 runs the FC layer and the convolutions on the tcgen05 tensor
  *    cores with bfloat16 operands (round to nearest even) and float32
- *    accumulation.
+ *    accumulation; DEEPINV_FP8_E4M3 is the bf16 path with conv2 (95 % of the
+ *    flops) on e4m3 operands: weights scaled per filter (max |w| -> 448), the
+ *    conv1 output scaled by one static factor found by deepinv_net_calibrate,
+ *    float32 accumulation; it is inference only.
  */
 #ifndef DEEPINV_H
 #define DEEPINV_H
@@ -49,7 +52,8 @@ typedef enum {
 
 typedef enum {
     DEEPINV_F32 = 0,
-    DEEPINV_BF16 = 1
+    DEEPINV_BF16 = 1,
+    DEEPINV_FP8_E4M3 = 2   /* bf16 path with conv2 in e4m3 (see deepinv_net_calibrate) */
 } deepinv_precision;
 
 /* Network shape (Sec. 4 and Sec. 5).  The paper's network is
@@ -119,6 +123,14 @@ int deepinv_measure_noalloc(const float* phi, int M, int N, const float* x, int 
 int deepinv_net_create(const deepinv_net_desc* desc, const float* phi,
                        const float* const w[3], const float* const b[3],
                        void* stream, deepinv_net** out);
+
+/* Fix the activation scale of a DEEPINV_FP8_E4M3 network: run the FC layer
+ * and conv1 on the calibration batch y [B][M] (device float32) and map the
+ * largest conv1 output to the largest finite e4m3 value (448); later values
+ * above it saturate.  Required once before the first forward pass of such a
+ * network (weight updates keep it).  Synchronises `stream`.  A no-op for the
+ * other precisions. */
+int deepinv_net_calibrate(deepinv_net* net, const float* y, int B, void* stream);
 
 /* Free everything the network owns.  Synchronises the device.  NULL is a no-op. */
 int deepinv_net_destroy(deepinv_net* net);

@@ -71,7 +71,8 @@ struct deepinv_net {
     int N = 0;
     int num_sms = 1;
     Geo geo{};
-    bool tc = false;   // bf16 tensor-core path
+    bool tc = false;   // tensor-core path (bf16, or e4m3 conv2)
+    bool fp8 = false;  // conv2 in e4m3
     // float32 masters
     float* phi = nullptr;
     float* w[3] = {nullptr, nullptr, nullptr};
@@ -88,6 +89,14 @@ struct deepinv_net {
     bf16* w1p = nullptr;
     bf16* w2p = nullptr;
     bf16* w3p = nullptr;
+    // e4m3 conv2: weights, per-filter scales, calibrated activation scale
+    uint8_t* w2q = nullptr;
+    float* sw = nullptr;        // [32] weight scales
+    float* oscale = nullptr;    // [32] sw * sa
+    float* inv_sa = nullptr;    // 1 / sa
+    float* amax_a1 = nullptr;   // calibrated max of a1
+    float* amax_w = nullptr;    // [32] scratch
+    bool calibrated = false;
     // forward workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -272,8 +281,9 @@ int check_desc(const deepinv_net_desc* d)
     DI_REQUIRE(d->l1 >= 1 && d->l2 >= 1 && d->l3 == 1, "filters (%d, %d, %d): need l1, l2 >= 1, l3 = 1",
                d->l1, d->l2, d->l3);
     DI_REQUIRE(d->k >= 1 && d->k <= 15 && d->k % 2 == 1, "kernel size %d must be odd and <= 15", d->k);
-    DI_REQUIRE(d->prec == DEEPINV_F32 || d->prec == DEEPINV_BF16, "unknown precision %d", d->prec);
-    if (d->prec == DEEPINV_BF16) {
+    DI_REQUIRE(d->prec == DEEPINV_F32 || d->prec == DEEPINV_BF16 || d->prec == DEEPINV_FP8_E4M3,
+               "unknown precision %d", d->prec);
+    if (d->prec != DEEPINV_F32) {
         if (d->l1 != 64 || d->l2 != 32 || d->k != 11) {
             set_error("bf16 path is built for the paper network (64, 32, 1 filters of 11 x 11)");
             return DEEPINV_EUNSUPPORTED;
@@ -291,6 +301,10 @@ int repack(deepinv_net* n, cudaStream_t st)
     if (!n->tc) return DEEPINV_OK;
     const int N = n->N, M = n->d.M;
     DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[2], n->w1p, n->w2p, n->w3p, st));
+    if (n->fp8) {
+        DI_TRY(pack_w2_e4m3(n->w[1], n->amax_w, n->w2q, n->sw, st));
+        if (n->calibrated) DI_TRY(e4m3_scales(n->amax_a1, n->sw, n->inv_sa, n->oscale, st));
+    }
     // FC operand (rows = pixel j, K = measurement i): Phi^T or the trained copy.
     if (n->wfc) DI_TRY(pack_kmajor(n->wfc, M, 1, N, M, 128, n->Kfc, n->fcA, st));
     else DI_TRY(pack_kmajor(n->phi, 1, N, N, M, 128, n->Kfc, n->fcA, st));
@@ -314,6 +328,8 @@ void free_net(deepinv_net* n)
     cudaFree(n->w1p);
     cudaFree(n->w2p);
     cudaFree(n->w3p);
+    cudaFree(n->w2q);
+    cudaFree(n->sw);
     cudaFree(n->ws);
     cudaFree(n->bws);
     for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
@@ -354,6 +370,14 @@ int measure_bf16_packed(const bf16* phiB, int Kp, int NB, const float* x, int N,
 // The forward pass in a given workspace `w` (carved for at least B images).
 int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* xhat, void* saved, cudaStream_t st)
 {
+    if (n->fp8 && !n->calibrated) {
+        set_error("e4m3 network: call deepinv_net_calibrate before the first forward pass");
+        return DEEPINV_EINVAL;
+    }
+    if (n->fp8 && saved) {
+        set_error("e4m3 networks are inference only (train in bf16 or f32)");
+        return DEEPINV_EUNSUPPORTED;
+    }
     const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2, k = n->d.k;
     Saved sv{};
     if (saved) {
@@ -375,11 +399,13 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
         }
         {
             StageTimer t(n, st, DEEPINV_STAGE_CONV1);
-            DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, status, st));
+            DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, n->fp8 ? kConv1OutE4M3 : kConv1OutBF16, n->inv_sa,
+                            nullptr, status, st));
         }
         {
             StageTimer t(n, st, DEEPINV_STAGE_CONV2);
-            DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], a2, n->num_sms, status, st));
+            if (n->fp8) DI_TRY(conv2_tc(a1, B, g, n->w2q, n->b[1], n->oscale, true, a2, n->num_sms, status, st));
+            else DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], nullptr, false, a2, n->num_sms, status, st));
         }
         {
             StageTimer t(n, st, DEEPINV_STAGE_CONV3);
@@ -539,7 +565,8 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
     n->d = *desc;
     n->dev = dev;
     n->N = desc->n1 * desc->n2;
-    n->tc = desc->prec == DEEPINV_BF16;
+    n->tc = desc->prec != DEEPINV_F32;
+    n->fp8 = desc->prec == DEEPINV_FP8_E4M3;
     n->num_sms = num_sms_current();
     const int N = n->N, M = desc->M;
     int rc = DEEPINV_OK;
@@ -574,6 +601,14 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
         DI_STEP(dev_alloc(&n->w1p, kW1PackElems));
         DI_STEP(dev_alloc(&n->w2p, kW2PackElems));
         DI_STEP(dev_alloc(&n->w3p, kW3PackElems));
+        if (n->fp8) {
+            DI_STEP(dev_alloc(&n->w2q, kW2E4M3Bytes));
+            DI_STEP(dev_alloc(&n->sw, 32 * 4 + 1 + 1 + 32));   // sw | oscale | inv_sa | amax_a1 | amax_w
+            n->oscale = n->sw + 32;
+            n->inv_sa = n->sw + 64;
+            n->amax_a1 = n->sw + 65;
+            n->amax_w = n->sw + 66;
+        }
         DI_STEP(pack_kmajor(n->phi, N, 1, M, N, n->NBms, n->Kms, n->msB, st));
     }
     if (desc->train_fc) DI_STEP(transpose_f32(n->phi, M, N, n->wfc, st));
@@ -677,6 +712,10 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
     DI_REQUIRE(y && x && saved && dW && db && loss, "null pointer");
     for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
+    if (net->fp8) {
+        set_error("e4m3 networks are inference only (train in bf16 or f32)");
+        return DEEPINV_EUNSUPPORTED;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
     const int l1 = net->d.l1, l2 = net->d.l2;
@@ -814,6 +853,30 @@ int deepinv_profile_read(deepinv_net* net, float stage_ms[DEEPINV_NSTAGES], int 
         if (stage_ms) stage_ms[s] = ms[s];
         if (stage_count) stage_count[s] = cnt[s];
     }
+    return DEEPINV_OK;
+}
+
+int deepinv_net_calibrate(deepinv_net* net, const float* y, int B, void* stream)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
+    DI_REQUIRE(B >= 1 && y, "calibration needs a batch (B >= 1) of measurements");
+    if (!net->fp8) return DEEPINV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DI_TRY(ensure_ws(net, B, st));
+    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
+    const Geo& g = net->geo;
+    int* status = device_status_word();
+    DI_REQUIRE(status, "no device status word");
+    const int N = net->N, M = net->d.M;
+    const int nb = fc_nb(B);
+    DI_TRY(pack_kmajor(y, M, 1, B, M, nb, net->Kfc, w.ypk, st));
+    DI_TRY(tc_gemm(net->fcA, w.ypk, net->Kfc, N, B, nb, GEMM_OUT_PLANE, nullptr, 0, w.xt, g, status, st));
+    DI_CUDA(cudaMemsetAsync(net->amax_a1, 0, sizeof(float), st));
+    DI_TRY(conv1_tc(w.xt, B, g, net->w1p, net->b[0], nullptr, kConv1AmaxOnly, nullptr, net->amax_a1, status, st));
+    DI_TRY(e4m3_scales(net->amax_a1, net->sw, net->inv_sa, net->oscale, st));
+    DI_CUDA(cudaStreamSynchronize(st));
+    net->calibrated = true;
     return DEEPINV_OK;
 }
 

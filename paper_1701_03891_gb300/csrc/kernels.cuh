@@ -52,12 +52,21 @@ enum GemmOut { GEMM_OUT_F32 = 0, GEMM_OUT_PLANE = 1 };
 int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mode, float* out_f32,
             long long ldo, bf16* plane, const Geo& geo, int* status, cudaStream_t st);
 
-// conv1: x~ plane [B][plane] -> a1 [B][8][plane][8] (bias, ReLU, zero pad columns).
-int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, bf16* a1,
-             int* status, cudaStream_t st);
-// conv2: a1 -> a2 [B][4][plane][8] (bias, ReLU, zero pad columns).
-int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* b2, bf16* a2,
-             int num_sms, int* status, cudaStream_t st);
+// conv1: x~ plane [B][plane] -> a1 (bias, ReLU, zero pad columns), as
+//   kConv1OutBF16: bf16 [B][8][plane][8];
+//   kConv1OutE4M3: e4m3 [B][4][plane][16], values times *inv_sa;
+//   kConv1AmaxOnly: no output, atomically raises *amax to the largest a1 value.
+enum { kConv1OutBF16 = 0, kConv1OutE4M3 = 1, kConv1AmaxOnly = 2 };
+int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
+             const float* inv_sa, float* amax, int* status, cudaStream_t st);
+// conv2: a1 (bf16, or e4m3 when fp8) -> a2 bf16 [B][4][plane][8] (bias, ReLU,
+// zero pad columns); the e4m3 path multiplies the accumulators by oscale[co].
+int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
+             bool fp8, bf16* a2, int num_sms, int* status, cudaStream_t st);
+// e4m3 conv2 weights: [dy][s][kk][2][128][16] bytes with per-filter scales sw[32].
+constexpr size_t kW2E4M3Bytes = 11 * 3 * 2 * 2 * 128 * 16;
+int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st);
+int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* oscale, cudaStream_t st);
 bool conv2_tc_supported(const Geo& g);
 // conv3: a2 -> row partial sums T [B][11][t3 * 128] -> xhat [B][n1 * n2] float32.
 size_t conv3_scratch_elems(const Geo& g, int B);

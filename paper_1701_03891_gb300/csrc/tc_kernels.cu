@@ -13,6 +13,8 @@
 // engine with 1-D bulk copies; accumulators live in TMEM.
 #include <cstdlib>
 
+#include <cuda_fp8.h>
+
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -30,6 +32,22 @@ __device__ __forceinline__ uint4 pack8_bf16(const float* v)
     for (int i = 0; i < 4; ++i) {
         __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
         u[i] = *reinterpret_cast<uint32_t*>(&p);
+    }
+    return r;
+}
+
+// 16 floats scaled by `scale` -> 16 e4m3 bytes (round to nearest, saturating to +-448).
+__device__ __forceinline__ uint4 pack16_e4m3(const float* v, float scale)
+{
+    uint4 r;
+    uint32_t* u = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i] * scale, v[4 * i + 1] * scale),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i + 2] * scale, v[4 * i + 3] * scale),
+                                                     __NV_SATFINITE, __NV_E4M3);
+        u[i] = (lo & 0xFFFFu) | (hi << 16);
     }
     return r;
 }
@@ -105,6 +123,56 @@ __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const flo
             w3p[j] = __float2bfloat16_rn(v);
         }
     }
+}
+
+// Per-filter absolute maximum of the conv2 weights: amax[co] = max |W2[co][.][.][.]|.
+__global__ void conv2_absmax_kernel(const float* __restrict__ w2, float* __restrict__ amax)
+{
+    const int co = blockIdx.x;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < 64 * 121; i += blockDim.x) m = fmaxf(m, fabsf(w2[(size_t)co * 64 * 121 + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        amax[co] = t;
+    }
+}
+
+// conv2 A operand in e4m3 with a scale per filter, sw[co] = amax[co] / 448:
+// block (dy, s, kk) holds rows m = 32 g + co, K = channels 32 kk .. 32 kk + 31
+// as two 16-byte chunks, value W2[co][ci][dy][4 s + g] / sw[co] (zero for 4 s + g = 11).
+__global__ void pack_w2_e4m3_kernel(const float* __restrict__ w2, const float* __restrict__ amax,
+                                    uint8_t* __restrict__ w2q, float* __restrict__ sw)
+{
+    const long long n = (long long)kW2E4M3Bytes;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(j % 16);
+        const int m = (int)((j / 16) % 128);
+        const int half = (int)((j / (16 * 128)) % 2);
+        const int kk = (int)((j / (16 * 128 * 2)) % 2);
+        const int s = (int)((j / (16 * 128 * 2 * 2)) % 3);
+        const int dy = (int)(j / (16 * 128 * 2 * 2 * 3));
+        const int co = m % 32, g = m / 32, dx = 4 * s + g, ci = kk * 32 + half * 16 + e;
+        const float scale = amax[co] > 0.f ? amax[co] / 448.f : 1.f;
+        if (j < 32) sw[j] = amax[j] > 0.f ? amax[j] / 448.f : 1.f;
+        const float v = dx < 11 ? w2[((co * 64 + ci) * 11 + dy) * 11 + dx] / scale : 0.f;
+        w2q[j] = (uint8_t)(__nv_cvt_float2_to_fp8x2(make_float2(v, 0.f), __NV_SATFINITE, __NV_E4M3) & 0xFFu);
+    }
+}
+
+// Activation scale of the e4m3 path from the calibrated maximum of a1:
+// sa = amax / 448, inv_sa = 1 / sa, oscale[co] = sw[co] * sa.
+__global__ void e4m3_scales_kernel(const float* __restrict__ amax_a1, const float* __restrict__ sw,
+                                   float* __restrict__ inv_sa, float* __restrict__ oscale)
+{
+    const float a = *amax_a1;
+    const float sa = a > 0.f ? a / 448.f : 1.f;
+    if (threadIdx.x == 0) *inv_sa = 1.f / sa;
+    if (threadIdx.x < 32) oscale[threadIdx.x] = sw[threadIdx.x] * sa;
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -248,7 +316,8 @@ struct Conv1Smem {
 
 __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt, int H, int W, int P,
                                                     int plane_len, int t1, const bf16* __restrict__ w1p,
-                                                    const float* __restrict__ b1, bf16* __restrict__ a1,
+                                                    const float* __restrict__ b1, void* __restrict__ a1, int mode,
+                                                    const float* __restrict__ inv_sa, float* __restrict__ amax,
                                                     int* status)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -335,17 +404,34 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
         const int qq = q0 + m;
         const bool valid = qq < HP;
         const bool data = valid && (qq % P) < W;
-        bf16* dst = a1 + ((size_t)b * 8 * plane_len + (size_t)(qq + kPad * P + kPad)) * 8;
+        const size_t pos = (size_t)(qq + kPad * P + kPad);
+        const float isa = mode == kConv1OutE4M3 ? __ldg(inv_sa) : 1.f;
+        float vmax = 0.f;
 #pragma unroll
         for (int c0 = 0; c0 < 64; c0 += 16) {
             float v[16];
             tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + ss->bias[c0 + i], 0.f) : 0.f;
-            if (valid) {
-                *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8) * plane_len * 8) = pack8_bf16(v);
-                *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8 + 1) * plane_len * 8) = pack8_bf16(v + 8);
+            if (mode == kConv1OutBF16) {
+                if (valid) {
+                    bf16* dst = reinterpret_cast<bf16*>(a1) + ((size_t)b * 8 * plane_len + pos) * 8;
+                    *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8) * plane_len * 8) = pack8_bf16(v);
+                    *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8 + 1) * plane_len * 8) = pack8_bf16(v + 8);
+                }
+            } else if (mode == kConv1OutE4M3) {
+                if (valid) {
+                    uint8_t* dst = reinterpret_cast<uint8_t*>(a1) + (((size_t)b * 4 + c0 / 16) * plane_len + pos) * 16;
+                    *reinterpret_cast<uint4*>(dst) = pack16_e4m3(v, isa);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) vmax = fmaxf(vmax, v[i]);
             }
+        }
+        if (mode == kConv1AmaxOnly) {
+            for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if (lane == 0) atomicMax(reinterpret_cast<int*>(amax), __float_as_int(vmax));   // vmax >= 0
         }
     }
     tc_fence_before();
@@ -412,21 +498,27 @@ __host__ __device__ inline int conv2_dylast(int j, int P)
     return d < 10 ? d : 10;
 }
 
-template <bool ROWS>
-__global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ a1, int B, int H, int W, int P,
+template <bool ROWS, bool FP8>
+__global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ a1, int B, int H, int W, int P,
                                                        int plane_len, int t2, int nslab,
-                                                       const bf16* __restrict__ w2p,
-                                                       const float* __restrict__ b2, bf16* __restrict__ a2,
+                                                       const void* __restrict__ w2p,
+                                                       const float* __restrict__ b2,
+                                                       const float* __restrict__ oscale, bf16* __restrict__ a2,
                                                        int* status)
 {
+    // bf16: 8 chunks of 8 channels per position, K = 16 per MMA (4 MMAs per (dy, s));
+    // e4m3: 4 chunks of 16 channels per position, K = 32 per MMA (2 MMAs per (dy, s)).
+    constexpr int NCH = FP8 ? 4 : 8;
+    constexpr int KK = FP8 ? 2 : 4;
+    constexpr uint32_t WSTAGE = KK * 4096;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // window mode: [8][nslab * 128][8] bf16; row mode: [nslab pieces][8][kPiecePx][8] bf16
+    // window mode: [NCH][nslab * 128][16 B]; row mode: [nslab pieces][NCH][kPiecePx][16 B]
     const uint32_t CH = ROWS ? (uint32_t)kPiecePx * 16 : (uint32_t)nslab * kSlabPx * 16;
-    const uint32_t win_bytes = ROWS ? (uint32_t)nslab * 8 * CH : 8 * CH;
+    const uint32_t win_bytes = ROWS ? (uint32_t)nslab * NCH * CH : NCH * CH;
     uint8_t* sWin = smem_raw;
-    uint8_t* sW = smem_raw + win_bytes;             // [kW2Stages][16 KB]
-    float* sX = reinterpret_cast<float*>(sW + kW2Stages * 16384);   // [4 slots][32 filters][kXStride]
-    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * 16384 + kXBytes);
+    uint8_t* sW = smem_raw + win_bytes;             // [kW2Stages][WSTAGE]
+    float* sX = reinterpret_cast<float*>(sW + kW2Stages * WSTAGE);   // [4 slots][32 filters][kXStride]
+    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * WSTAGE + kXBytes);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int HP = H * P;
@@ -468,17 +560,17 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
-            const uint8_t* src_img = reinterpret_cast<const uint8_t*>(a1) + (size_t)b * 8 * plane_len * 16;
+            const uint8_t* src_img = reinterpret_cast<const uint8_t*>(a1) + (size_t)b * NCH * plane_len * 16;
             int next_slab = 0;
             for (int dy = 0; dy < 11 && ok; ++dy) {
                 if (ROWS) {
                     const int slot = pc % nslab, n = pc / nslab;
                     ++pc;
                     if (!mbar_wait(smem_u32(&ss->empty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
-                    mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), 8 * kPiecePx * 16);
+                    mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), NCH * kPiecePx * 16);
                     slab_parity[slot] = n & 1;
-                    for (int c = 0; c < 8; ++c)
-                        bulk_g2s(smem_u32(sWin + (slot * 8 + c) * CH),
+                    for (int c = 0; c < NCH; ++c)
+                        bulk_g2s(smem_u32(sWin + (slot * NCH + c) * CH),
                                  src_img + ((size_t)c * plane_len + q0 + dy * P) * 16, kPiecePx * 16,
                                  smem_u32(&ss->full[slot]));
                 }
@@ -486,9 +578,9 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                 while (next_slab <= last) {
                     const int j = next_slab++;
                     if (!mbar_wait(smem_u32(&ss->empty[j]), (it & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
-                    mbar_arrive_expect_tx(smem_u32(&ss->full[j]), 8 * kSlabPx * 16);
+                    mbar_arrive_expect_tx(smem_u32(&ss->full[j]), NCH * kSlabPx * 16);
                     slab_parity[j] = it & 1;
-                    for (int c = 0; c < 8; ++c)
+                    for (int c = 0; c < NCH; ++c)
                         bulk_g2s(smem_u32(sWin + c * CH + j * kSlabPx * 16),
                                  src_img + ((size_t)c * plane_len + q0 + j * kSlabPx) * 16, kSlabPx * 16,
                                  smem_u32(&ss->full[j]));
@@ -496,10 +588,10 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                 for (int s = 0; s < 3 && ok; ++s, ++wst) {
                     const int slot = wst % kW2Stages, n = wst / kW2Stages;
                     if (!mbar_wait(smem_u32(&ss->wempty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
-                    mbar_arrive_expect_tx(smem_u32(&ss->wfull[slot]), 16384);
+                    mbar_arrive_expect_tx(smem_u32(&ss->wfull[slot]), WSTAGE);
                     w_parity[slot] = n & 1;
-                    bulk_g2s(smem_u32(sW + slot * 16384),
-                             reinterpret_cast<const uint8_t*>(w2p) + (size_t)(dy * 3 + s) * 16384, 16384,
+                    bulk_g2s(smem_u32(sW + slot * WSTAGE),
+                             reinterpret_cast<const uint8_t*>(w2p) + (size_t)(dy * 3 + s) * WSTAGE, WSTAGE,
                              smem_u32(&ss->wfull[slot]));
                 }
             }
@@ -510,7 +602,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
             if (w_parity[s] >= 0) mbar_wait_drain(smem_u32(&ss->wfull[s]), w_parity[s]);
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_bf16(128, kConv2N);
+        const uint32_t idesc = FP8 ? idesc_e4m3(128, kConv2N) : idesc_bf16(128, kConv2N);
         int it = 0, wst = 0, pc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
@@ -527,7 +619,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                     const int n = pc / nslab;
                     ++pc;
                     if (!mbar_wait(smem_u32(&ss->full[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
-                    bbase = smem_u32(sWin + slot * 8 * CH);
+                    bbase = smem_u32(sWin + slot * NCH * CH);
                     off = 0;
                 } else {
                     const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
@@ -546,10 +638,11 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                     tc_fence_after();
                     const uint32_t boff = off + (uint32_t)(4 * s) * 16;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = sdesc(smem_u32(sW + wslot * 16384 + kk * 4096), 2048, 128);
+                    for (int kk = 0; kk < KK; ++kk) {
+                        const uint64_t ad = sdesc(smem_u32(sW + wslot * WSTAGE + kk * 4096), 2048, 128);
                         const uint64_t bd = sdesc(bbase + (2 * kk) * CH + boff, CH, 128);
-                        mma_bf16(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
+                        if (FP8) mma_e4m3(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
+                        else mma_bf16(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
                     }
                     mma_commit(smem_u32(&ss->wempty[wslot]));
                 }
@@ -570,9 +663,12 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
         const int g = warp % 4;                   // TMEM lane quarter = tap slot; lane = filter
         const int le = threadIdx.x - 64;          // 0..127
         const int c8 = le / 32, jl = le % 32;     // sum phase: filters 8 c8 .. 8 c8 + 7, column jl
-        float bias8[8];
+        float bias8[8], scale8[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) bias8[e] = __ldg(&b2[c8 * 8 + e]);
+        for (int e = 0; e < 8; ++e) {
+            bias8[e] = __ldg(&b2[c8 * 8 + e]);
+            scale8[e] = FP8 ? __ldg(&oscale[c8 * 8 + e]) : 1.f;
+        }
         float* xrow = sX + (g * 32 + lane) * kXStride;
         const float* xsum = sX + c8 * 8 * kXStride + jl;
         int it = 0;
@@ -606,10 +702,10 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const bf16* __restrict__ 
                 float acc[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    float t = bias8[e];
+                    float t = 0.f;
 #pragma unroll
                     for (int gg = 0; gg < 4; ++gg) t += xsum[(gg * 32 + e) * kXStride];
-                    acc[e] = t;
+                    acc[e] = FP8 ? fmaf(t, scale8[e], bias8[e]) : t + bias8[e];
                 }
                 const int jcol = cc + jl, qq = q0 + jcol;
                 if (jcol < kConv2Valid && qq < HP) {
@@ -809,64 +905,90 @@ int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mo
     return DEEPINV_OK;
 }
 
-int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, bf16* a1, int* status,
-             cudaStream_t st)
+int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
+             const float* inv_sa, float* amax, int* status, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
     const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
     const size_t smem = 16384 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, status);
+    conv1_kernel<<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa, amax,
+                                              status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
 
-static size_t conv2_smem_bytes(const Geo& g, bool rows)
+int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st)
 {
-    const size_t win = rows ? (size_t)kRowSlots * 8 * kPiecePx * 16 : (size_t)8 * g.nslab * kSlabPx * 16;
-    return win + (size_t)kW2Stages * 16384 + kXBytes + sizeof(Conv2Smem);
+    conv2_absmax_kernel<<<32, 256, 0, st>>>(w2, amax_scratch);
+    DI_LAUNCH_CHECK();
+    pack_w2_e4m3_kernel<<<grid1d(kW2E4M3Bytes), 256, 0, st>>>(w2, amax_scratch, w2q, sw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* oscale, cudaStream_t st)
+{
+    e4m3_scales_kernel<<<1, 32, 0, st>>>(amax_a1, sw, inv_sa, oscale);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+static size_t conv2_smem_bytes(const Geo& g, bool rows, bool fp8)
+{
+    const int nch = fp8 ? 4 : 8;
+    const size_t wstage = fp8 ? 8192 : 16384;
+    const size_t win = rows ? (size_t)kRowSlots * nch * kPiecePx * 16 : (size_t)nch * g.nslab * kSlabPx * 16;
+    return win + (size_t)kW2Stages * wstage + kXBytes + sizeof(Conv2Smem);
 }
 
 // Window mode when the whole input window of a tile fits in shared memory.
 // DEEPINV_CONV2_FORCE_ROWS=1 in the environment selects row mode everywhere
 // (both modes give bit-identical results; the tests compare them).
-static bool conv2_window_mode(const Geo& g)
+static bool conv2_window_mode(const Geo& g, bool fp8)
 {
     static const bool force_rows = [] {
         const char* e = getenv("DEEPINV_CONV2_FORCE_ROWS");
         return e && e[0] == '1';
     }();
-    return !force_rows && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false) <= 227 * 1024;
+    return !force_rows && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false, fp8) <= 227 * 1024;
 }
 
 bool conv2_tc_supported(const Geo& g)
 {
-    return conv2_window_mode(g) || conv2_smem_bytes(g, true) <= 227 * 1024;
+    return conv2_window_mode(g, false) || conv2_smem_bytes(g, true, false) <= 227 * 1024;
 }
 
-int conv2_tc(const bf16* a1, int B, const Geo& g, const bf16* w2p, const float* b2, bf16* a2, int num_sms,
-             int* status, cudaStream_t st)
+template <bool ROWS, bool FP8>
+static int launch_conv2(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
+                        bf16* a2, int grid, size_t smem, int nslab, int* status, cudaStream_t st)
+{
+    DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv2_kernel<ROWS, FP8><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2, oscale,
+                                                     a2, status);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
+             bool fp8, bf16* a2, int num_sms, int* status, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
     if (!conv2_tc_supported(g)) {
         set_error("conv2_tc: no kernel configuration for image width %d", g.W);
         return DEEPINV_EUNSUPPORTED;
     }
-    const bool rows = !conv2_window_mode(g);
-    const size_t smem = conv2_smem_bytes(g, rows);
+    const bool rows = !conv2_window_mode(g, fp8);
+    const size_t smem = conv2_smem_bytes(g, rows, fp8);
     const int ntiles = B * g.t2;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
+    const int nslab = rows ? kRowSlots : g.nslab;
     if (rows) {
-        DI_CUDA(cudaFuncSetAttribute(conv2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        conv2_kernel<true><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, kRowSlots, w2p, b2, a2,
-                                                    status);
-    } else {
-        DI_CUDA(cudaFuncSetAttribute(conv2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        conv2_kernel<false><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, g.nslab, w2p, b2, a2,
-                                                     status);
+        return fp8 ? launch_conv2<true, true>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st)
+                   : launch_conv2<true, false>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st);
     }
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
+    return fp8 ? launch_conv2<false, true>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st)
+               : launch_conv2<false, false>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st);
 }
 
 size_t conv3_scratch_elems(const Geo& g, int B) { return (size_t)B * 11 * g.t3 * 128; }

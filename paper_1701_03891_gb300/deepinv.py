@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "libdeepinv.so")
 
 F32 = 0
 BF16 = 1
-PRECISIONS = {"f32": F32, "fp32": F32, "bf16": BF16}
+FP8 = 2
+PRECISIONS = {"f32": F32, "fp32": F32, "bf16": BF16, "fp8": FP8, "e4m3": FP8}
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6
 _STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EUNSUPPORTED: "EUNSUPPORTED",
@@ -73,6 +74,7 @@ SIGNATURES = {
     "deepinv_measure_noalloc": (_I, [_P, _I, _I, _P, _I, _P, _P]),
     "deepinv_net_create": (_I, [ctypes.POINTER(NetDesc), _P, _PP, _PP, _P, ctypes.POINTER(_P)]),
     "deepinv_net_destroy": (_I, [_P]),
+    "deepinv_net_calibrate": (_I, [_P, _P, _I, _P]),
     "deepinv_net_get_desc": (_I, [_P, ctypes.POINTER(NetDesc)]),
     "deepinv_net_reserve": (_I, [_P, _I, _P]),
     "deepinv_net_measure": (_I, [_P, _P, _I, _P, _P]),
@@ -211,6 +213,11 @@ class Net:
     @property
     def handle(self):
         return self._h
+
+    def calibrate(self, y, stream=None):
+        """Fix the e4m3 activation scale from a calibration batch y [B][M] (no-op otherwise)."""
+        _need_f32_cuda(y, "y")
+        _check(lib().deepinv_net_calibrate(self._h, _ptr(y), y.shape[0], _stream(stream)))
 
     def reserve(self, max_B: int, stream=None):
         _check(lib().deepinv_net_reserve(self._h, max_B, _stream(stream)))
