@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--serve-rates", default="20000,80000,200000",
                     help="offered request rates (requests/s) of the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window per rate")
@@ -173,6 +175,60 @@ def traffic_record():
     except Exception:
         pass
     return None
+
+
+def large_bench(args):
+    """256 x 256 images (N = 65536), M/N = 0.1 (M = 6554), batch 256 of DCT-sparse
+    images (K = 2000, seed 5): the bf16 path and the e4m3-conv2 path on the same batch.
+    Step = y = Phi x then x^ = M(y); images/s by CUDA events; conv2 TFLOP/s from the
+    library's stage events; rel-L2 of the e4m3 result against the bf16 one."""
+    import numpy as np
+    import torch
+    from paper_1701_03891_gb300 import deepinv, synth
+    n, B, ratio = 256, 256, 0.10
+    N = n * n
+    M = synth.m_for_ratio(ratio, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    params = synth.he_params(seed=1)
+    x = synth.dct_sparse_images(B, n, n, K=2000, seed=5)
+    xd = torch.from_numpy(x).cuda()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "sense+recover 256x256, M/N=0.10 (M=%d), batch %d, DCT-sparse K=2000" % (M, B)}
+    results = {}
+    for prec in ("bf16", "fp8"):
+        net = deepinv.Net(phi, params, n, n, prec=prec)
+        net.reserve(B)
+        yd = torch.empty((B, M), device="cuda")
+        xh = torch.empty((B, N), device="cuda")
+        net.measure(xd, out=yd)
+        if prec == "fp8":
+            net.calibrate(yd)
+        for _ in range(2):
+            net.measure(xd, out=yd)
+            net.forward(yd, out=xh)
+        torch.cuda.synchronize()
+        net.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.large_steps):
+            net.measure(xd, out=yd)
+            net.forward(yd, out=xh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = net.profile_read()
+        net.profile(False)
+        ms = e0.elapsed_time(e1) / args.large_steps
+        c2 = st["conv2"][0] / max(1, st["conv2"][1])
+        results[prec] = xh.cpu().numpy()
+        out[prec] = {"images_per_s": B / (ms / 1000.0), "ms_per_step": ms,
+                     "conv2_ms": c2, "conv2_tflops": 2.0 * 64 * 32 * 121 * B * N / (c2 / 1000.0) / 1e12,
+                     "stage_ms": {k: v[0] / max(1, v[1]) for k, v in st.items()}}
+        net.close()
+        del yd, xh
+    rel = np.linalg.norm(results["fp8"] - results["bf16"], axis=1) / np.linalg.norm(results["bf16"], axis=1)
+    out["fp8_over_bf16"] = out["fp8"]["images_per_s"] / out["bf16"]["images_per_s"]
+    out["fp8_vs_bf16_max_rel_l2"] = float(rel.max())
+    return out
 
 
 SERVE_SIZES = (32, 64, 128)
@@ -401,6 +457,9 @@ def run_native(args):
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_bench(args)
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_bench(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -416,7 +475,7 @@ def run_native(args):
             "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
-            "e2e": e2e, "serving": serving, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "serving": serving, "large_256": large, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)
