@@ -89,6 +89,8 @@ struct deepinv_net {
     bf16* w1p = nullptr;
     bf16* w2p = nullptr;
     bf16* w3p = nullptr;
+    bf16* w2t = nullptr;        // conv2 input-gradient weights (flipped, transposed)
+    bf16* w3t = nullptr;        // conv3 input-gradient weights
     // e4m3 conv2: weights, per-filter scales, calibrated activation scale
     uint8_t* w2q = nullptr;
     float* sw = nullptr;        // [32] weight scales
@@ -104,6 +106,7 @@ struct deepinv_net {
     // backward workspace
     char* bws = nullptr;
     size_t bws_bytes = 0;
+    int bws_B = 0;
     // profiler: event pool and (stage, start event, end event) spans
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -301,6 +304,7 @@ int repack(deepinv_net* n, cudaStream_t st)
     if (!n->tc) return DEEPINV_OK;
     const int N = n->N, M = n->d.M;
     DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[2], n->w1p, n->w2p, n->w3p, st));
+    if (n->w2t) DI_TRY(pack_dgrad_weights(n->w[1], n->w[2], n->w2t, n->w3t, st));
     if (n->fp8) {
         DI_TRY(pack_w2_e4m3(n->w[1], n->amax_w, n->w2q, n->sw, st));
         if (n->calibrated) DI_TRY(e4m3_scales(n->amax_a1, n->sw, n->inv_sa, n->oscale, st));
@@ -330,6 +334,8 @@ void free_net(deepinv_net* n)
     cudaFree(n->w3p);
     cudaFree(n->w2q);
     cudaFree(n->sw);
+    cudaFree(n->w2t);
+    cudaFree(n->w3t);
     cudaFree(n->ws);
     cudaFree(n->bws);
     for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
@@ -444,6 +450,88 @@ int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved
     // carve at the allocated batch so that plane offsets never move
     const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
     return forward_core(n, w, y, B, xhat, saved, st);
+}
+
+
+// Backward of the bf16 path on the forward pass's planes (tensor cores for the
+// conv2 and conv3 input gradients and the conv2 weight gradient).
+struct BwdWs {
+    float* g3;            // dL/dz3 [B][N]
+    bf16 *g3p, *g2, *g1;  // gradient planes (zero borders)
+    float* part2;         // conv2 weight-gradient partials
+    double *acc, *bpart, *lpart;
+    float *g1f, *dxt, *wt;  // train_fc: conv1 input gradient on CUDA cores
+    size_t bytes;
+};
+
+BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
+{
+    Arena a{base, 0};
+    BwdWs w{};
+    const Geo& g = n->geo;
+    const int N = n->N;
+    w.g3p = a.take<bf16>((size_t)B * g.plane);
+    w.g2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
+    w.g1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
+    w.g3 = a.take<float>((size_t)B * N);
+    w.part2 = a.take<float>(wgrad2_scratch_floats());
+    w.acc = a.take<double>(64 * 121);
+    w.bpart = a.take<double>((size_t)B * 64);
+    w.lpart = a.take<double>(kLossBlocks);
+    if (n->d.train_fc) {
+        w.g1f = a.take<float>((size_t)B * 64 * N);
+        w.dxt = a.take<float>((size_t)B * N);
+        w.wt = a.take<float>(64 * 121);
+    }
+    w.bytes = align_up(a.off, 256);
+    return w;
+}
+
+int backward_tc(deepinv_net* n, const float* y, const float* x, int B, const Saved& sv, float* const dW[3],
+                float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+{
+    const Geo& g = n->geo;
+    const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2;
+    if (B > n->bws_B || !n->bws) {
+        const size_t need = carve_bwd_tc(n, B, nullptr).bytes;
+        DI_CUDA(cudaStreamSynchronize(st));
+        cudaFree(n->bws);
+        n->bws = nullptr;
+        n->bws_bytes = 0;
+        n->bws_B = 0;
+        if (cudaMalloc(&n->bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            n->bws = nullptr;
+            set_error("backward workspace of %zu bytes: out of device memory", need);
+            return DEEPINV_ENOMEM;
+        }
+        DI_CUDA(cudaMemset(n->bws, 0, need));   // gradient planes need zero borders
+        n->bws_bytes = need;
+        n->bws_B = B;
+    }
+    const BwdWs w = carve_bwd_tc(n, n->bws_B, n->bws);
+    int* status = device_status_word();
+    DI_REQUIRE(status, "no device status word");
+    // dL/dz3 = 2 (x^ - x) / B (times [x^ > 0] with final_relu) and the loss in float64
+    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, B, n->d.final_relu, w.g3, w.lpart, loss, st));
+    DI_TRY(grad_plane(w.g3, B, g, w.g3p, st));
+    // conv3: bias and weight gradients, input gradient times [a2 > 0] -> g2
+    DI_TRY(plane_channel_sums(w.g3p, B, 1, g, w.bpart, db[2], st));
+    DI_TRY(small_wgrad(false, w.g3p, sv.a2, B, g, w.acc, dW[2], st));
+    DI_TRY(conv3_dgrad_tc(w.g3p, B, g, n->w3t, sv.a2, w.g2, status, st));
+    // conv2
+    DI_TRY(plane_channel_sums(w.g2, B, 32, g, w.bpart, db[1], st));
+    DI_TRY(wgrad2_tc(w.g2, sv.a1, B, g, w.part2, dW[1], status, st));
+    DI_TRY(conv2_dgrad_tc(w.g2, B, g, n->w2t, sv.a1, w.g1, n->num_sms, status, st));
+    // conv1
+    DI_TRY(plane_channel_sums(w.g1, B, 64, g, w.bpart, db[0], st));
+    DI_TRY(small_wgrad(true, w.g1, sv.xt, B, g, w.acc, dW[0], st));
+    if (n->d.train_fc) {
+        DI_TRY(plane_to_nchw(w.g1, B, 64, g, w.g1f, st));
+        DI_TRY(conv_dgrad_f32(w.g1f, B, 64, H, W, n->w[0], 1, n->d.k, w.wt, w.dxt, st));
+        DI_TRY(sgemm(N, M, B, w.dxt, 1, N, y, M, 1, dWfc, M, st));
+    }
+    return DEEPINV_OK;
 }
 
 int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream_t st)
@@ -601,6 +689,10 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
         DI_STEP(dev_alloc(&n->w1p, kW1PackElems));
         DI_STEP(dev_alloc(&n->w2p, kW2PackElems));
         DI_STEP(dev_alloc(&n->w3p, kW3PackElems));
+        if (!n->fp8) {
+            DI_STEP(dev_alloc(&n->w2t, kW2PackElems));
+            DI_STEP(dev_alloc(&n->w3t, kW3tPackElems));
+        }
         if (n->fp8) {
             DI_STEP(dev_alloc(&n->w2q, kW2E4M3Bytes));
             DI_STEP(dev_alloc(&n->sw, 32 * 4 + 1 + 1 + 32));   // sw | oscale | inv_sa | amax_a1 | amax_w
@@ -720,6 +812,7 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
     const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
     const int l1 = net->d.l1, l2 = net->d.l2;
     const Saved sv = carve_saved(net, B, static_cast<char*>(const_cast<void*>(saved)));
+    if (net->tc) return backward_tc(net, y, x, B, sv, dW, db, dWfc, loss, st);
 
     size_t maxw = 0;
     for (int l = 0; l < 3; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;

@@ -89,7 +89,7 @@ static inline Geo make_geo(int H, int W)
     g.t2 = cdiv(g.HP, kConv2Valid);
     // conv3 computes row partial sums T[p] for p in [0, (H + 10) P).
     g.t3 = cdiv((H + kConv2Reach) * g.P, 128);
-    const int win2 = kConv2Reach * g.P + 8 + kConv2N;    // positions one conv2 tile reads
+    const int win2 = kConv2Reach * g.P + 16 + kConv2N;   // positions one conv2 tile reads (shift <= 10)
     g.nslab = cdiv(win2, kSlabPx);
     size_t need = 0;
     auto upd = [&](size_t v) { if (v > need) need = v; };
@@ -97,6 +97,7 @@ static inline Geo make_geo(int H, int W)
     upd((size_t)g.t1 * 128 + (size_t)kConv2Reach * g.P + 16);              // conv1 im2col window
     upd((size_t)g.t3 * 128 + 16);                                          // conv3 window
     upd((size_t)(H + 2 * kPad) * g.P + 2 * kPad);                          // data + borders
+    upd((size_t)g.HP + (size_t)kConv2Reach * g.P + 48);                     // conv2 weight-gradient windows
     g.plane = (int)align_up(need, 8);
     return g;
 }

@@ -56,13 +56,40 @@ int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mo
 //   kConv1OutBF16: bf16 [B][8][plane][8];
 //   kConv1OutE4M3: e4m3 [B][4][plane][16], values times *inv_sa;
 //   kConv1AmaxOnly: no output, atomically raises *amax to the largest a1 value.
-enum { kConv1OutBF16 = 0, kConv1OutE4M3 = 1, kConv1AmaxOnly = 2 };
+//   kConv1GradMask: (backward, 32 filters) result times [mask > 0] as a bf16 gradient plane.
+enum { kConv1OutBF16 = 0, kConv1OutE4M3 = 1, kConv1AmaxOnly = 2, kConv1GradMask = 3 };
 int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
              const float* inv_sa, float* amax, int* status, cudaStream_t st);
 // conv2: a1 (bf16, or e4m3 when fp8) -> a2 bf16 [B][4][plane][8] (bias, ReLU,
 // zero pad columns); the e4m3 path multiplies the accumulators by oscale[co].
 int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
              bool fp8, bf16* a2, int num_sms, int* status, cudaStream_t st);
+// ---------------------------------------------------------------- backward (bf16 path)
+// Input gradients as correlations with flipped kernels, ReLU masks fused:
+// conv3: gradient plane of x^ [B][plane] -> g2 = dL/dz2 [B][4][plane][8] (mask a2 > 0);
+// conv2: g2 -> g1 = dL/dz1 [B][8][plane][8] (mask a1 > 0).
+int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const bf16* a2, bf16* g2, int* status,
+                   cudaStream_t st);
+int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
+                   int* status, cudaStream_t st);
+constexpr size_t kW3tPackElems = 16 * 32 * 8;          // conv3 input-gradient weights [16][32][8]
+// w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
+int pack_dgrad_weights(const float* w2, const float* w3, bf16* w2t, bf16* w3t, cudaStream_t st);
+// g [B][N] float32 -> data positions of the one-channel plane gp (pads untouched).
+int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st);
+// Channel sums of a bf16 plane (bias gradients): part [B][C] float64 scratch, out [C].
+int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st);
+// Weight gradient of conv1 (conv1 = true: G = g1 plane, A = x~ plane) or conv3
+// (G = x^ gradient plane, A = a2 plane) into dw [O][I][11][11]; acc is
+// float64 scratch of O * I * 121.
+int small_wgrad(bool conv1, const bf16* G, const bf16* A, int B, const Geo& g, double* acc, float* dw,
+                cudaStream_t st);
+// conv2 weight gradient on the tensor cores: g2 plane [B][4][plane][8] and a1
+// plane [B][8][plane][8] -> dw [32][64][11][11]; part is float32 scratch of
+// wgrad2_scratch_floats().
+size_t wgrad2_scratch_floats();
+int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
+              cudaStream_t st);
 // e4m3 conv2 weights: [dy][s][kk][2][128][16] bytes with per-filter scales sw[32].
 constexpr size_t kW2E4M3Bytes = 11 * 3 * 2 * 2 * 128 * 16;
 int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st);

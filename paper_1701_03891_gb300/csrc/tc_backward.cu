@@ -1,0 +1,409 @@
+// Backward pass of the bfloat16 path (the MSE objective of Sec. 4 by
+// backpropagation), on the padded planes of the forward pass.
+//
+// In plane coordinates the forward convolution reads input position
+// q + dy P + dx for output q (data at plane index q + 5 P + 5).  Hence
+//   input gradient:  dA[q] = sum_{dy',dx'} W[10-dy'][10-dx']^T G[q + dy' P + dx']
+//                    -- the same correlation with flipped, transposed kernels,
+//                       run by the forward kernels (conv1<32>, conv2 DGRAD);
+//   weight gradient: dW[dy][dx] = sum_u G[u] A[u + (dy-5) P + (dx-5)]^T over
+//                    plane positions u (G is zero off the data positions).
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace di {
+namespace {
+
+using namespace tc;
+
+inline int grid_for(long long n, int threads = 256)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// conv2 input-gradient weights: block (dy', s) holds rows m = 64 g + ci
+// (g = tap slot, dx' = 2 s + g), K = the 32 output channels in two chunks of
+// 16, value W2[co][ci][10 - dy'][10 - dx'] (zero for dx' = 11).
+// conv3 input-gradient weights (conv1<32> layout): row n = ci, K = tap
+// t = 11 dy' + dx' (t >= 121 zero), value W3[0][ci][10 - dy'][10 - dx'].
+__global__ void pack_dgrad_weights_kernel(const float* __restrict__ w2, const float* __restrict__ w3,
+                                          bf16* __restrict__ w2t, bf16* __restrict__ w3t)
+{
+    const long long n2 = kW2PackElems, n3 = kW3tPackElems;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2 + n3;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < n2) {
+            const int e = (int)(i % 8);
+            const int m = (int)((i / 8) % 128);
+            const int half = (int)((i / (8 * 128)) % 2);
+            const int kk = (int)((i / (8 * 128 * 2)) % 2);
+            const int s = (int)((i / (8 * 128 * 2 * 2)) % 6);
+            const int dy = (int)(i / (8 * 128 * 2 * 2 * 6));
+            const int ci = m % 64, g = m / 64, dx = 2 * s + g, co = kk * 16 + half * 8 + e;
+            const float v = dx < 11 ? w2[((co * 64 + ci) * 11 + (10 - dy)) * 11 + (10 - dx)] : 0.f;
+            w2t[i] = __float2bfloat16_rn(v);
+        } else {
+            const long long j = i - n2;
+            const int e = (int)(j % 8), ci = (int)((j / 8) % 32), kc = (int)(j / (8 * 32));
+            const int t = kc * 8 + e;
+            const float v = t < 121 ? w3[(ci * 11 + (10 - t / 11)) * 11 + (10 - t % 11)] : 0.f;
+            w3t[j] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// Gradient plane of x^: gp[b][q + 5 P + 5] = g[b][r n2 + c], q = r P + c (other entries untouched).
+__global__ void grad_plane_kernel(const float* __restrict__ g, int B, int H, int W, int P, int plane_len,
+                                  bf16* __restrict__ gp)
+{
+    const long long n = (long long)B * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % W), r = (int)((i / W) % H);
+        const long long b = i / ((long long)W * H);
+        gp[(size_t)b * plane_len + (size_t)r * P + c + kPad * P + kPad] = __float2bfloat16_rn(g[i]);
+    }
+}
+
+// Per-image channel sums of a chunked bf16 plane [B][C/8][plane][8] (C % 8 == 0)
+// or of a one-channel plane (C == 1): part[b][c] in float64.
+__global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_len, double* __restrict__ part)
+{
+    const int b = blockIdx.x;
+    const int nch = C == 1 ? 1 : C / 8;
+    __shared__ double red[8][64];
+    for (int k = threadIdx.x; k < 8 * 64; k += blockDim.x) red[k / 64][k % 64] = 0.0;
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (C == 1) {
+            for (int p = threadIdx.x; p < plane_len; p += blockDim.x)
+                acc[0] += (double)__bfloat162float(src[(size_t)b * plane_len + p]);
+        } else {
+            const uint4* s4 = reinterpret_cast<const uint4*>(src + (((size_t)b * nch + ch) * plane_len) * 8);
+            for (int p = threadIdx.x; p < plane_len; p += blockDim.x) {
+                const uint4 u = s4[p];
+                const bf16* v = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[e] += (double)__bfloat162float(v[e]);
+            }
+        }
+        for (int e = 0; e < 8; ++e) {
+            double t = acc[e];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&red[e][ch], t);   // shared-memory add of warp totals
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x)
+        part[(size_t)b * C + c] = C == 1 ? red[0][0] : red[c % 8][c / 8];
+}
+
+// out[c] = sum_b part[b][c] in a fixed order.
+__global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, float* __restrict__ out)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < B; ++b) s += part[(size_t)b * C + c];
+        out[c] = (float)s;
+    }
+}
+
+// Weight gradient of the layers with one channel on one side (conv1: G has
+// 64 channels, A = x~ one; conv3: G = x^ gradient one channel, A = a2 with
+// 32), over NPOS plane positions of one image per block:
+//   dW[o][i][dy][dx] += sum_u G[u][o] A[u + (dy-5) P + dx - 5][i].
+// Thread (j, dy) owns the 11 taps dx of one kernel row and one channel j of
+// the many-channel side (32 channels per block, blockIdx.y selects them); it
+// slides an 11-value window along u.  Block totals are added into acc
+// (float64) with atomics.
+constexpr int kWgNpos = 256;
+
+template <int O, int I>
+__global__ void __launch_bounds__(352) small_wgrad_kernel(const bf16* __restrict__ G, const bf16* __restrict__ A,
+                                                          int P, int plane_len, int u_begin, int u_count,
+                                                          double* __restrict__ acc)
+{
+    constexpr int J = O > I ? O : I;                 // channels of the many-channel side (64 or 32)
+    static_assert(O == 1 || I == 1, "one side has one channel");
+    const int nblk = (u_count + kWgNpos - 1) / kWgNpos;
+    const int b = blockIdx.x / nblk;
+    const int u0 = u_begin + (blockIdx.x % nblk) * kWgNpos;
+    const int npos = min(kWgNpos, u_begin + u_count - u0);
+    const int wlen = npos + 10 * P + 10;
+    extern __shared__ float sm[];
+    float* sG = sm;                                  // [kWgNpos][O]
+    float* sA = sm + kWgNpos * O;                    // [wlen][I], window starts at u0 - 5 P - 5
+    const int gch = O == 1 ? 1 : O / 8, ach = I == 1 ? 1 : I / 8;
+    for (int k = threadIdx.x; k < npos * O; k += blockDim.x) {
+        const int u = k / O, o = k % O;
+        const size_t pos = (size_t)(u0 + u);
+        sG[k] = O == 1 ? __bfloat162float(G[(size_t)b * plane_len + pos])
+                       : __bfloat162float(G[(((size_t)b * gch + o / 8) * plane_len + pos) * 8 + o % 8]);
+    }
+    for (int k = threadIdx.x; k < wlen * I; k += blockDim.x) {
+        const int u = k / I, i = k % I;
+        const long long pos = (long long)u0 - 5 * P - 5 + u;
+        float v = 0.f;
+        if (pos >= 0 && pos < plane_len)
+            v = I == 1 ? __bfloat162float(A[(size_t)b * plane_len + pos])
+                       : __bfloat162float(A[(((size_t)b * ach + i / 8) * plane_len + pos) * 8 + i % 8]);
+        sA[k] = v;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < 32 * 11) {
+        const int j = blockIdx.y * 32 + t % 32, dy = t / 32;   // blockIdx.y picks 32 of the J channels
+        const int o = O == 1 ? 0 : j, i = I == 1 ? 0 : j;
+        float w[11], a[11];
+#pragma unroll
+        for (int dx = 0; dx < 11; ++dx) {
+            w[dx] = sA[(dy * P + dx) * I + i];      // u = 0: window index u + dy P + dx
+            a[dx] = 0.f;
+        }
+        for (int u = 0; u < npos; ++u) {
+            const float gv = sG[u * O + o];
+#pragma unroll
+            for (int dx = 0; dx < 11; ++dx) a[dx] = fmaf(gv, w[dx], a[dx]);
+#pragma unroll
+            for (int dx = 0; dx < 10; ++dx) w[dx] = w[dx + 1];
+            w[10] = sA[((u + 1) + dy * P + 10) * I + i];
+        }
+#pragma unroll
+        for (int dx = 0; dx < 11; ++dx) atomicAdd(&acc[((size_t)o * I + i) * 121 + dy * 11 + dx], (double)a[dx]);
+    }
+}
+
+__global__ void d2f_kernel(const double* __restrict__ src, int n, float* __restrict__ dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = (float)src[i];
+}
+
+
+// ---------------------------------------------------------------- conv2 weight gradient
+// dW2[co][ci][dy][4 s + g] = sum_u' G[u' - g][co] A1[u' + (dy - 5) P + 4 s - 5][ci]
+// as MMAs with K = 16 plane positions u', both operands MN-major (channels
+// contiguous in 16-byte chunks, positions 16 bytes apart -- the planes' own
+// layout): A = 128 rows (tap slot g, filter co) read from four windows of the
+// g2 plane shifted by g; B = up to 256 rows (kernel-row group p = (dy, s),
+// channel ci) read from four windows of a1.  33 groups p -> 9 CTAs columns
+// ("quads"); positions are split over kWgSplit CTAs each; every CTA leaves a
+// 128 x 256 float32 partial, summed in float64 in a fixed order.
+constexpr int kWgKB = 128;           // positions per stage
+constexpr int kWgStages = 2;
+constexpr int kWgQuads = 9;
+constexpr int kWgSplit = 16;          // 9 x 16 = 144 CTAs
+constexpr uint32_t kWgABytes = 16 * kWgKB * 16;     // 16 M-groups
+constexpr uint32_t kWgBBytes = 32 * kWgKB * 16;     // 32 N-groups
+
+struct WgSmem {
+    uint64_t full[kWgStages], empty[kWgStages], acc_full, drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
+                                                        int B, int P, int HP16, int plane_len,
+                                                        float* __restrict__ part, int* status)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sA = smem_raw;                                        // [stage][16 groups][KB][16 B]
+    uint8_t* sB = smem_raw + kWgStages * kWgABytes;                // [stage][32 groups][KB][16 B]
+    WgSmem* ss = reinterpret_cast<WgSmem*>(sB + kWgStages * kWgBBytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int quad = blockIdx.x % kWgQuads, split = blockIdx.x / kWgQuads;
+    const int npairs = quad < 8 ? 4 : 1;
+    const int NB = npairs * 64;
+    const int nb_img = (HP16 + kWgKB - 1) / kWgKB;
+    const long long total = (long long)B * nb_img;
+    const long long blk0 = total * split / kWgSplit, blk1 = total * (split + 1) / kWgSplit;
+    const int u_begin = kPad * P + kPad;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(smem_u32(&ss->full[s]), 1);
+            mbar_init(smem_u32(&ss->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&ss->acc_full), 1);
+        mbar_init(smem_u32(&ss->drain), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        int parity[kWgStages] = {-1, -1};
+        for (long long k = blk0; k < blk1; ++k) {
+            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
+            if (!mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag)) break;
+            const int b = (int)(k / nb_img);
+            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
+            const int npos = min(kWgKB, u_begin + HP16 - u0);
+            const uint32_t bytes = (uint32_t)npos * 16;
+            mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (16 + 8 * npairs) * bytes);
+            parity[st] = n & 1;
+            const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
+            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * 8 * plane_len * 16;
+            uint8_t* dA = sA + st * kWgABytes;
+            uint8_t* dB = sB + st * kWgBBytes;
+            for (int g = 0; g < 4; ++g)
+                for (int c4 = 0; c4 < 4; ++c4)
+                    bulk_g2s(smem_u32(dA + (g * 4 + c4) * kWgKB * 16),
+                             g2b + ((size_t)c4 * plane_len + u0 - g) * 16, bytes, smem_u32(&ss->full[st]));
+            for (int pl = 0; pl < npairs; ++pl) {
+                const int p = quad * 4 + pl, dy = p / 3, s = p % 3;
+                const int off = (dy - 5) * P + 4 * s - 5;
+                for (int c8 = 0; c8 < 8; ++c8)
+                    bulk_g2s(smem_u32(dB + (pl * 8 + c8) * kWgKB * 16),
+                             a1b + ((size_t)c8 * plane_len + u0 + off) * 16, bytes, smem_u32(&ss->full[st]));
+            }
+        }
+        for (int s = 0; s < kWgStages; ++s)
+            if (parity[s] >= 0) {
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try_wait(smem_u32(&ss->full[s]), parity[s]) && globaltimer() - t0 < 1000000000ull) {}
+            }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_mn(128, NB);
+        bool first = true;
+        for (long long k = blk0; k < blk1; ++k) {
+            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
+            if (!mbar_wait(smem_u32(&ss->full[st]), n & 1, status, &ss->abort_flag)) break;
+            tc_fence_after();
+            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
+            const int nsteps = min(kWgKB, u_begin + HP16 - u0) / 16;
+            const uint32_t a0 = smem_u32(sA + st * kWgABytes), b0 = smem_u32(sB + st * kWgBBytes);
+            for (int ks = 0; ks < nsteps; ++ks) {
+                const uint64_t ad = sdesc(a0 + ks * 256, 128, kWgKB * 16);
+                const uint64_t bd = sdesc(b0 + ks * 256, 128, kWgKB * 16);
+                mma_bf16(tbase, ad, bd, idesc, first ? 0u : 1u);
+                first = false;
+            }
+            mma_commit(smem_u32(&ss->empty[st]));
+        }
+        // an empty range still produces a (zero) partial
+        mma_commit(smem_u32(&ss->acc_full));
+        mma_commit(smem_u32(&ss->drain));
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(smem_u32(&ss->drain), 0) && globaltimer() - t0 < 1000000000ull) {}
+    } else if (warp >= 2) {
+        const int q = warp % 4;
+        bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        tc_fence_after();
+        float* dst = part + ((size_t)blockIdx.x * 128 + q * 32 + lane) * 256;
+        const bool empty = blk1 <= blk0;
+        for (int c0 = 0; c0 < 256; c0 += 16) {
+            float v[16];
+            if (ok && !empty && c0 < NB) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + c0, v);
+            else
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 256);
+    }
+}
+
+// dW2[co][ci][dy][dx] = sum over splits of part[quad + 9 split][32 g + co][64 pl + ci],
+// with p = 4 quad + pl = 3 dy + s and dx = 4 s + g (< 11).
+__global__ void wgrad2_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
+{
+    const int n = 32 * 64 * 121;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int dx = i % 11, dy = (i / 11) % 11, ci = (i / 121) % 64, co = i / (121 * 64);
+        const int s = dx / 4, g = dx % 4, p = dy * 3 + s, quad = p / 4, pl = p % 4;
+        double acc = 0.0;
+        for (int k = 0; k < kWgSplit; ++k)
+            acc += (double)part[((size_t)(quad + kWgQuads * k) * 128 + g * 32 + co) * 256 + pl * 64 + ci];
+        dw[i] = (float)acc;
+    }
+}
+
+}  // namespace
+
+int pack_dgrad_weights(const float* w2, const float* w3, bf16* w2t, bf16* w3t, cudaStream_t st)
+{
+    pack_dgrad_weights_kernel<<<grid_for((long long)(kW2PackElems + kW3tPackElems)), 256, 0, st>>>(w2, w3, w2t, w3t);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st)
+{
+    const long long n = (long long)B * geo.H * geo.W;
+    grad_plane_kernel<<<grid_for(n), 256, 0, st>>>(g, B, geo.H, geo.W, geo.P, geo.plane, gp);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st)
+{
+    plane_sum_kernel<<<B, 256, 0, st>>>(src, C, geo.plane, part);
+    DI_LAUNCH_CHECK();
+    sum_parts_kernel<<<1, 64, 0, st>>>(part, B, C, out);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+// Positions u that can carry a nonzero gradient: the data rows [5P+5, 5P+5+HP).
+int small_wgrad(bool conv1, const bf16* G, const bf16* A, int B, const Geo& g, double* acc, float* dw,
+                cudaStream_t st)
+{
+    const int O = conv1 ? 64 : 1, I = conv1 ? 1 : 32;
+    const int n = O * I * 121;
+    DI_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * sizeof(double), st));
+    const int u_begin = kPad * g.P + kPad, u_count = g.HP;
+    const int nblk = (u_count + kWgNpos - 1) / kWgNpos;
+    const int wlen = kWgNpos + 10 * g.P + 10;
+    const size_t smem = ((size_t)kWgNpos * O + (size_t)(wlen + 1) * I) * sizeof(float);
+    if (conv1) {
+        DI_CUDA(cudaFuncSetAttribute(small_wgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        small_wgrad_kernel<64, 1><<<dim3(B * nblk, 2), 352, smem, st>>>(G, A, g.P, g.plane, u_begin, u_count, acc);
+    } else {
+        DI_CUDA(cudaFuncSetAttribute(small_wgrad_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        small_wgrad_kernel<1, 32><<<B * nblk, 352, smem, st>>>(G, A, g.P, g.plane, u_begin, u_count, acc);
+    }
+    DI_LAUNCH_CHECK();
+    d2f_kernel<<<grid_for(n), 256, 0, st>>>(acc, n, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+size_t wgrad2_scratch_floats() { return (size_t)kWgQuads * kWgSplit * 128 * 256; }
+
+int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
+              cudaStream_t st)
+{
+    const int HP16 = (g.HP + 15) / 16 * 16;
+    const size_t smem = (size_t)kWgStages * (kWgABytes + kWgBBytes) + sizeof(WgSmem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(wgrad2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad2_kernel<<<kWgQuads * kWgSplit, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, part, status);
+    DI_LAUNCH_CHECK();
+    wgrad2_reduce_kernel<<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+}  // namespace di

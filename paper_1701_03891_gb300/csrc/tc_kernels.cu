@@ -314,18 +314,23 @@ struct Conv1Smem {
     float bias[64];
 };
 
+// COUT = 64: conv1 itself.  COUT = 32 with mode kConv1GradMask: the input
+// gradient of conv3 (one input channel, the gradient plane of x^, correlated
+// with conv3's flipped kernels), times the ReLU mask of a2.
+template <int COUT>
 __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt, int H, int W, int P,
                                                     int plane_len, int t1, const bf16* __restrict__ w1p,
                                                     const float* __restrict__ b1, void* __restrict__ a1, int mode,
                                                     const float* __restrict__ inv_sa, float* __restrict__ amax,
-                                                    int* status)
+                                                    const bf16* __restrict__ mask_src, int* status)
 {
+    constexpr uint32_t BBYTES = 16 * COUT * 16;   // [16 chunks][COUT rows][8]
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* sB = smem_raw;                 // 16 KB
-    uint8_t* sA = smem_raw + 16384;         // 32 KB
-    bf16* sWin = reinterpret_cast<bf16*>(smem_raw + 16384 + 32768);
+    uint8_t* sB = smem_raw;
+    uint8_t* sA = smem_raw + BBYTES;        // 32 KB
+    bf16* sWin = reinterpret_cast<bf16*>(smem_raw + BBYTES + 32768);
     const int winx = (128 + kConv2Reach * P + 10 + 7) / 8 * 8;
-    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + 16384 + 32768 + winx * 2);
+    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + BBYTES + 32768 + winx * 2);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int b = blockIdx.x / t1, t = blockIdx.x % t1;
@@ -338,9 +343,9 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
         ss->abort_flag = 0;
         fence_mbar_init();
     }
-    if (threadIdx.x < 64) ss->bias[threadIdx.x] = __ldg(&b1[threadIdx.x]);
+    if (threadIdx.x < 64) ss->bias[threadIdx.x] = (b1 && threadIdx.x < COUT) ? __ldg(&b1[threadIdx.x]) : 0.f;
     if (warp == 0) {
-        tmem_alloc(smem_u32(&ss->tmem_base), 64);
+        tmem_alloc(smem_u32(&ss->tmem_base), COUT < 32 ? 32 : COUT);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -349,8 +354,8 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
     const uint32_t tbase = ss->tmem_base;
 
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(smem_u32(&ss->wbar), 16384);
-        bulk_g2s(smem_u32(sB), w1p, 16384, smem_u32(&ss->wbar));
+        mbar_arrive_expect_tx(smem_u32(&ss->wbar), BBYTES);
+        bulk_g2s(smem_u32(sB), w1p, BBYTES, smem_u32(&ss->wbar));
     }
     // proxy window -> shared memory (16-byte vectors; the plane is 16-byte aligned)
     {
@@ -384,11 +389,11 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
     if (threadIdx.x == 0) {
         if (mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag)) {
             tc_fence_after();
-            const uint32_t idesc = idesc_bf16(128, 64);
+            const uint32_t idesc = idesc_bf16(128, COUT);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const uint64_t ad = sdesc(smem_u32(sA + kk * 4096), 2048, 128);
-                const uint64_t bd = sdesc(smem_u32(sB + kk * 2048), 1024, 128);
+                const uint64_t bd = sdesc(smem_u32(sB + kk * 2 * COUT * 16), COUT * 16, 128);
                 mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
             }
         } else {
@@ -408,9 +413,30 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
         const float isa = mode == kConv1OutE4M3 ? __ldg(inv_sa) : 1.f;
         float vmax = 0.f;
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
             float v[16];
             tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (mode == kConv1GradMask) {
+                if (valid) {
+                    const size_t base = ((size_t)b * (COUT / 8) + c0 / 8) * plane_len + pos;
+                    uint4 m0 = make_uint4(0, 0, 0, 0), m1 = make_uint4(0, 0, 0, 0);
+                    if (data) {
+                        m0 = *reinterpret_cast<const uint4*>(mask_src + base * 8);
+                        m1 = *reinterpret_cast<const uint4*>(mask_src + (base + plane_len) * 8);
+                    }
+                    const bf16* mv0 = reinterpret_cast<const bf16*>(&m0);
+                    const bf16* mv1 = reinterpret_cast<const bf16*>(&m1);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        v[i] = __bfloat162float(mv0[i]) > 0.f ? v[i] : 0.f;
+                        v[8 + i] = __bfloat162float(mv1[i]) > 0.f ? v[8 + i] : 0.f;
+                    }
+                    bf16* dst = reinterpret_cast<bf16*>(a1);
+                    *reinterpret_cast<uint4*>(dst + base * 8) = pack8_bf16(v);
+                    *reinterpret_cast<uint4*>(dst + (base + plane_len) * 8) = pack8_bf16(v + 8);
+                }
+                continue;
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + ss->bias[c0 + i], 0.f) : 0.f;
             if (mode == kConv1OutBF16) {
@@ -438,7 +464,7 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tbase, 64);
+        tmem_dealloc(tbase, COUT < 32 ? 32 : COUT);
     }
 }
 
@@ -466,7 +492,7 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
 constexpr int kW2Stages = 4;
 constexpr int kMaxSlabs = 10;
 
-constexpr int kPiecePx = 8 + kConv2N;  // positions one kernel row's MMAs read (row mode)
+constexpr int kPiecePx = 16 + kConv2N; // positions one kernel row's MMAs read (row mode; shift <= 10)
 constexpr int kRowSlots = 4;           // row-mode ring of input pieces
 constexpr int kXStride = 36;          // floats per row of the slot exchange (32 + 4 pad)
 constexpr int kXBytes = 4 * 32 * kXStride * 4;
@@ -498,18 +524,27 @@ __host__ __device__ inline int conv2_dylast(int j, int P)
     return d < 10 ? d : 10;
 }
 
-template <bool ROWS, bool FP8>
+template <bool ROWS, bool FP8, bool DGRAD>
 __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ a1, int B, int H, int W, int P,
                                                        int plane_len, int t2, int nslab,
                                                        const void* __restrict__ w2p,
                                                        const float* __restrict__ b2,
-                                                       const float* __restrict__ oscale, bf16* __restrict__ a2,
+                                                       const float* __restrict__ oscale,
+                                                       const bf16* __restrict__ mask_src, bf16* __restrict__ a2,
                                                        int* status)
 {
-    // bf16: 8 chunks of 8 channels per position, K = 16 per MMA (4 MMAs per (dy, s));
-    // e4m3: 4 chunks of 16 channels per position, K = 32 per MMA (2 MMAs per (dy, s)).
-    constexpr int NCH = FP8 ? 4 : 8;
-    constexpr int KK = FP8 ? 2 : 4;
+    // Forward: 4 tap slots x 32 filters, input 64 channels.  bf16: 8 chunks of
+    // 8 channels per position, K = 16 per MMA (4 MMAs per (dy, s)); e4m3: 4
+    // chunks of 16 channels, K = 32 per MMA (2 MMAs per (dy, s)).
+    // DGRAD (input gradient of conv2, a correlation of the 32-channel output
+    // gradient with the flipped, transposed weights): 2 tap slots x 64 input
+    // channels, taps dx = 2 s + g for s = 0..5, input 32 channels (4 chunks,
+    // 2 MMAs per (dy, s)); the epilogue applies the ReLU mask of a1.
+    constexpr int NCH = (FP8 || DGRAD) ? 4 : 8;
+    constexpr int KK = (FP8 || DGRAD) ? 2 : 4;
+    constexpr int GROUPS = DGRAD ? 6 : 3;      // column groups s per kernel row
+    constexpr int SSTEP = DGRAD ? 2 : 4;       // taps per group (= position shift between groups)
+    constexpr int MAXSHIFT = SSTEP * (GROUPS - 1);
     constexpr uint32_t WSTAGE = KK * 4096;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // window mode: [NCH][nslab * 128][16 B]; row mode: [nslab pieces][NCH][kPiecePx][16 B]
@@ -574,7 +609,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                                  src_img + ((size_t)c * plane_len + q0 + dy * P) * 16, kPiecePx * 16,
                                  smem_u32(&ss->full[slot]));
                 }
-                const int last = ROWS ? -1 : (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                const int last = ROWS ? -1 : (dy * P + MAXSHIFT + kConv2N - 1) / kSlabPx;
                 while (next_slab <= last) {
                     const int j = next_slab++;
                     if (!mbar_wait(smem_u32(&ss->empty[j]), (it & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
@@ -585,13 +620,13 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                                  src_img + ((size_t)c * plane_len + q0 + j * kSlabPx) * 16, kSlabPx * 16,
                                  smem_u32(&ss->full[j]));
                 }
-                for (int s = 0; s < 3 && ok; ++s, ++wst) {
+                for (int s = 0; s < GROUPS && ok; ++s, ++wst) {
                     const int slot = wst % kW2Stages, n = wst / kW2Stages;
                     if (!mbar_wait(smem_u32(&ss->wempty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
                     mbar_arrive_expect_tx(smem_u32(&ss->wfull[slot]), WSTAGE);
                     w_parity[slot] = n & 1;
                     bulk_g2s(smem_u32(sW + slot * WSTAGE),
-                             reinterpret_cast<const uint8_t*>(w2p) + (size_t)(dy * 3 + s) * WSTAGE, WSTAGE,
+                             reinterpret_cast<const uint8_t*>(w2p) + (size_t)(dy * GROUPS + s) * WSTAGE, WSTAGE,
                              smem_u32(&ss->wfull[slot]));
                 }
             }
@@ -622,7 +657,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                     bbase = smem_u32(sWin + slot * NCH * CH);
                     off = 0;
                 } else {
-                    const int last = (dy * P + 8 + kConv2N - 1) / kSlabPx;
+                    const int last = (dy * P + MAXSHIFT + kConv2N - 1) / kSlabPx;
                     while (next_wait <= last) {
                         if (!mbar_wait(smem_u32(&ss->full[next_wait]), it & 1, status, &ss->abort_flag)) { ok = false; break; }
                         ++next_wait;
@@ -632,11 +667,11 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                 }
                 if (!ok) break;
                 tc_fence_after();
-                for (int s = 0; s < 3; ++s, ++wst) {
+                for (int s = 0; s < GROUPS; ++s, ++wst) {
                     const int wslot = wst % kW2Stages, n = wst / kW2Stages;
                     if (!mbar_wait(smem_u32(&ss->wfull[wslot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t boff = off + (uint32_t)(4 * s) * 16;
+                    const uint32_t boff = off + (uint32_t)(SSTEP * s) * 16;
 #pragma unroll
                     for (int kk = 0; kk < KK; ++kk) {
                         const uint64_t ad = sdesc(smem_u32(sW + wslot * WSTAGE + kk * 4096), 2048, 128);
@@ -660,30 +695,30 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
         mbar_wait_drain(smem_u32(&ss->drain), 0);
     } else if (warp >= 2) {
         // ------------------------------------------------ epilogue
-        const int g = warp % 4;                   // TMEM lane quarter = tap slot; lane = filter
-        const int le = threadIdx.x - 64;          // 0..127
-        const int c8 = le / 32, jl = le % 32;     // sum phase: filters 8 c8 .. 8 c8 + 7, column jl
+        const int quarter = warp % 4;                         // TMEM lane quarter
+        const int g = DGRAD ? quarter / 2 : quarter;          // tap slot of this warp's rows
+        const int le = threadIdx.x - 64;                      // 0..127
+        const int jl = le % 32;                               // sum phase: column jl of the chunk
+        constexpr int ITEMS = DGRAD ? 2 : 1;                  // 8-channel groups per thread in the sum phase
         float bias8[8], scale8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            bias8[e] = __ldg(&b2[c8 * 8 + e]);
-            scale8[e] = FP8 ? __ldg(&oscale[c8 * 8 + e]) : 1.f;
+            bias8[e] = DGRAD ? 0.f : __ldg(&b2[(le / 32) * 8 + e]);
+            scale8[e] = FP8 ? __ldg(&oscale[(le / 32) * 8 + e]) : 1.f;
         }
-        float* xrow = sX + (g * 32 + lane) * kXStride;
-        const float* xsum = sX + c8 * 8 * kXStride + jl;
+        float* xrow = sX + (quarter * 32 + lane) * kXStride;  // exchange row = TMEM lane (32 g + co or 64 g + co)
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int buf = it & 1, use = it >> 1;
             bool ok = mbar_wait(smem_u32(&ss->acc_full[buf]), use & 1, status, &ss->abort_flag);
             ok = __all_sync(0xffffffffu, ok);
-            if (lane == 0) ss->vote[buf][g] = ok ? 1 : 0;
+            if (lane == 0) ss->vote[buf][quarter] = ok ? 1 : 0;
             epi_bar();
             ok = ss->vote[buf][0] && ss->vote[buf][1] && ss->vote[buf][2] && ss->vote[buf][3];
             if (!ok) break;
             tc_fence_after();
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
-            bf16* dst = a2 + ((size_t)b * 4 + c8) * plane_len * 8;
-            const uint32_t lane_addr = tbase + ((uint32_t)(g * 32) << 16) + (uint32_t)buf * kConv2N;
+            const uint32_t lane_addr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * kConv2N;
             for (int cc = 0; cc < kConv2N; cc += 32) {
                 float v[36];
                 tmem_ld32(lane_addr + cc, v);
@@ -699,20 +734,42 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                     default: put_shifted<3>(xrow, v); break;
                 }
                 epi_bar();
-                float acc[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    float t = 0.f;
-#pragma unroll
-                    for (int gg = 0; gg < 4; ++gg) t += xsum[(gg * 32 + e) * kXStride];
-                    acc[e] = FP8 ? fmaf(t, scale8[e], bias8[e]) : t + bias8[e];
-                }
                 const int jcol = cc + jl, qq = q0 + jcol;
-                if (jcol < kConv2Valid && qq < HP) {
-                    const bool data = (qq % P) < W;
+                const bool store = jcol < kConv2Valid && qq < HP;
+                const bool data = store && (qq % P) < W;
+                const size_t pos = (size_t)(qq + kPad * P + kPad);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[e] = data ? fmaxf(acc[e], 0.f) : 0.f;
-                    *reinterpret_cast<uint4*>(dst + (size_t)(qq + kPad * P + kPad) * 8) = pack8_bf16(acc);
+                for (int item = 0; item < ITEMS; ++item) {
+                    const int c8 = le / 32 + 4 * item;                // 8-channel group of the output
+                    float acc[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float t = 0.f;
+                        if (DGRAD) {
+                            t = sX[(c8 * 8 + e) * kXStride + jl] + sX[(64 + c8 * 8 + e) * kXStride + jl];
+                        } else {
+#pragma unroll
+                            for (int gg = 0; gg < 4; ++gg) t += sX[(gg * 32 + c8 * 8 + e) * kXStride + jl];
+                        }
+                        acc[e] = FP8 ? fmaf(t, scale8[e], bias8[e]) : t + bias8[e];
+                    }
+                    if (store) {
+                        constexpr int OUTCH = DGRAD ? 8 : 4;
+                        bf16* dst = a2 + (((size_t)b * OUTCH + c8) * plane_len + pos) * 8;
+                        if (DGRAD) {
+                            // gradient of a1 times the ReLU mask [a1 > 0]; zero outside the image
+                            uint4 mk = make_uint4(0, 0, 0, 0);
+                            if (data)
+                                mk = *reinterpret_cast<const uint4*>(mask_src + (((size_t)b * 8 + c8) * plane_len + pos) * 8);
+                            const bf16* mv = reinterpret_cast<const bf16*>(&mk);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) acc[e] = (data && __bfloat162float(mv[e]) > 0.f) ? acc[e] : 0.f;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) acc[e] = data ? fmaxf(acc[e], 0.f) : 0.f;
+                        }
+                        *reinterpret_cast<uint4*>(dst) = pack8_bf16(acc);
+                    }
                 }
                 epi_bar();
             }
@@ -911,9 +968,22 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
     if (B <= 0) return DEEPINV_OK;
     const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
     const size_t smem = 16384 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(conv1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa, amax,
-                                              status);
+    DI_CUDA(cudaFuncSetAttribute(conv1_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv1_kernel<64><<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa, amax,
+                                                  nullptr, status);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const bf16* a2, bf16* g2, int* status,
+                   cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
+    const size_t smem = 8192 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(conv1_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv1_kernel<32><<<B * g.t1, 128, smem, st>>>(g3p, g.H, g.W, g.P, g.plane, g.t1, w3t, nullptr, g2, kConv1GradMask,
+                                                  nullptr, nullptr, a2, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -959,13 +1029,14 @@ bool conv2_tc_supported(const Geo& g)
     return conv2_window_mode(g, false) || conv2_smem_bytes(g, true, false) <= 227 * 1024;
 }
 
-template <bool ROWS, bool FP8>
+template <bool ROWS, bool FP8, bool DGRAD>
 static int launch_conv2(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
-                        bf16* a2, int grid, size_t smem, int nslab, int* status, cudaStream_t st)
+                        const bf16* mask_src, bf16* a2, int grid, size_t smem, int nslab, int* status, cudaStream_t st)
 {
-    DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv2_kernel<ROWS, FP8><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2, oscale,
-                                                     a2, status);
+    DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, FP8, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    conv2_kernel<ROWS, FP8, DGRAD><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2,
+                                                            oscale, mask_src, a2, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -984,11 +1055,25 @@ int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* 
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     const int nslab = rows ? kRowSlots : g.nslab;
     if (rows) {
-        return fp8 ? launch_conv2<true, true>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st)
-                   : launch_conv2<true, false>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st);
+        return fp8 ? launch_conv2<true, true, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st)
+                   : launch_conv2<true, false, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st);
     }
-    return fp8 ? launch_conv2<false, true>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st)
-               : launch_conv2<false, false>(a1, B, g, w2p, b2, oscale, a2, grid, smem, nslab, status, st);
+    return fp8 ? launch_conv2<false, true, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st)
+               : launch_conv2<false, false, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st);
+}
+
+int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
+                   int* status, cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    // the 32-channel gradient uses 4 chunks per position, like the e4m3 input
+    const bool rows = !conv2_window_mode(g, true);
+    const size_t smem = conv2_smem_bytes(g, rows, true);
+    const int ntiles = B * g.t2;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    const int nslab = rows ? kRowSlots : g.nslab;
+    if (rows) return launch_conv2<true, false, true>(g2, B, g, w2t, nullptr, nullptr, a1, g1, grid, smem, nslab, status, st);
+    return launch_conv2<false, false, true>(g2, B, g, w2t, nullptr, nullptr, a1, g1, grid, smem, nslab, status, st);
 }
 
 size_t conv3_scratch_elems(const Geo& g, int B) { return (size_t)B * 11 * g.t3 * 128; }

@@ -239,6 +239,29 @@ def test_backward_matches_oracle(di, prec, train_fc):
         assert err <= tol, ("wfc", err)
 
 
+@pytest.mark.parametrize("n1,n2,M,B", [(32, 32, 102, 3), (24, 40, 96, 2), (64, 64, 410, 2), (20, 37, 74, 2)])
+def test_backward_bf16_shapes(di, n1, n2, M, B):
+    """bf16 backward (tensor-core conv2/conv3 input gradients and conv2 weight
+    gradient) against the FP64 oracle on several image shapes."""
+    N = n1 * n2
+    phi = synth.gaussian_phi(M, N, seed=4)
+    params = synth.he_params(seed=5, bias_std=0.02)
+    x = synth.dct_sparse_images(B, n1, n2, K=max(4, N // 40), seed=6)
+    y = oracle.measure(phi, x).astype(np.float32)
+    loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
+    yd, xd = _cuda(y), _cuda(x)
+    saved = net.new_saved(B)
+    net.forward(yd, saved=saved)
+    loss, dW, db, _ = net.backward(yd, xd, saved)
+    assert abs(float(loss) - loss_ref) <= 2e-2 * abs(loss_ref)
+    for i in range(3):
+        for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
+            ref = g[name]
+            err = float(np.linalg.norm(got.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30))
+            assert err <= 5e-2, (name, err)
+
+
 def test_sgd_momentum_step(di):
     n1, n2, phi, params, x, y = _train_case(False)
     net = di.Net(phi, params, n1, n2, prec="f32")
