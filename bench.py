@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=10)
     ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--serve-rates", default="20000,80000,200000",
                     help="offered request rates (requests/s) of the serving sweep")
@@ -229,6 +231,56 @@ def large_bench(args):
     out["fp8_over_bf16"] = out["fp8"]["images_per_s"] / out["bf16"]["images_per_s"]
     out["fp8_vs_bf16_max_rel_l2"] = float(rel.max())
     return out
+
+
+def train_bench(args):
+    """Training step at 64 x 64, M/N = 0.25 (M = 1024), batch 256, bf16 compute with
+    float32 masters: forward (activations saved) + MSE loss + backward (conv
+    dgrad/wgrad, ReLU masks, FC weight gradient) + SGD with momentum."""
+    import numpy as np
+    import torch
+    from paper_1701_03891_gb300 import deepinv, synth
+    n, B, ratio = 64, 256, 0.25
+    N = n * n
+    M = synth.m_for_ratio(ratio, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    params = synth.he_params(seed=1)
+    x = synth.voronoi_images(B, n, n, seed=7)
+    net = deepinv.Net(phi, params, n, n, prec="bf16", train_fc=True)
+    net.reserve(B)
+    xd = torch.from_numpy(x).cuda()
+    yd = net.measure(xd)
+    xh = torch.empty((B, N), device="cuda")
+    saved = net.new_saved(B)
+    grads = net.grad_buffers()
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        net.forward(yd, out=xh, saved=saved)
+        if ev: ev[1].record(stream)
+        loss, dW, db, dWfc = net.backward(yd, xd, saved, grads=grads)
+        if ev: ev[2].record(stream)
+        net.sgd_momentum(dW, db, dWfc, lr=1e-4, mu=0.9)
+        if ev: ev[3].record(stream)
+        return loss
+
+    losses = [float(step()) for _ in range(2)]
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.train_steps)]
+    for k in range(args.train_steps):
+        loss = step(evs[k])
+    torch.cuda.synchronize()
+    losses.append(float(loss))
+    fwd = np.mean([e[0].elapsed_time(e[1]) for e in evs])
+    bwd = np.mean([e[1].elapsed_time(e[2]) for e in evs])
+    upd = np.mean([e[2].elapsed_time(e[3]) for e in evs])
+    tot = np.mean([e[0].elapsed_time(e[3]) for e in evs])
+    net.close()
+    return {"workload": "training step 64x64, M/N=0.25 (M=%d), batch %d, bf16 compute, fp32 masters, FC trained" % (M, B),
+            "images_per_s": B / (tot / 1000.0), "ms_per_step": tot,
+            "phase_ms": {"forward_saved": fwd, "loss_and_backward": bwd, "sgd_momentum": upd},
+            "loss_first": losses[0], "loss_last": losses[-1]}
 
 
 SERVE_SIZES = (32, 64, 128)
@@ -460,6 +512,9 @@ def run_native(args):
     large = None
     if rank == 0 and not args.no_large:
         large = large_bench(args)
+    train = None
+    if rank == 0 and not args.no_train:
+        train = train_bench(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -475,7 +530,7 @@ def run_native(args):
             "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
-            "e2e": e2e, "serving": serving, "large_256": large, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)

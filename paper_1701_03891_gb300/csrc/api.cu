@@ -91,6 +91,7 @@ struct deepinv_net {
     bf16* w3p = nullptr;
     bf16* w2t = nullptr;        // conv2 input-gradient weights (flipped, transposed)
     bf16* w3t = nullptr;        // conv3 input-gradient weights
+    bf16* w1t = nullptr;        // conv1 input-gradient weights
     // e4m3 conv2: weights, per-filter scales, calibrated activation scale
     uint8_t* w2q = nullptr;
     float* sw = nullptr;        // [32] weight scales
@@ -304,7 +305,7 @@ int repack(deepinv_net* n, cudaStream_t st)
     if (!n->tc) return DEEPINV_OK;
     const int N = n->N, M = n->d.M;
     DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[2], n->w1p, n->w2p, n->w3p, st));
-    if (n->w2t) DI_TRY(pack_dgrad_weights(n->w[1], n->w[2], n->w2t, n->w3t, st));
+    if (n->w2t) DI_TRY(pack_dgrad_weights(n->w[0], n->w[1], n->w[2], n->w1t, n->w2t, n->w3t, st));
     if (n->fp8) {
         DI_TRY(pack_w2_e4m3(n->w[1], n->amax_w, n->w2q, n->sw, st));
         if (n->calibrated) DI_TRY(e4m3_scales(n->amax_a1, n->sw, n->inv_sa, n->oscale, st));
@@ -336,6 +337,7 @@ void free_net(deepinv_net* n)
     cudaFree(n->sw);
     cudaFree(n->w2t);
     cudaFree(n->w3t);
+    cudaFree(n->w1t);
     cudaFree(n->ws);
     cudaFree(n->bws);
     for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
@@ -460,7 +462,8 @@ struct BwdWs {
     bf16 *g3p, *g2, *g1;  // gradient planes (zero borders)
     float* part2;         // conv2 weight-gradient partials
     double *acc, *bpart, *lpart;
-    float *g1f, *dxt, *wt;  // train_fc: conv1 input gradient on CUDA cores
+    float *T, *dxt;         // train_fc: conv1 input gradient (row sums, result)
+    bf16 *dxp, *ypk;        // train_fc: packed operands of the FC weight gradient
     size_t bytes;
 };
 
@@ -474,14 +477,17 @@ BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
     w.g2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
     w.g1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
     w.g3 = a.take<float>((size_t)B * N);
-    w.part2 = a.take<float>(wgrad2_scratch_floats());
+    w.part2 = a.take<float>(wgrad2_scratch_floats() > tapwgrad_scratch_floats() ? wgrad2_scratch_floats()
+                                                                                 : tapwgrad_scratch_floats());
     w.acc = a.take<double>(64 * 121);
     w.bpart = a.take<double>((size_t)B * 64);
     w.lpart = a.take<double>(kLossBlocks);
     if (n->d.train_fc) {
-        w.g1f = a.take<float>((size_t)B * 64 * N);
+        const int Kb = (B + 15) / 16 * 16, M = n->d.M;
+        w.T = a.take<float>(conv3_scratch_elems(g, B));
         w.dxt = a.take<float>((size_t)B * N);
-        w.wt = a.take<float>(64 * 121);
+        w.dxp = a.take<bf16>(packed_elems(N, 128, Kb));
+        w.ypk = a.take<bf16>(packed_elems(M, gemm_nb(M), Kb));
     }
     w.bytes = align_up(a.off, 256);
     return w;
@@ -517,19 +523,22 @@ int backward_tc(deepinv_net* n, const float* y, const float* x, int B, const Sav
     DI_TRY(grad_plane(w.g3, B, g, w.g3p, st));
     // conv3: bias and weight gradients, input gradient times [a2 > 0] -> g2
     DI_TRY(plane_channel_sums(w.g3p, B, 1, g, w.bpart, db[2], st));
-    DI_TRY(small_wgrad(false, w.g3p, sv.a2, B, g, w.acc, dW[2], st));
+    DI_TRY(tap_wgrad_tc(false, w.g3p, sv.a2, B, g, w.part2, dW[2], nullptr, status, st));
     DI_TRY(conv3_dgrad_tc(w.g3p, B, g, n->w3t, sv.a2, w.g2, status, st));
     // conv2
     DI_TRY(plane_channel_sums(w.g2, B, 32, g, w.bpart, db[1], st));
     DI_TRY(wgrad2_tc(w.g2, sv.a1, B, g, w.part2, dW[1], status, st));
     DI_TRY(conv2_dgrad_tc(w.g2, B, g, n->w2t, sv.a1, w.g1, n->num_sms, status, st));
     // conv1
-    DI_TRY(plane_channel_sums(w.g1, B, 64, g, w.bpart, db[0], st));
-    DI_TRY(small_wgrad(true, w.g1, sv.xt, B, g, w.acc, dW[0], st));
+    DI_TRY(tap_wgrad_tc(true, sv.xt, w.g1, B, g, w.part2, dW[0], db[0], status, st));
     if (n->d.train_fc) {
-        DI_TRY(plane_to_nchw(w.g1, B, 64, g, w.g1f, st));
-        DI_TRY(conv_dgrad_f32(w.g1f, B, 64, H, W, n->w[0], 1, n->d.k, w.wt, w.dxt, st));
-        DI_TRY(sgemm(N, M, B, w.dxt, 1, N, y, M, 1, dWfc, M, st));
+        // dx~ = conv1's input gradient, then dWfc[j][i] = sum_b dx~[b][j] y[b][i]
+        // on the tensor cores with K = the batch
+        DI_TRY(conv1_dgrad_tc(w.g1, B, g, n->w1t, w.T, w.dxt, status, st));
+        const int Kb = (B + 15) / 16 * 16, NB = gemm_nb(M);
+        DI_TRY(pack_kmajor(w.dxt, 1, N, N, B, 128, Kb, w.dxp, st));
+        DI_TRY(pack_kmajor(y, 1, M, M, B, NB, Kb, w.ypk, st));
+        DI_TRY(tc_gemm(w.dxp, w.ypk, Kb, N, M, NB, GEMM_OUT_F32, dWfc, M, nullptr, g, status, st));
     }
     return DEEPINV_OK;
 }
@@ -692,6 +701,7 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
         if (!n->fp8) {
             DI_STEP(dev_alloc(&n->w2t, kW2PackElems));
             DI_STEP(dev_alloc(&n->w3t, kW3tPackElems));
+            DI_STEP(dev_alloc(&n->w1t, kW1tPackElems));
         }
         if (n->fp8) {
             DI_STEP(dev_alloc(&n->w2q, kW2E4M3Bytes));

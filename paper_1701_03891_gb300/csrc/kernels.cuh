@@ -73,8 +73,14 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
 int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
                    int* status, cudaStream_t st);
 constexpr size_t kW3tPackElems = 16 * 32 * 8;          // conv3 input-gradient weights [16][32][8]
-// w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
-int pack_dgrad_weights(const float* w2, const float* w3, bf16* w2t, bf16* w3t, cudaStream_t st);
+constexpr size_t kW1tPackElems = 11 * 4 * 2 * 16 * 8;  // conv1 input-gradient weights [dx][4][2][16][8]
+// w1t, w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
+int pack_dgrad_weights(const float* w1, const float* w2, const float* w3, bf16* w1t, bf16* w2t, bf16* w3t,
+                       cudaStream_t st);
+// Input gradient of conv1 (for training the FC layer): g1 plane -> row sums T
+// (scratch, conv3_scratch_elems) -> dxt [B][N] float32.
+int conv1_dgrad_tc(const bf16* g1, int B, const Geo& g, const bf16* w1t, float* T, float* dxt, int* status,
+                   cudaStream_t st);
 // g [B][N] float32 -> data positions of the one-channel plane gp (pads untouched).
 int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st);
 // Channel sums of a bf16 plane (bias gradients): part [B][C] float64 scratch, out [C].
@@ -84,6 +90,12 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 // float64 scratch of O * I * 121.
 int small_wgrad(bool conv1, const bf16* G, const bf16* A, int B, const Geo& g, double* acc, float* dw,
                 cudaStream_t st);
+// conv1 (conv1 = true: S = x~ plane, C = g1 plane; also db = conv1's bias
+// gradient) or conv3 (S = x^ gradient plane, C = a2 plane; db unused) weight
+// gradient on the tensor cores; part is float32 scratch of tapwgrad_scratch_floats().
+size_t tapwgrad_scratch_floats();
+int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, float* part, float* dw, float* db,
+                 int* status, cudaStream_t st);
 // conv2 weight gradient on the tensor cores: g2 plane [B][4][plane][8] and a1
 // plane [B][8][plane][8] -> dw [32][64][11][11]; part is float32 scratch of
 // wgrad2_scratch_floats().

@@ -29,13 +29,24 @@ inline int grid_for(long long n, int threads = 256)
 // 16, value W2[co][ci][10 - dy'][10 - dx'] (zero for dx' = 11).
 // conv3 input-gradient weights (conv1<32> layout): row n = ci, K = tap
 // t = 11 dy' + dx' (t >= 121 zero), value W3[0][ci][10 - dy'][10 - dx'].
-__global__ void pack_dgrad_weights_kernel(const float* __restrict__ w2, const float* __restrict__ w3,
+// conv1 input-gradient weights (conv3_rows<64> layout): block (dx', kk) holds
+// rows n = dy' (zero for dy' >= 11), K = filters 16 kk .. 16 kk + 15, value
+// W1[co][0][10 - dy'][10 - dx'].
+__global__ void pack_dgrad_weights_kernel(const float* __restrict__ w1, const float* __restrict__ w2,
+                                          const float* __restrict__ w3, bf16* __restrict__ w1t,
                                           bf16* __restrict__ w2t, bf16* __restrict__ w3t)
 {
-    const long long n2 = kW2PackElems, n3 = kW3tPackElems;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2 + n3;
+    const long long n2 = kW2PackElems, n3 = kW3tPackElems, n1 = kW1tPackElems;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2 + n3 + n1;
          i += (long long)gridDim.x * blockDim.x) {
-        if (i < n2) {
+        if (i >= n2 + n3) {
+            const long long j = i - n2 - n3;
+            const int e = (int)(j % 8), n = (int)((j / 8) % 16), half = (int)((j / (8 * 16)) % 2);
+            const int kk = (int)((j / (8 * 16 * 2)) % 4), dx = (int)(j / (8 * 16 * 2 * 4));
+            const int co = kk * 16 + half * 8 + e;
+            const float v = n < 11 ? w1[(co * 11 + (10 - n)) * 11 + (10 - dx)] : 0.f;
+            w1t[j] = __float2bfloat16_rn(v);
+        } else if (i < n2) {
             const int e = (int)(i % 8);
             const int m = (int)((i / 8) % 128);
             const int half = (int)((i / (8 * 128)) % 2);
@@ -68,37 +79,39 @@ __global__ void grad_plane_kernel(const float* __restrict__ g, int B, int H, int
 }
 
 // Per-image channel sums of a chunked bf16 plane [B][C/8][plane][8] (C % 8 == 0)
-// or of a one-channel plane (C == 1): part[b][c] in float64.
+// or of a one-channel plane (C == 1): part[b][c] in float64.  One block per
+// (image, 8-channel chunk); float32 per thread, float64 across threads.
 __global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_len, double* __restrict__ part)
 {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, ch = blockIdx.y;
     const int nch = C == 1 ? 1 : C / 8;
-    __shared__ double red[8][64];
-    for (int k = threadIdx.x; k < 8 * 64; k += blockDim.x) red[k / 64][k % 64] = 0.0;
-    __syncthreads();
-    for (int ch = 0; ch < nch; ++ch) {
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (C == 1) {
-            for (int p = threadIdx.x; p < plane_len; p += blockDim.x)
-                acc[0] += (double)__bfloat162float(src[(size_t)b * plane_len + p]);
-        } else {
-            const uint4* s4 = reinterpret_cast<const uint4*>(src + (((size_t)b * nch + ch) * plane_len) * 8);
-            for (int p = threadIdx.x; p < plane_len; p += blockDim.x) {
-                const uint4 u = s4[p];
-                const bf16* v = reinterpret_cast<const bf16*>(&u);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (C == 1) {
+        for (int p = threadIdx.x; p < plane_len; p += blockDim.x)
+            acc[0] += __bfloat162float(src[(size_t)b * plane_len + p]);
+    } else {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src + (((size_t)b * nch + ch) * plane_len) * 8);
+        for (int p = threadIdx.x; p < plane_len; p += blockDim.x) {
+            const uint4 u = s4[p];
+            const bf16* v = reinterpret_cast<const bf16*>(&u);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) acc[e] += (double)__bfloat162float(v[e]);
-            }
-        }
-        for (int e = 0; e < 8; ++e) {
-            double t = acc[e];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if ((threadIdx.x & 31) == 0) atomicAdd(&red[e][ch], t);   // shared-memory add of warp totals
+            for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(v[e]);
         }
     }
+    __shared__ double red[8][8];
+    const int w = threadIdx.x / 32;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        double t = acc[e];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[w][e] = t;
+    }
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x)
-        part[(size_t)b * C + c] = C == 1 ? red[0][0] : red[c % 8][c / 8];
+    if (threadIdx.x < (C == 1 ? 1 : 8)) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += red[k][threadIdx.x];
+        part[(size_t)b * C + (C == 1 ? 0 : ch * 8 + threadIdx.x)] = t;
+    }
 }
 
 // out[c] = sum_b part[b][c] in a fixed order.
@@ -341,11 +354,164 @@ __global__ void wgrad2_reduce_kernel(const float* __restrict__ part, float* __re
     }
 }
 
+
+// ---------------------------------------------------------------- conv1 / conv3 weight gradients
+// D[t][j] = sum_u S[u + sgn off(t)] C[u][j], off(t) = (dy - 5) P + (dx - 5) for
+// tap t = 11 dy + dx, over the data positions u of every image:
+//   conv1: S = x~ plane, sgn = +1, C = g1 plane (64 ch):  dW1[j][0][t] = D[t][j]
+//   conv3: S = x^ gradient plane, sgn = -1, C = a2 plane (32 ch): dW3[0][j][t] = D[t][j]
+// MMAs with M = 128 taps (rows >= 121 zero; with sgn = +1 row 127 is all ones,
+// giving sum_u C[u][j], conv1's bias gradient), N = CJ channels, K = 16
+// positions.  A is an im2col of S built in shared memory (K-major); B is the C
+// plane itself (MN-major, bulk-copied).  Each CTA covers a run of 128-position
+// blocks, keeps its sum in TMEM and leaves a float32 partial.
+constexpr int kTwKB = 128;
+constexpr int kTwCtas = 456;          // 3 per SM
+
+struct TwSmem {
+    uint64_t lbar, mbar;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+template <int CJ, int SGN>
+__global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ S, const bf16* __restrict__ C,
+                                                       int B, int P, int HP16, int plane_len,
+                                                       float* __restrict__ part, int* status)
+{
+    constexpr uint32_t ABYTES = (kTwKB / 8) * 128 * 16;   // [16 chunks][128 rows][8]
+    constexpr uint32_t BBYTES = (CJ / 8) * kTwKB * 16;    // [CJ/8 groups][128 positions][8]
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sA = smem_raw;
+    uint8_t* sB = smem_raw + ABYTES;
+    const int wlen = (kTwKB + 10 * P + 10 + 7) / 8 * 8;
+    bf16* sS = reinterpret_cast<bf16*>(sB + BBYTES);
+    TwSmem* ss = reinterpret_cast<TwSmem*>(sB + BBYTES + wlen * 2);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nb_img = (HP16 + kTwKB - 1) / kTwKB;
+    const long long total = (long long)B * nb_img;
+    const long long blk0 = total * blockIdx.x / gridDim.x, blk1 = total * (blockIdx.x + 1) / gridDim.x;
+    const int u_begin = kPad * P + kPad;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&ss->lbar), 1);
+        mbar_init(smem_u32(&ss->mbar), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&ss->tmem_base), CJ < 32 ? 32 : CJ);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+    const int t = threadIdx.x;                                  // im2col row = tap
+    const int dy = t / 11, dx = t % 11;
+    const int base_t = SGN * ((dy - 5) * P + (dx - 5)) + 5 * P + 5;   // window index of position 0
+    bool ok = true;
+    int n = 0;
+    for (long long k = blk0; k < blk1 && ok; ++k, ++n) {
+        const int b = (int)(k / nb_img);
+        const int u0 = u_begin + (int)(k % nb_img) * kTwKB;
+        const int npos = min(kTwKB, u_begin + HP16 - u0);
+        if (threadIdx.x == 0) {
+            // the previous block's MMAs must be done before its operands are overwritten
+            if (n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag);
+            if (ok) {
+                const uint32_t bar = smem_u32(&ss->lbar);
+                // the part of the window this block reads (stays inside the plane for the last block)
+                const int wcopy = (npos + 10 * P + 10 + 7) / 8 * 8;
+                mbar_arrive_expect_tx(bar, (uint32_t)wcopy * 2 + (CJ / 8) * npos * 16);
+                bulk_g2s(smem_u32(sS), S + (size_t)b * plane_len + u0 - 5 * P - 5, (uint32_t)wcopy * 2, bar);
+                for (int c = 0; c < CJ / 8; ++c)
+                    bulk_g2s(smem_u32(sB + c * kTwKB * 16),
+                             reinterpret_cast<const uint8_t*>(C) + (((size_t)b * (CJ / 8) + c) * plane_len + u0) * 16,
+                             npos * 16, bar);
+                ok = mbar_wait(bar, n & 1, status, &ss->abort_flag);
+            }
+        }
+        __syncthreads();
+        ok = !ss->abort_flag;
+        if (!ok) break;
+        // im2col row t: S at window index base_t + position, 8 positions per chunk
+        const unsigned short* w16 = reinterpret_cast<const unsigned short*>(sS) + base_t;
+        for (int kc = 0; kc < npos / 8; ++kc) {
+            uint32_t u[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+                uint32_t lo, hi;
+                if (t < 121) {
+                    lo = w16[kc * 8 + 2 * e2];
+                    hi = w16[kc * 8 + 2 * e2 + 1];
+                } else {
+                    lo = hi = (SGN > 0 && t == 127) ? 0x3F80u : 0u;   // bf16 1.0 (bias row) or 0
+                }
+                u[e2] = lo | (hi << 16);
+            }
+            reinterpret_cast<uint4*>(sA)[kc * 128 + t] = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(CJ >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+            for (int ks = 0; ks < npos / 16; ++ks) {
+                const uint64_t ad = sdesc(smem_u32(sA + ks * 2 * 2048), 2048, 128);
+                const uint64_t bd = sdesc(smem_u32(sB + ks * 256), 128, kTwKB * 16);
+                mma_bf16(tbase, ad, bd, idesc, (k == blk0 && ks == 0) ? 0u : 1u);
+            }
+            mma_commit(smem_u32(&ss->mbar));
+        }
+    }
+    // wait for the last MMAs, then write this CTA's partial
+    if (threadIdx.x == 0 && n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag) && ok;
+    __syncthreads();
+    tc_fence_after();
+    ok = __all_sync(0xffffffffu, !ss->abort_flag);
+    float* dst = part + ((size_t)blockIdx.x * 128 + warp * 32 + lane) * CJ;
+    for (int c0 = 0; c0 < CJ; c0 += 16) {
+        float v[16];
+        if (ok && n > 0) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c0, v);
+        else
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, CJ < 32 ? 32 : CJ);
+    }
+}
+
+// conv1: dw[j][t] (= [64][1][11][11]) and db[j] from row 127; conv3: dw[j][t] (= [1][32][11][11]).
+template <int CJ>
+__global__ void tapwgrad_reduce_kernel(const float* __restrict__ part, int nctas, float* __restrict__ dw,
+                                       float* __restrict__ db)
+{
+    const int n = CJ * 122;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = i / 122, r = i % 122;
+        const int row = r < 121 ? r : 127;
+        if (r == 121 && !db) continue;
+        double acc = 0.0;
+        for (int c = 0; c < nctas; ++c) acc += (double)part[((size_t)c * 128 + row) * CJ + j];
+        if (r < 121) dw[j * 121 + r] = (float)acc;
+        else db[j] = (float)acc;
+    }
+}
+
 }  // namespace
 
-int pack_dgrad_weights(const float* w2, const float* w3, bf16* w2t, bf16* w3t, cudaStream_t st)
+int pack_dgrad_weights(const float* w1, const float* w2, const float* w3, bf16* w1t, bf16* w2t, bf16* w3t,
+                       cudaStream_t st)
 {
-    pack_dgrad_weights_kernel<<<grid_for((long long)(kW2PackElems + kW3tPackElems)), 256, 0, st>>>(w2, w3, w2t, w3t);
+    pack_dgrad_weights_kernel<<<grid_for((long long)(kW2PackElems + kW3tPackElems + kW1tPackElems)), 256, 0, st>>>(
+        w1, w2, w3, w1t, w2t, w3t);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -360,7 +526,7 @@ int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st)
 
 int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st)
 {
-    plane_sum_kernel<<<B, 256, 0, st>>>(src, C, geo.plane, part);
+    plane_sum_kernel<<<dim3(B, C == 1 ? 1 : C / 8), 256, 0, st>>>(src, C, geo.plane, part);
     DI_LAUNCH_CHECK();
     sum_parts_kernel<<<1, 64, 0, st>>>(part, B, C, out);
     DI_LAUNCH_CHECK();
@@ -402,6 +568,35 @@ int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, 
     wgrad2_kernel<<<kWgQuads * kWgSplit, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, part, status);
     DI_LAUNCH_CHECK();
     wgrad2_reduce_kernel<<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+size_t tapwgrad_scratch_floats() { return (size_t)kTwCtas * 128 * 64; }
+
+int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, float* part, float* dw, float* db,
+                 int* status, cudaStream_t st)
+{
+    const int HP16 = (g.HP + 15) / 16 * 16;
+    const int wlen = (kTwKB + 10 * g.P + 10 + 7) / 8 * 8;
+    const int CJ = conv1 ? 64 : 32;
+    const size_t smem = (size_t)(kTwKB / 8) * 128 * 16 + (size_t)(CJ / 8) * kTwKB * 16 + (size_t)wlen * 2 +
+                        sizeof(TwSmem) + 16;
+    if (smem > 227 * 1024) {
+        set_error("weight gradient: image width %d too large for the shared-memory window", g.W);
+        return DEEPINV_EUNSUPPORTED;
+    }
+    if (conv1) {
+        DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tapwgrad_kernel<64, 1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
+        DI_LAUNCH_CHECK();
+        tapwgrad_reduce_kernel<64><<<grid_for(64 * 122), 256, 0, st>>>(part, kTwCtas, dw, db);
+    } else {
+        DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tapwgrad_kernel<32, -1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
+        DI_LAUNCH_CHECK();
+        tapwgrad_reduce_kernel<32><<<grid_for(32 * 122), 256, 0, st>>>(part, kTwCtas, dw, nullptr);
+    }
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

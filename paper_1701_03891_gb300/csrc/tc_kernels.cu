@@ -798,14 +798,19 @@ struct Conv3Smem {
 };
 constexpr int kConv3Win = 144;      // 128 + 10 positions, rounded up to 16
 
+// CIN = 32: conv3 (input a2).  CIN = 64: the input gradient of conv1 (input
+// the gradient plane of z1, conv1's kernels flipped), needed to train the FC layer.
+template <int CIN>
 __global__ void __launch_bounds__(128) conv3_rows_kernel(const bf16* __restrict__ a2, int plane_len, int t3,
                                                          int tlen, const bf16* __restrict__ w3p,
                                                          float* __restrict__ T, int* status)
 {
+    constexpr int NCH = CIN / 8, KK = CIN / 16;
+    constexpr uint32_t WB = 11 * KK * 512;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* sWin = smem_raw;                         // [4][144][8] bf16 = 9216 B
-    uint8_t* sW = smem_raw + 4 * kConv3Win * 16;      // 11264 B
-    Conv3Smem* ss = reinterpret_cast<Conv3Smem*>(sW + 11264);
+    uint8_t* sWin = smem_raw;                         // [NCH][144][8] bf16
+    uint8_t* sW = smem_raw + NCH * kConv3Win * 16;    // [11][KK][2][16][8] bf16
+    Conv3Smem* ss = reinterpret_cast<Conv3Smem*>(sW + WB);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int b = blockIdx.x / t3, u = blockIdx.x % t3;
     const int p0 = u * 128;
@@ -827,21 +832,21 @@ __global__ void __launch_bounds__(128) conv3_rows_kernel(const bf16* __restrict_
 
     if (threadIdx.x == 0) {
         const uint32_t bar = smem_u32(&ss->bar);
-        mbar_arrive_expect_tx(bar, 4 * kConv3Win * 16 + 11264);
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(a2) + (size_t)b * 4 * plane_len * 16;
-        for (int c = 0; c < 4; ++c)
+        mbar_arrive_expect_tx(bar, NCH * kConv3Win * 16 + WB);
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(a2) + (size_t)b * NCH * plane_len * 16;
+        for (int c = 0; c < NCH; ++c)
             bulk_g2s(smem_u32(sWin + c * kConv3Win * 16), src + ((size_t)c * plane_len + p0) * 16,
                      kConv3Win * 16, bar);
-        bulk_g2s(smem_u32(sW), w3p, 11264, bar);
+        bulk_g2s(smem_u32(sW), w3p, WB, bar);
         if (mbar_wait(bar, 0, status, &ss->abort_flag)) {
             tc_fence_after();
             const uint32_t idesc = idesc_bf16(128, 16);
             for (int dx = 0; dx < 11; ++dx)
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
+                for (int kk = 0; kk < KK; ++kk) {
                     const uint64_t ad = sdesc(smem_u32(sWin + (2 * kk) * kConv3Win * 16 + dx * 16),
                                               kConv3Win * 16, 128);
-                    const uint64_t bd = sdesc(smem_u32(sW + (dx * 2 + kk) * 512), 256, 128);
+                    const uint64_t bd = sdesc(smem_u32(sW + (dx * KK + kk) * 512), 256, 128);
                     mma_bf16(tbase, ad, bd, idesc, (dx | kk) ? 1u : 0u);
                 }
         } else {
@@ -872,7 +877,7 @@ __global__ void conv3_sum_kernel(const float* __restrict__ T, int B, int H, int 
                                  const float* __restrict__ b3, int final_relu, float* __restrict__ xhat)
 {
     const long long n = (long long)B * H * W;
-    const float bias = __ldg(b3);
+    const float bias = b3 ? __ldg(b3) : 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % W);
@@ -1083,12 +1088,27 @@ int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* 
 {
     if (B <= 0) return DEEPINV_OK;
     const size_t smem = 4 * kConv3Win * 16 + 11264 + sizeof(Conv3Smem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int tlen = g.t3 * 128;
-    conv3_rows_kernel<<<B * g.t3, 128, smem, st>>>(a2, g.plane, g.t3, tlen, w3p, T, status);
+    conv3_rows_kernel<32><<<B * g.t3, 128, smem, st>>>(a2, g.plane, g.t3, tlen, w3p, T, status);
     DI_LAUNCH_CHECK();
     const long long n = (long long)B * g.H * g.W;
     conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, B, g.H, g.W, g.P, tlen, b3, final_relu, xhat);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int conv1_dgrad_tc(const bf16* g1, int B, const Geo& g, const bf16* w1t, float* T, float* dxt, int* status,
+                   cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    const size_t smem = 8 * kConv3Win * 16 + 22528 + sizeof(Conv3Smem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int tlen = g.t3 * 128;
+    conv3_rows_kernel<64><<<B * g.t3, 128, smem, st>>>(g1, g.plane, g.t3, tlen, w1t, T, status);
+    DI_LAUNCH_CHECK();
+    const long long n = (long long)B * g.H * g.W;
+    conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, B, g.H, g.W, g.P, tlen, nullptr, 0, dxt);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
