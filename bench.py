@@ -121,6 +121,17 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(dev_ms, per_rank_batch, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput: every rank recovers its own batch (no collective on the data
+    path); the job's time is the slowest rank's.  Returns (max ms over ranks, images/s)."""
+    import torch
+    t = torch.tensor([float(dev_ms)], device=device, dtype=torch.float64)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * per_rank_batch * steps / (ms / 1000.0)
+
+
 def workload(args, rank=0):
     from paper_1701_03891_gb300 import synth
     n = args.size
@@ -451,11 +462,7 @@ def run_native(args):
     stages = net.profile_read()
     net.profile(False)
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms = float(t.item())
-    value = world * B * args.steps / (dev_ms / 1000.0)
+    dev_ms, value = aggregate(dev_ms, B, args.steps, world, dist, device="cuda")
     ms_per_step = dev_ms / args.steps
 
     conv2_ms = stages["conv2"][0] / max(1, stages["conv2"][1])
