@@ -195,6 +195,7 @@ struct FwdWs {
     float *T;
     float *fxt, *fa1, *fa2;
     float *yd, *xd, *xhd;   // device staging of the host-memory entry points
+    float* mpart;           // split-K partials of the measurement GEMM
     size_t bytes;
 };
 
@@ -217,6 +218,7 @@ FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
         w.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
         w.fa2 = a.take<float>((size_t)B * n->d.l2 * N);
     }
+    if (n->tc) w.mpart = a.take<float>((size_t)16 * B * M);   // split-K partials of y = Phi x
     w.yd = a.take<float>((size_t)B * M);
     w.xd = a.take<float>((size_t)B * N);
     w.xhd = a.take<float>((size_t)B * N);
@@ -551,7 +553,11 @@ int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream
     StageTimer t(n, st, DEEPINV_STAGE_MEASURE);
     if (n->tc) {
         const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
-        return measure_bf16_packed(n->msB, n->Kms, n->NBms, x, N, M, B, y, w.xpk, st);
+        int* status = device_status_word();
+        DI_REQUIRE(status, "no device status word");
+        DI_TRY(pack_kmajor(x, N, 1, B, N, 128, n->Kms, w.xpk, st));
+        const int ks = gemm_ksplit(B, M, n->NBms, n->Kms, n->num_sms);
+        return tc_gemm_splitk(w.xpk, n->msB, n->Kms, B, M, n->NBms, y, w.mpart, ks, status, st);
     }
     return sgemm(B, M, N, x, N, 1, n->phi, 1, N, y, M, st);
 }

@@ -52,6 +52,20 @@ enum GemmOut { GEMM_OUT_F32 = 0, GEMM_OUT_PLANE = 1 };
 int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mode, float* out_f32,
             long long ldo, bf16* plane, const Geo& geo, int* status, cudaStream_t st);
 
+// out [Mr][Nc] float32 = A B^T with the K steps split over `ksplit` CTAs per
+// tile; part holds ksplit * Mr * Nc floats of partial sums (summed in order).
+int tc_gemm_splitk(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, float* out, float* part, int ksplit,
+                   int* status, cudaStream_t st);
+// Split that keeps about one wave of CTAs busy for a GEMM with the given tiles.
+inline int gemm_ksplit(int Mr, int Nc, int NB, int Kp, int num_sms)
+{
+    const int tiles = ((Mr + 127) / 128) * ((Nc + NB - 1) / NB);
+    int k = num_sms / (tiles > 0 ? tiles : 1);
+    const int kmax = Kp / 16 / 16;               // at least 16 MMA steps per split
+    if (k > kmax) k = kmax;
+    if (k > 16) k = 16;
+    return k < 1 ? 1 : k;
+}
 // conv1: x~ plane [B][plane] -> a1 (bias, ReLU, zero pad columns), as
 //   kConv1OutBF16: bf16 [B][8][plane][8];
 //   kConv1OutE4M3: e4m3 [B][4][plane][16], values times *inv_sa;

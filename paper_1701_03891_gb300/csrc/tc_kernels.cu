@@ -207,8 +207,13 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int mt = blockIdx.x, nt = blockIdx.y;
-    const int nsteps = Kp / 16;
+    // split-K: this CTA sums MMA steps [s0, s1) of the Kp / 16 and writes slice z
+    const int ksplit = gridDim.z, z = blockIdx.z;
+    const int nsteps_all = Kp / 16;
+    const int s0 = nsteps_all * z / ksplit, s1 = nsteps_all * (z + 1) / ksplit;
+    const int nsteps = s1 - s0;
     const int nstages = (nsteps + kGemmKS - 1) / kGemmKS;
+    if (ksplit > 1) out_f32 += (size_t)z * Mr * ldo;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGemmNS; ++s) {
@@ -238,8 +243,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
         for (int st = 0; st < nstages; ++st) {
             const int slot = st % kGemmNS, n = st / kGemmNS;
             if (!mbar_wait(smem_u32(&ss->empty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) break;
-            const int k0 = st * kGemmKS;
-            const int ks = min(kGemmKS, nsteps - k0);
+            const int k0 = s0 + st * kGemmKS;
+            const int ks = min(kGemmKS, s1 - k0);
             const uint32_t abytes = ks * 4096, bbytes = ks * NB * 32;
             mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), abytes + bbytes);
             armed_parity[slot] = n & 1;
@@ -258,12 +263,12 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
             const int slot = st % kGemmNS, n = st / kGemmNS;
             if (!mbar_wait(smem_u32(&ss->full[slot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const int k0 = st * kGemmKS;
-            const int ks = min(kGemmKS, nsteps - k0);
+            const int k0 = s0 + st * kGemmKS;
+            const int ks = min(kGemmKS, s1 - k0);
             for (int j = 0; j < ks; ++j) {
                 const uint64_t ad = sdesc(smem_u32(sA + slot * a_stage + j * 4096), 2048, 128);
                 const uint64_t bd = sdesc(smem_u32(sB + slot * b_stage + j * NB * 32), NB * 16, 128);
-                mma_bf16(tbase, ad, bd, idesc, (k0 + j) > 0 ? 1u : 0u);
+                mma_bf16(tbase, ad, bd, idesc, (k0 + j) > s0 ? 1u : 0u);
             }
             mma_commit(smem_u32(&ss->empty[slot]));
         }
@@ -280,7 +285,12 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
             const int m = mt * 128 + q * 32 + lane;
             for (int c0 = 0; c0 < NB; c0 += 16) {
                 float v[16];
-                tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (nsteps > 0) {
+                    tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
                 if (m >= Mr) continue;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -910,6 +920,16 @@ __global__ void plane_to_nchw_kernel(const bf16* __restrict__ src, int B, int C,
     }
 }
 
+// y[m][n] = sum_z part[z][m][n] (fixed order) for the split-K GEMM.
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, long long n, float* __restrict__ y)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < ksplit; ++z) s += part[(size_t)z * n + i];
+        y[i] = s;
+    }
+}
+
 inline int grid1d(long long n, int threads = 256)
 {
     long long b = (n + threads - 1) / threads;
@@ -938,6 +958,29 @@ int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w
 {
     const long long n = (long long)(kW1PackElems + kW2PackElems + kW3PackElems);
     pack_conv_weights_kernel<<<grid1d(n), 256, 0, st>>>(w1, w2, w3, w1p, w2p, w3p);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int tc_gemm_splitk(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, float* out, float* part, int ksplit,
+                   int* status, cudaStream_t st)
+{
+    if (Mr <= 0 || Nc <= 0) return DEEPINV_OK;
+    if (ksplit <= 1 || !part) return tc_gemm(A, B, Kp, Mr, Nc, NB, GEMM_OUT_F32, out, Nc, nullptr, Geo{}, status, st);
+    if (NB < 16 || NB > 256 || NB % 16 || Kp % 16 || Kp <= 0) {
+        set_error("tc_gemm_splitk: bad tile N=%d or K=%d", NB, Kp);
+        return DEEPINV_EINVAL;
+    }
+    uint32_t cols = 32;
+    while (cols < (uint32_t)NB) cols <<= 1;
+    const size_t smem = (size_t)kGemmNS * (kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
+    dim3 grid(cdiv(Mr, 128), cdiv(Nc, NB), ksplit);
+    DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc_gemm_kernel<GEMM_OUT_F32><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, part, Nc, nullptr, 0, 0, 0, 0,
+                                                          status);
+    DI_LAUNCH_CHECK();
+    const long long n = (long long)Mr * Nc;
+    splitk_reduce_kernel<<<grid1d(n), 256, 0, st>>>(part, ksplit, n, out);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
