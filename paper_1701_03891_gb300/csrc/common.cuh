@@ -94,7 +94,7 @@ static inline Geo make_geo(int H, int W)
     size_t need = 0;
     auto upd = [&](size_t v) { if (v > need) need = v; };
     upd((size_t)(g.t2 - 1) * kConv2Valid + (size_t)g.nslab * kSlabPx);     // conv2 window
-    upd((size_t)g.t1 * 128 + (size_t)kConv2Reach * g.P + 16);              // conv1 im2col window
+    upd((size_t)g.t1 * 128 + (size_t)kConv2Reach * g.P + 24);              // conv1 expanded window
     upd((size_t)g.t3 * 128 + 16);                                          // conv3 window
     upd((size_t)(H + 2 * kPad) * g.P + 2 * kPad);                          // data + borders
     upd((size_t)g.HP + (size_t)kConv2Reach * g.P + 48);                     // conv2 weight-gradient windows

@@ -37,7 +37,7 @@ int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int 
                 bf16* dst, cudaStream_t st);
 
 // Weight layouts of the paper network (l1 = 64, l2 = 32, l3 = 1, k = 11).
-constexpr size_t kW1PackElems = 16 * 64 * 8;             // [16 chunks][64 rows][8]
+constexpr size_t kW1PackElems = 11 * 2 * 64 * 8;         // [dy][h][64 rows][8]
 constexpr size_t kW2PackElems = 11 * 3 * 4 * 2 * 128 * 8;  // [dy][s][kk][2][128][8]
 constexpr size_t kW3PackElems = 11 * 2 * 2 * 16 * 8;     // [dx][kk][2][16][8]
 int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p,
@@ -86,7 +86,7 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
                    cudaStream_t st);
 int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
                    int* status, cudaStream_t st);
-constexpr size_t kW3tPackElems = 16 * 32 * 8;          // conv3 input-gradient weights [16][32][8]
+constexpr size_t kW3tPackElems = 11 * 2 * 32 * 8;      // conv3 input-gradient weights [dy'][h][32][8]
 constexpr size_t kW1tPackElems = 11 * 4 * 2 * 16 * 8;  // conv1 input-gradient weights [dx][4][2][16][8]
 // w1t, w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
 int pack_dgrad_weights(const float* w1, const float* w2, const float* w3, bf16* w1t, bf16* w2t, bf16* w3t,

@@ -27,8 +27,9 @@ inline int grid_for(long long n, int threads = 256)
 // conv2 input-gradient weights: block (dy', s) holds rows m = 64 g + ci
 // (g = tap slot, dx' = 2 s + g), K = the 32 output channels in two chunks of
 // 16, value W2[co][ci][10 - dy'][10 - dx'] (zero for dx' = 11).
-// conv3 input-gradient weights (conv1<32> layout): row n = ci, K = tap
-// t = 11 dy' + dx' (t >= 121 zero), value W3[0][ci][10 - dy'][10 - dx'].
+// conv3 input-gradient weights (conv1<32> layout): block (dy', h) holds rows
+// n = ci, K = columns dx' = 8 h .. 8 h + 7 (zero for dx' >= 11), value
+// W3[0][ci][10 - dy'][10 - dx'].
 // conv1 input-gradient weights (conv3_rows<64> layout): block (dx', kk) holds
 // rows n = dy' (zero for dy' >= 11), K = filters 16 kk .. 16 kk + 15, value
 // W1[co][0][10 - dy'][10 - dx'].
@@ -58,9 +59,9 @@ __global__ void pack_dgrad_weights_kernel(const float* __restrict__ w1, const fl
             w2t[i] = __float2bfloat16_rn(v);
         } else {
             const long long j = i - n2;
-            const int e = (int)(j % 8), ci = (int)((j / 8) % 32), kc = (int)(j / (8 * 32));
-            const int t = kc * 8 + e;
-            const float v = t < 121 ? w3[(ci * 11 + (10 - t / 11)) * 11 + (10 - t % 11)] : 0.f;
+            const int e = (int)(j % 8), ci = (int)((j / 8) % 32), blk = (int)(j / (8 * 32));
+            const int dy = blk / 2, dx = (blk % 2) * 8 + e;
+            const float v = dx < 11 ? w3[(ci * 11 + (10 - dy)) * 11 + (10 - dx)] : 0.f;
             w3t[j] = __float2bfloat16_rn(v);
         }
     }

@@ -82,7 +82,8 @@ __global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, 
     }
 }
 
-// conv1 B operand: (n = filter co, k = tap t = 11 dy + dx), t >= 121 zero.
+// conv1 B operand: block (dy, h) holds rows n = filter co, K = columns
+//   dx = 8 h .. 8 h + 7, weight W1[co][0][dy][dx] (zero for dx >= 11).
 // conv2 A operand: block (dy, s, kk) holds rows m = 32 g + co (g = tap slot),
 //   K = input channels 16 kk .. 16 kk + 15, weight W2[co][ci][dy][4 s + g]
 //   (zero when 4 s + g = 11).
@@ -96,9 +97,9 @@ __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const flo
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n1 + n2 + n3;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < n1) {
-            const int e = (int)(i % 8), co = (int)((i / 8) % 64), kc = (int)(i / (8 * 64));
-            const int t = kc * 8 + e;
-            const float v = t < 121 ? w1[co * 121 + t] : 0.f;
+            const int e = (int)(i % 8), co = (int)((i / 8) % 64), blk = (int)(i / (8 * 64));
+            const int dy = blk / 2, dx = (blk % 2) * 8 + e;
+            const float v = dx < 11 ? w1[co * 121 + dy * 11 + dx] : 0.f;
             w1p[i] = __float2bfloat16_rn(v);
         } else if (i < n1 + n2) {
             const long long j = i - n1;
@@ -313,49 +314,146 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
     }
 }
 
+// Named barrier of the 128 epilogue threads (warps of one role).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 // ---------------------------------------------------------------- conv1
-// One CTA per 128 output positions of one image; 4 warps.  The im2col A
-// operand (128 positions x 128 taps, taps >= 121 zero) is built in shared
-// memory from the proxy window; B = the 64 filters (resident, 16 KB).
+// Correlating one input channel with 11 x 11 kernels is, per kernel row dy, a
+// GEMM with K = the 11 columns dx (padded to 16, weights of dx >= 11 zero).
+// Its A operand (position m, column dx) = x~[q0 + m + dy P + dx] is read by
+// the tensor core straight from an expanded window: row i of the window holds
+// the 8 consecutive plane values x~[base + i .. base + i + 7], so the MN-major
+// core matrix (K group h, M group mg) of kernel row dy is the 8 rows starting
+// at dy P + 8 h + 8 mg; both core-matrix strides are 128 bytes and no im2col
+// is built.  One piece of kC1Rows window rows per kernel row.
+//
+// Persistent CTAs over tiles of 128 positions, 13 warps: warps 8..11 expand
+// the window of the next tile into a 2-stage ring; warp 12 owns TMEM (2
+// accumulators) and one of its threads issues the 11 MMAs per tile; warps
+// 0..7 drain an accumulator, warp w reading TMEM lane quarter w % 4 (32
+// positions) and half w / 4 of the channels.  Each epilogue warp applies
+// bias/ReLU (or the mode's transform) and stores its 32 positions straight to
+// the output planes (one 512-byte run per channel chunk and warp), so the
+// epilogue warps never wait on one another.
+constexpr int kC1Rows = 144;                 // 8-value rows per piece (136 read + alignment)
+constexpr int kC1Stride = kC1Rows + 1;       // piece stride in 16-byte rows (staggers banks)
+constexpr int kC1Groups = kC1Rows / 8;       // 8-row groups per piece
+constexpr int kC1Items = 11 * kC1Groups;     // groups per tile window
+constexpr int kC1PerThread = (kC1Items + 127) / 128;
+constexpr uint32_t kC1XBytes = 11 * kC1Stride * 16;
+constexpr int kC1Threads = 416;
+
 struct Conv1Smem {
-    uint64_t wbar, mbar;
+    alignas(16) float bias[64];   // read as float4
+    uint64_t wbar;
+    uint64_t xfull[2], xempty[2];
+    uint64_t afull[2], aempty[2];
+    uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
-    float bias[64];
 };
+
+__host__ __device__ constexpr uint32_t conv1_wbytes(int cout) { return 11u * 2u * cout * 16u; }
+// 16-byte output chunks per position
+__host__ __device__ constexpr int conv1_out_chunks(int cout, int mode)
+{
+    return mode == kConv1OutE4M3 ? cout / 16 : (mode == kConv1AmaxOnly ? 0 : cout / 8);
+}
+__host__ __device__ constexpr size_t conv1_smem_bytes(int cout)
+{
+    return conv1_wbytes(cout) + 2 * (size_t)kC1XBytes + sizeof(Conv1Smem) + 16;
+}
+
+// Window of tile (b, q0): piece dy starts at the 8-aligned plane index
+// a = (q0 + dy P) & ~7, group j of it (rows 8 j .. 8 j + 7) comes from the 16
+// values x~[a + 8 j .. a + 8 j + 15] (two aligned 16-byte loads; the plane
+// holds at least t1 * 128 + 10 P + 24 values); row k of the group is values
+// k .. k + 7 of those 16.  Items run dy-fastest so that the 8 lanes of one
+// store phase mostly hit different banks.
+__device__ __forceinline__ void conv1_load(const bf16* __restrict__ img, int q0, int P, int pt, uint4* lo, uint4* hi)
+{
+#pragma unroll
+    for (int r = 0; r < kC1PerThread; ++r) {
+        const int it = pt + r * 128;
+        if (it < kC1Items) {
+            const int dy = it % 11, j = it / 11;
+            const uint4* src = reinterpret_cast<const uint4*>(img + ((q0 + dy * P) & ~7) + 8 * j);
+            lo[r] = __ldg(src);
+            hi[r] = __ldg(src + 1);
+        }
+    }
+}
+
+__device__ __forceinline__ void conv1_expand(uint4* sx, int pt, const uint4* lo, const uint4* hi)
+{
+#pragma unroll
+    for (int r = 0; r < kC1PerThread; ++r) {
+        const int it = pt + r * 128;
+        if (it < kC1Items) {
+            const int dy = it % 11, j = it / 11;
+            const uint32_t w[8] = {lo[r].x, lo[r].y, lo[r].z, lo[r].w, hi[r].x, hi[r].y, hi[r].z, hi[r].w};
+            uint4* dst = sx + dy * kC1Stride + 8 * j;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    o[e] = (k & 1) ? __byte_perm(w[k / 2 + e], w[k / 2 + e + 1], 0x5432) : w[k / 2 + e];
+                dst[k] = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+}
+
+// Tiles [lo, hi) of CTA `cta` out of `ncta`: contiguous, so that the image and
+// tile index of successive tiles advance without divisions.
+struct TileRange {
+    int lo, hi;
+};
+__device__ __forceinline__ TileRange tile_range(int ntiles, int cta, int ncta)
+{
+    return {(int)((long long)ntiles * cta / ncta), (int)((long long)ntiles * (cta + 1) / ncta)};
+}
 
 // COUT = 64: conv1 itself.  COUT = 32 with mode kConv1GradMask: the input
 // gradient of conv3 (one input channel, the gradient plane of x^, correlated
 // with conv3's flipped kernels), times the ReLU mask of a2.
 template <int COUT>
-__global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt, int H, int W, int P,
-                                                    int plane_len, int t1, const bf16* __restrict__ w1p,
-                                                    const float* __restrict__ b1, void* __restrict__ a1, int mode,
-                                                    const float* __restrict__ inv_sa, float* __restrict__ amax,
-                                                    const bf16* __restrict__ mask_src, int* status)
+__global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __restrict__ xt, int B, int H, int W,
+                                                              int P, int plane_len, int t1,
+                                                              const bf16* __restrict__ w1p,
+                                                              const float* __restrict__ b1, void* __restrict__ a1,
+                                                              int mode, const float* __restrict__ inv_sa,
+                                                              float* __restrict__ amax,
+                                                              const bf16* __restrict__ mask_src, int* status)
 {
-    constexpr uint32_t BBYTES = 16 * COUT * 16;   // [16 chunks][COUT rows][8]
+    constexpr uint32_t BBYTES = conv1_wbytes(COUT);
+    constexpr int CPW = COUT / 2;                             // channels per epilogue warp
+    constexpr uint32_t TCOLS = 2 * COUT < 32 ? 32 : 2 * COUT;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sB = smem_raw;
-    uint8_t* sA = smem_raw + BBYTES;        // 32 KB
-    bf16* sWin = reinterpret_cast<bf16*>(smem_raw + BBYTES + 32768);
-    const int winx = (128 + kConv2Reach * P + 10 + 7) / 8 * 8;
-    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + BBYTES + 32768 + winx * 2);
+    uint4* sX = reinterpret_cast<uint4*>(smem_raw + BBYTES);                       // [2][11][kC1Stride]
+    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + BBYTES + 2 * kC1XBytes);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int b = blockIdx.x / t1, t = blockIdx.x % t1;
-    const int q0 = t * 128;
     const int HP = H * P;
+    const int ntiles = B * t1;
 
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&ss->wbar), 1);
-        mbar_init(smem_u32(&ss->mbar), 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&ss->xfull[s]), 128);
+            mbar_init(smem_u32(&ss->xempty[s]), 1);
+            mbar_init(smem_u32(&ss->afull[s]), 1);
+            mbar_init(smem_u32(&ss->aempty[s]), 8);
+        }
+        mbar_init(smem_u32(&ss->drain), 1);
         ss->abort_flag = 0;
         fence_mbar_init();
     }
     if (threadIdx.x < 64) ss->bias[threadIdx.x] = (b1 && threadIdx.x < COUT) ? __ldg(&b1[threadIdx.x]) : 0.f;
-    if (warp == 0) {
-        tmem_alloc(smem_u32(&ss->tmem_base), COUT < 32 ? 32 : COUT);
+    if (warp == 12) {
+        tmem_alloc(smem_u32(&ss->tmem_base), TCOLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -363,106 +461,145 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
 
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(smem_u32(&ss->wbar), BBYTES);
-        bulk_g2s(smem_u32(sB), w1p, BBYTES, smem_u32(&ss->wbar));
-    }
-    // proxy window -> shared memory (16-byte vectors; the plane is 16-byte aligned)
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(xt + (size_t)b * plane_len + q0);
-        uint4* dst = reinterpret_cast<uint4*>(sWin);
-        for (int i = threadIdx.x; i < winx / 8; i += 128) dst[i] = src[i];
-    }
-    __syncthreads();
-    // im2col: thread m builds row m (position q0 + m) of all 16 chunks; chunk kc
-    // holds taps 8 kc .. 8 kc + 7 (tap t = 11 dy + dx, taps >= 121 zero),
-    // copied as raw bf16 bits.
-    {
-        const int m = threadIdx.x;
-        const unsigned short* w16 = reinterpret_cast<const unsigned short*>(sWin) + m;
-#pragma unroll
-        for (int kc = 0; kc < 16; ++kc) {
-            uint32_t u[4];
-#pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-                const int t0 = kc * 8 + 2 * e2, t1 = t0 + 1;
-                const uint32_t lo = t0 < 121 ? w16[(t0 / 11) * P + t0 % 11] : 0u;
-                const uint32_t hi = t1 < 121 ? w16[(t1 / 11) * P + t1 % 11] : 0u;
-                u[e2] = lo | (hi << 16);
+    if (warp >= 8 && warp < 12) {
+        // ------------------------------------------------ window producers
+        const int pt = threadIdx.x - 256;
+        const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
+        uint4 lo[kC1PerThread], hi[kC1PerThread];
+        int b = tr.lo / t1, tt = tr.lo % t1;
+        if (tr.lo < tr.hi) conv1_load(xt + (size_t)b * plane_len, tt * 128, P, pt, lo, hi);
+        for (int tile = tr.lo, it = 0; tile < tr.hi; ++tile, ++it) {
+            const int s = it & 1, use = it >> 1;
+            if (!mbar_wait(smem_u32(&ss->xempty[s]), (use & 1) ^ 1, status, &ss->abort_flag)) break;
+            conv1_expand(sX + s * (11 * kC1Stride), pt, lo, hi);
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&ss->xfull[s]));
+            if (++tt == t1) {
+                tt = 0;
+                ++b;
             }
-            reinterpret_cast<uint4*>(sA)[kc * 128 + m] = make_uint4(u[0], u[1], u[2], u[3]);
+            if (tile + 1 < tr.hi) conv1_load(xt + (size_t)b * plane_len, tt * 128, P, pt, lo, hi);
         }
-    }
-    fence_proxy_async();
-    __syncthreads();
-
-    if (threadIdx.x == 0) {
-        if (mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag)) {
-            tc_fence_after();
-            const uint32_t idesc = idesc_bf16(128, COUT);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const uint64_t ad = sdesc(smem_u32(sA + kk * 4096), 2048, 128);
-                const uint64_t bd = sdesc(smem_u32(sB + kk * 2 * COUT * 16), COUT * 16, 128);
-                mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    } else if (warp == 12) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            bool ok = true;
+            if (blockIdx.x < ntiles) {
+                mbar_arrive_expect_tx(smem_u32(&ss->wbar), BBYTES);
+                bulk_g2s(smem_u32(sB), w1p, BBYTES, smem_u32(&ss->wbar));
+                ok = mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag);
+                if (!ok) mbar_wait_drain(smem_u32(&ss->wbar), 0);
             }
-        } else {
-            mbar_wait_drain(smem_u32(&ss->wbar), 0);
+            // A MN-major (bit 15), B K-major
+            const uint32_t idesc = idesc_bf16(128, COUT) | (1u << 15);
+            const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
+            int tt = tr.lo % t1;
+            for (int tile = tr.lo, it = 0; tile < tr.hi && ok; ++tile, ++it, tt = tt + 1 == t1 ? 0 : tt + 1) {
+                const int s = it & 1, use = it >> 1;
+                if (!mbar_wait(smem_u32(&ss->aempty[s]), (use & 1) ^ 1, status, &ss->abort_flag)) break;
+                if (!mbar_wait(smem_u32(&ss->xfull[s]), use & 1, status, &ss->abort_flag)) break;
+                tc_fence_after();
+                const int q0 = tt * 128;
+                const uint32_t d = tbase + (uint32_t)(s * COUT);
+                const uint4* sx = sX + s * (11 * kC1Stride);
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) {
+                    const int row = dy * kC1Stride + ((q0 + dy * P) & 7);
+                    const uint64_t ad = sdesc(smem_u32(sx + row), 128, 128);
+                    const uint64_t bd = sdesc(smem_u32(sB + dy * 2 * COUT * 16), COUT * 16, 128);
+                    mma_bf16(d, ad, bd, idesc, dy > 0 ? 1u : 0u);
+                }
+                mma_commit(smem_u32(&ss->xempty[s]));
+                mma_commit(smem_u32(&ss->afull[s]));
+            }
+            mma_commit(smem_u32(&ss->drain));
+            mbar_wait_drain(smem_u32(&ss->drain), 0);
         }
-        mma_commit(smem_u32(&ss->mbar));
-    }
-    bool ok = mbar_wait(smem_u32(&ss->mbar), 0, status, &ss->abort_flag);
-    ok = __all_sync(0xffffffffu, ok && !ss->abort_flag);
-    tc_fence_after();
-    if (ok) {
-        const int m = warp * 32 + lane;
-        const int qq = q0 + m;
-        const bool valid = qq < HP;
-        const bool data = valid && (qq % P) < W;
-        const size_t pos = (size_t)(qq + kPad * P + kPad);
+    } else {
+        // ------------------------------------------------ epilogue (warps 0..7)
+        const int quarter = warp & 3, half = warp >> 2;
+        const int c_lo = half * CPW;                          // first channel of this warp
+        const int m = quarter * 32 + lane;                    // position within the tile = TMEM lane
         const float isa = mode == kConv1OutE4M3 ? __ldg(inv_sa) : 1.f;
+        const int nch = conv1_out_chunks(COUT, mode);         // 16-byte chunks per position
+        const int wch = nch / 2;                              // chunks of this warp
         float vmax = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float v[16];
-            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (mode == kConv1GradMask) {
-                if (valid) {
-                    const size_t base = ((size_t)b * (COUT / 8) + c0 / 8) * plane_len + pos;
-                    uint4 m0 = make_uint4(0, 0, 0, 0), m1 = make_uint4(0, 0, 0, 0);
-                    if (data) {
-                        m0 = *reinterpret_cast<const uint4*>(mask_src + base * 8);
-                        m1 = *reinterpret_cast<const uint4*>(mask_src + (base + plane_len) * 8);
-                    }
-                    const bf16* mv0 = reinterpret_cast<const bf16*>(&m0);
-                    const bf16* mv1 = reinterpret_cast<const bf16*>(&m1);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        v[i] = __bfloat162float(mv0[i]) > 0.f ? v[i] : 0.f;
-                        v[8 + i] = __bfloat162float(mv1[i]) > 0.f ? v[8 + i] : 0.f;
-                    }
-                    bf16* dst = reinterpret_cast<bf16*>(a1);
-                    *reinterpret_cast<uint4*>(dst + base * 8) = pack8_bf16(v);
-                    *reinterpret_cast<uint4*>(dst + (base + plane_len) * 8) = pack8_bf16(v + 8);
+        const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
+        const int r128 = 128 % P;
+        int b = tr.lo / t1, tt = tr.lo % t1;
+        int col = (tt * 128 + m) % P;                         // column of this lane's position
+        for (int tile = tr.lo, it = 0; tile < tr.hi; ++tile, ++it) {
+            if (tile > tr.lo) {
+                if (++tt == t1) {
+                    tt = 0;
+                    ++b;
+                    col = m % P;
+                } else {
+                    col += r128;
+                    if (col >= P) col -= P;
                 }
-                continue;
             }
+            const int s = it & 1, use = it >> 1;
+            const bool ok = mbar_wait(smem_u32(&ss->afull[s]), use & 1, status, &ss->abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            float v[CPW];
+            if (CPW == 32) tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * COUT + c_lo), v);
+            else tmem_ld16(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * COUT + c_lo), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ss->aempty[s]));
+            const int q0 = tt * 128;
+            const int qq = q0 + m;
+            const bool valid = qq < HP;
+            const bool data = valid && col < W;
+            // chunk c of this warp: 16 bytes at plane position qq + 5 P + 5 of output chunk half * wch + c
+            uint8_t* so = reinterpret_cast<uint8_t*>(a1) +
+                          (((size_t)b * nch + half * wch) * plane_len + (size_t)(qq + kPad * P + kPad)) * 16;
+            const size_t cstride = (size_t)plane_len * 16;
+            if (mode == kConv1GradMask) {
+                const size_t pos = (size_t)(qq + kPad * P + kPad);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = data ? fmaxf(v[i] + ss->bias[c0 + i], 0.f) : 0.f;
-            if (mode == kConv1OutBF16) {
-                if (valid) {
-                    bf16* dst = reinterpret_cast<bf16*>(a1) + ((size_t)b * 8 * plane_len + pos) * 8;
-                    *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8) * plane_len * 8) = pack8_bf16(v);
-                    *reinterpret_cast<uint4*>(dst + (size_t)(c0 / 8 + 1) * plane_len * 8) = pack8_bf16(v + 8);
-                }
-            } else if (mode == kConv1OutE4M3) {
-                if (valid) {
-                    uint8_t* dst = reinterpret_cast<uint8_t*>(a1) + (((size_t)b * 4 + c0 / 16) * plane_len + pos) * 16;
-                    *reinterpret_cast<uint4*>(dst) = pack16_e4m3(v, isa);
+                for (int c = 0; c < CPW / 8; ++c) {
+                    uint4 mk = make_uint4(0, 0, 0, 0);
+                    if (data)
+                        mk = *reinterpret_cast<const uint4*>(
+                            mask_src + (((size_t)b * (COUT / 8) + c_lo / 8 + c) * plane_len + pos) * 8);
+                    const bf16* mv = reinterpret_cast<const bf16*>(&mk);
+                    float o[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) o[i] = __bfloat162float(mv[i]) > 0.f ? v[8 * c + i] : 0.f;
+                    if (valid) *reinterpret_cast<uint4*>(so + c * cstride) = pack8_bf16(o);
                 }
             } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) vmax = fmaxf(vmax, v[i]);
+                for (int i = 0; i < CPW; i += 4) {
+                    const float4 bb = *reinterpret_cast<const float4*>(&ss->bias[c_lo + i]);
+                    v[i] = fmaxf(v[i] + bb.x, 0.f);
+                    v[i + 1] = fmaxf(v[i + 1] + bb.y, 0.f);
+                    v[i + 2] = fmaxf(v[i + 2] + bb.z, 0.f);
+                    v[i + 3] = fmaxf(v[i + 3] + bb.w, 0.f);
+                }
+                // positions outside the image (pad columns, past the last row) store zeros
+                const uint32_t keep = data ? 0xFFFFFFFFu : 0u;
+                if (mode == kConv1OutBF16) {
+#pragma unroll
+                    for (int c = 0; c < CPW / 8; ++c) {
+                        uint4 u = pack8_bf16(v + 8 * c);
+                        u.x &= keep; u.y &= keep; u.z &= keep; u.w &= keep;
+                        if (valid) *reinterpret_cast<uint4*>(so + c * cstride) = u;
+                    }
+                } else if (mode == kConv1OutE4M3) {
+#pragma unroll
+                    for (int c = 0; c < CPW / 16; ++c) {
+                        uint4 u = pack16_e4m3(v + 16 * c, isa);
+                        u.x &= keep; u.y &= keep; u.z &= keep; u.w &= keep;
+                        if (valid) *reinterpret_cast<uint4*>(so + c * cstride) = u;
+                    }
+                } else if (data) {
+#pragma unroll
+                    for (int i = 0; i < CPW; ++i) vmax = fmaxf(vmax, v[i]);
+                }
             }
         }
         if (mode == kConv1AmaxOnly) {
@@ -472,9 +609,9 @@ __global__ void __launch_bounds__(128) conv1_kernel(const bf16* __restrict__ xt,
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 12) {
         tc_fence_after();
-        tmem_dealloc(tbase, COUT < 32 ? 32 : COUT);
+        tmem_dealloc(tbase, TCOLS);
     }
 }
 
@@ -516,8 +653,6 @@ struct Conv2Smem {
     int abort_flag;
     int vote[2][4];
 };
-
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Row of the slot exchange: x[j] = v[j + G] (the slot-G contribution to column j).
 template <int G>
@@ -1014,11 +1149,15 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
              const float* inv_sa, float* amax, int* status, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
-    const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
-    const size_t smem = 16384 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
+    const size_t smem = conv1_smem_bytes(64);
+    int dev = 0, sms = 0;
+    DI_CUDA(cudaGetDevice(&dev));
+    DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int ntiles = B * g.t1;
+    const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<64><<<B * g.t1, 128, smem, st>>>(xt, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa, amax,
-                                                  nullptr, status);
+    conv1_kernel<64><<<grid, kC1Threads, smem, st>>>(xt, B, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa,
+                                                     amax, nullptr, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1027,11 +1166,15 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
                    cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
-    const int winx = (128 + kConv2Reach * g.P + 10 + 7) / 8 * 8;
-    const size_t smem = 8192 + 32768 + (size_t)winx * 2 + sizeof(Conv1Smem) + 16;
+    const size_t smem = conv1_smem_bytes(32);
+    int dev = 0, sms = 0;
+    DI_CUDA(cudaGetDevice(&dev));
+    DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int ntiles = B * g.t1;
+    const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<32><<<B * g.t1, 128, smem, st>>>(g3p, g.H, g.W, g.P, g.plane, g.t1, w3t, nullptr, g2, kConv1GradMask,
-                                                  nullptr, nullptr, a2, status);
+    conv1_kernel<32><<<grid, kC1Threads, smem, st>>>(g3p, B, g.H, g.W, g.P, g.plane, g.t1, w3t, nullptr, g2,
+                                                     kConv1GradMask, nullptr, nullptr, a2, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
