@@ -212,7 +212,7 @@ FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
         w.xt = a.take<bf16>((size_t)B * g.plane);
         w.a1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
         w.a2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
-        w.T = a.take<float>(conv3_scratch_elems(g, B));
+        w.T = a.take<float>(conv3_scratch_elems(g, B, 32));
     } else {
         w.fxt = a.take<float>((size_t)B * N);
         w.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
@@ -486,7 +486,7 @@ BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
     w.lpart = a.take<double>(kLossBlocks);
     if (n->d.train_fc) {
         const int Kb = (B + 15) / 16 * 16, M = n->d.M;
-        w.T = a.take<float>(conv3_scratch_elems(g, B));
+        w.T = a.take<float>(conv3_scratch_elems(g, B, 64));
         w.dxt = a.take<float>((size_t)B * N);
         w.dxp = a.take<bf16>(packed_elems(N, 128, Kb));
         w.ypk = a.take<bf16>(packed_elems(M, gemm_nb(M), Kb));

@@ -67,7 +67,8 @@ struct Geo {
     int HP;        // H * P output positions per image
     int t1;        // conv1 tiles (128 positions) per image
     int t2;        // conv2 tiles (kConv2Valid positions) per image
-    int t3;        // conv3 row-sum blocks (128 positions) per image
+    int t3;        // conv3 row-sum tiles (kConv3Valid positions) per image
+    int tlen;      // row sums per image and kernel row (>= t3 * kConv3Valid)
     int nslab;     // conv2 window slabs of kSlabPx positions
     int plane;     // positions per image plane (multiple of 8)
 };
@@ -77,6 +78,7 @@ constexpr int kConv2N = 256;       // MMA N of conv2 (positions per tile)
 constexpr int kConv2Valid = 253;   // outputs a conv2 tile completes (256 - 3)
 constexpr int kSlabPx = 128;       // conv2 window slab
 constexpr int kConv2Reach = 10;    // rows of halo below an output row (k - 1)
+constexpr int kConv3Valid = 125;   // row sums a conv3 tile completes (128 - 3)
 
 static inline Geo make_geo(int H, int W)
 {
@@ -88,16 +90,17 @@ static inline Geo make_geo(int H, int W)
     g.t1 = cdiv(g.HP, 128);
     g.t2 = cdiv(g.HP, kConv2Valid);
     // conv3 computes row partial sums T[p] for p in [0, (H + 10) P).
-    g.t3 = cdiv((H + kConv2Reach) * g.P, 128);
+    g.t3 = cdiv((H + kConv2Reach) * g.P, kConv3Valid);
+    g.tlen = (int)align_up((size_t)g.t3 * kConv3Valid, 32);
     const int win2 = kConv2Reach * g.P + 16 + kConv2N;   // positions one conv2 tile reads (shift <= 10)
     g.nslab = cdiv(win2, kSlabPx);
     size_t need = 0;
     auto upd = [&](size_t v) { if (v > need) need = v; };
     upd((size_t)(g.t2 - 1) * kConv2Valid + (size_t)g.nslab * kSlabPx);     // conv2 window
     upd((size_t)g.t1 * 128 + (size_t)kConv2Reach * g.P + 24);              // conv1 expanded window
-    upd((size_t)g.t3 * 128 + 16);                                          // conv3 window
+    upd((size_t)g.t3 * kConv3Valid + 16);                                  // conv3 window (136 rows per tile)
     upd((size_t)(H + 2 * kPad) * g.P + 2 * kPad);                          // data + borders
-    upd((size_t)g.HP + (size_t)kConv2Reach * g.P + 48);                     // conv2 weight-gradient windows
+    upd((size_t)g.HP + (size_t)kConv2Reach * g.P + 136);                    // conv2 weight-gradient / fused conv3 windows
     g.plane = (int)align_up(need, 8);
     return g;
 }

@@ -39,7 +39,7 @@ int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int 
 // Weight layouts of the paper network (l1 = 64, l2 = 32, l3 = 1, k = 11).
 constexpr size_t kW1PackElems = 11 * 2 * 64 * 8;         // [dy][h][64 rows][8]
 constexpr size_t kW2PackElems = 11 * 3 * 4 * 2 * 128 * 8;  // [dy][s][kk][2][128][8]
-constexpr size_t kW3PackElems = 11 * 2 * 2 * 16 * 8;     // [dx][kk][2][16][8]
+constexpr size_t kW3PackElems = 3 * 2 * 2 * 64 * 8;      // [x][kk][2][64][8]
 int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p,
                       bf16* w3p, cudaStream_t st);
 
@@ -87,7 +87,7 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
 int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
                    int* status, cudaStream_t st);
 constexpr size_t kW3tPackElems = 11 * 2 * 32 * 8;      // conv3 input-gradient weights [dy'][h][32][8]
-constexpr size_t kW1tPackElems = 11 * 4 * 2 * 16 * 8;  // conv1 input-gradient weights [dx][4][2][16][8]
+constexpr size_t kW1tPackElems = 3 * 4 * 2 * 64 * 8;   // conv1 input-gradient weights [x][4][2][64][8]
 // w1t, w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
 int pack_dgrad_weights(const float* w1, const float* w2, const float* w3, bf16* w1t, bf16* w2t, bf16* w3t,
                        cudaStream_t st);
@@ -121,8 +121,14 @@ constexpr size_t kW2E4M3Bytes = 11 * 3 * 2 * 2 * 128 * 16;
 int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st);
 int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* oscale, cudaStream_t st);
 bool conv2_tc_supported(const Geo& g);
-// conv3: a2 -> row partial sums T [B][11][t3 * 128] -> xhat [B][n1 * n2] float32.
-size_t conv3_scratch_elems(const Geo& g, int B);
+// conv3: a2 -> row partial sums T [images of one pass][11][tlen] -> xhat [B][n1 * n2] float32.
+// conv3 keeps its row sums (or, for pitches >= 125, its partial outputs) in a
+// shared-memory ring and needs no scratch, up to about 4000 columns; wider
+// images use a float scratch of row sums, conv3_scratch_elems floats for a
+// batch of B, filled conv3_chunk images at a time.
+bool conv3_fused(const Geo& g, int cin);
+size_t conv3_chunk(const Geo& g, int B);
+size_t conv3_scratch_elems(const Geo& g, int B, int cin);
 int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* b3, float* T,
              float* xhat, int final_relu, int* status, cudaStream_t st);
 

@@ -30,9 +30,10 @@ inline int grid_for(long long n, int threads = 256)
 // conv3 input-gradient weights (conv1<32> layout): block (dy', h) holds rows
 // n = ci, K = columns dx' = 8 h .. 8 h + 7 (zero for dx' >= 11), value
 // W3[0][ci][10 - dy'][10 - dx'].
-// conv1 input-gradient weights (conv3_rows<64> layout): block (dx', kk) holds
-// rows n = dy' (zero for dy' >= 11), K = filters 16 kk .. 16 kk + 15, value
-// W1[co][0][10 - dy'][10 - dx'].
+// conv1 input-gradient weights (conv3<64> layout): block (x, kk) holds rows
+// n = 4 dy' + e, K = filters 16 kk .. 16 kk + 15, value
+// W1[co][0][10 - dy'][10 - dx'] with dx' = 4 x + e (zero for dy' >= 11 or
+// dx' >= 11).
 __global__ void pack_dgrad_weights_kernel(const float* __restrict__ w1, const float* __restrict__ w2,
                                           const float* __restrict__ w3, bf16* __restrict__ w1t,
                                           bf16* __restrict__ w2t, bf16* __restrict__ w3t)
@@ -42,10 +43,10 @@ __global__ void pack_dgrad_weights_kernel(const float* __restrict__ w1, const fl
          i += (long long)gridDim.x * blockDim.x) {
         if (i >= n2 + n3) {
             const long long j = i - n2 - n3;
-            const int e = (int)(j % 8), n = (int)((j / 8) % 16), half = (int)((j / (8 * 16)) % 2);
-            const int kk = (int)((j / (8 * 16 * 2)) % 4), dx = (int)(j / (8 * 16 * 2 * 4));
-            const int co = kk * 16 + half * 8 + e;
-            const float v = n < 11 ? w1[(co * 11 + (10 - n)) * 11 + (10 - dx)] : 0.f;
+            const int e8 = (int)(j % 8), n = (int)((j / 8) % 64), half = (int)((j / 512) % 2);
+            const int kk = (int)((j / 1024) % 4), x = (int)(j / 4096);
+            const int co = kk * 16 + half * 8 + e8, dy = n / 4, dx = 4 * x + n % 4;
+            const float v = (dy < 11 && dx < 11) ? w1[(co * 11 + (10 - dy)) * 11 + (10 - dx)] : 0.f;
             w1t[j] = __float2bfloat16_rn(v);
         } else if (i < n2) {
             const int e = (int)(i % 8);

@@ -87,8 +87,9 @@ __global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, 
 // conv2 A operand: block (dy, s, kk) holds rows m = 32 g + co (g = tap slot),
 //   K = input channels 16 kk .. 16 kk + 15, weight W2[co][ci][dy][4 s + g]
 //   (zero when 4 s + g = 11).
-// conv3 B operand: block (dx, kk) holds rows n = dy (zero for dy >= 11),
-//   K = channels 16 kk .. 16 kk + 15, weight W3[0][ci][dy][dx].
+// conv3 B operand: block (x, kk) holds rows n = 4 dy + e, K = channels
+//   16 kk .. 16 kk + 15, weight W3[0][ci][dy][4 x + e] (zero for dy >= 11 or
+//   4 x + e >= 11).
 __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const float* __restrict__ w2,
                                          const float* __restrict__ w3, bf16* __restrict__ w1p,
                                          bf16* __restrict__ w2p, bf16* __restrict__ w3p)
@@ -114,13 +115,10 @@ __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const flo
             w2p[j] = __float2bfloat16_rn(v);
         } else {
             const long long j = i - n1 - n2;
-            const int e = (int)(j % 8);
-            const int n = (int)((j / 8) % 16);
-            const int half = (int)((j / (8 * 16)) % 2);
-            const int kk = (int)((j / (8 * 16 * 2)) % 2);
-            const int dx = (int)(j / (8 * 16 * 2 * 2));
-            const int ci = kk * 16 + half * 8 + e;
-            const float v = n < 11 ? w3[(ci * 11 + n) * 11 + dx] : 0.f;
+            const int e8 = (int)(j % 8), n = (int)((j / 8) % 64), half = (int)((j / 512) % 2);
+            const int kk = (int)((j / 1024) % 2), x = (int)(j / 2048);
+            const int ci = kk * 16 + half * 8 + e8, dy = n / 4, dx = 4 * x + n % 4;
+            const float v = (dy < 11 && dx < 11) ? w3[(ci * 11 + dy) * 11 + dx] : 0.f;
             w3p[j] = __float2bfloat16_rn(v);
         }
     }
@@ -932,42 +930,134 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
 }
 
 // ---------------------------------------------------------------- conv3
-// Row partial sums T[p][dy] = sum_{dx, ci} W3[ci][dy][dx] a2[p + dx][ci] for
-// 128 positions p per CTA: 11 columns x 2 channel chunks = 22 MMAs with
-// M = 128, N = 16 (rows dy >= 11 zero), K = 16.  Then
-// xhat[q] = b3 + sum_dy T[q + dy P][dy].
+// conv3 (one output channel) as row partial sums
+//   T[p][dy] = sum_{dx, ci} W3[ci][dy][dx] a2[p + dx][ci],
+// then xhat[q] = b3 + sum_dy T[q + dy P][dy].  With column groups x = 0..2
+// (dx0 = 4 x) and column phases e = 0..3 (dx = 4 x + e), one tile of 128
+// positions pstart + m accumulates
+//   D[m][4 dy + e] = sum_x sum_ci W3[ci][dy][4 x + e] a2[pstart + m + 4 x][ci]
+// (A = the input window shifted by 4 x rows, K = channels; B = 64 rows
+// (dy, e), zero for dy >= 11 or dx >= 11): 3 x CIN / 16 MMAs with M = 128,
+// N = 64.  The product of tap dx taken at input pstart + m + 4 x belongs to
+// output pstart + m - e, so T[pstart + m][dy] = sum_e D[m + e][4 dy + e]; the
+// epilogue adds the phases with warp shuffles and takes the 3 rows past a
+// warp from the next warp through shared memory.  Tiles advance by
+// kConv3Valid = 125 positions (the last 3 rows of a tile lack their e > 0
+// partners).
+//
+// Fused modes: each CTA owns a contiguous range of output tiles (125
+// positions) and walks, per image it touches, the row-sum tiles from its
+// first output q_a to its last output + 10 P.  kConv3RingT (pitch P < 125)
+// keeps the last R >= 10 P + 125 positions of T in a shared-memory ring and
+// after tile k completes the outputs q = pstart - 10 P + m, whose 11 row sums
+// are then all in the ring.  kConv3RingAcc (P >= 125) keeps one partial sum
+// per pending output instead: T[p][dy] is added to acc[p - dy P] (dy = 0
+// sets it, dy = 10 completes the output), which no two threads of a tile can
+// share because their positions differ by less than P; every output still
+// adds its kernel rows in the order dy = 0..10.  kConv3Global writes T to
+// global memory and conv3_sum_kernel adds the kernel rows (images too wide
+// for the ring).
+//
+// Persistent CTAs, 6 warps: warp 4 streams the input windows (136 rows per
+// channel chunk) through a kC3Stages ring, warp 5 owns TMEM (2 accumulators
+// of 64 columns) and issues the MMAs, warps 0..3 (TMEM lane quarters) drain
+// an accumulator.
+constexpr int kC3Rows = 136;            // window rows per channel chunk (128 + 8)
+constexpr int kC3Stages = 2;
+constexpr int kC3Threads = 192;
+
 struct Conv3Smem {
-    uint64_t bar, mbar;
+    uint64_t wbar;
+    uint64_t xfull[kC3Stages], xempty[kC3Stages];
+    uint64_t afull[2], aempty[2];
+    uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
+    int vote[2][4];
+    float halo[2][4][3][11][4];         // [tile parity][warp][lane 0..2][dy][e]
 };
-constexpr int kConv3Win = 144;      // 128 + 10 positions, rounded up to 16
 
-// CIN = 32: conv3 (input a2).  CIN = 64: the input gradient of conv1 (input
-// the gradient plane of z1, conv1's kernels flipped), needed to train the FC layer.
-template <int CIN>
-__global__ void __launch_bounds__(128) conv3_rows_kernel(const bf16* __restrict__ a2, int plane_len, int t3,
-                                                         int tlen, const bf16* __restrict__ w3p,
-                                                         float* __restrict__ T, int* status)
+__host__ __device__ constexpr uint32_t conv3_wbytes(int cin) { return 3u * (cin / 16) * 2048u; }
+__host__ __device__ constexpr uint32_t conv3_stage_bytes(int cin) { return (cin / 8) * kC3Rows * 16u; }
+__host__ __device__ constexpr size_t conv3_base_smem(int cin)
+{
+    return conv3_wbytes(cin) + kC3Stages * (size_t)conv3_stage_bytes(cin) + sizeof(Conv3Smem) + 16;
+}
+// ring positions of the fused kernel
+__host__ __device__ inline int conv3_ring(int P) { return (10 * P + 128 + 31) / 32 * 32; }
+
+enum { kConv3Global = 0, kConv3RingT = 1, kConv3RingAcc = 2 };
+
+// Calls f(it, b, pstart, qa, qb) for the row-sum tiles of output tiles [lo, hi)
+// in order until f returns false.  FUSED: per image, tiles pstart = qa + 125 k
+// covering [qa, qb + 10 P); otherwise tiles u of [0, t3) with pstart = 125 u.
+template <bool FUSED, typename F>
+__device__ __forceinline__ void conv3_walk(int lo, int hi, int tper, int HP, int P, F f)
+{
+    int it = 0;
+    if (FUSED) {
+        for (int b = lo / tper; b * tper < hi; ++b) {
+            const int ua = lo - b * tper > 0 ? lo - b * tper : 0;
+            const int ub = hi - b * tper < tper ? hi - b * tper : tper;
+            if (ua >= ub) continue;
+            const int qa = ua * kConv3Valid, qb = ub * kConv3Valid < HP ? ub * kConv3Valid : HP;
+            const int K = (qb + kConv2Reach * P - qa + kConv3Valid - 1) / kConv3Valid;
+            for (int k = 0; k < K; ++k, ++it)
+                if (!f(it, b, qa + k * kConv3Valid, qa, qb)) return;
+        }
+    } else {
+        int b = lo / tper, u = lo % tper;
+        for (int tile = lo; tile < hi; ++tile, ++it) {
+            if (!f(it, b, u * kConv3Valid, 0, 0)) return;
+            if (++u == tper) {
+                u = 0;
+                ++b;
+            }
+        }
+    }
+}
+
+// CIN = 32: conv3 (input a2, [B][4][plane][8]).  CIN = 64: the input gradient
+// of conv1 (input the gradient plane of z1, [B][8][plane][8], conv1's kernels
+// flipped), needed to train the FC layer.  tper = output tiles per image
+// (fused modes: cdiv(H P, 125)) or row-sum tiles per image (t3).
+template <int CIN, int MODE>
+__global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restrict__ a2, int B, int H, int W, int P,
+                                                           int plane_len, int tper, int tlen,
+                                                           const bf16* __restrict__ w3p, float* __restrict__ T,
+                                                           const float* __restrict__ b3, int final_relu,
+                                                           float* __restrict__ xhat, int R, int* status)
 {
     constexpr int NCH = CIN / 8, KK = CIN / 16;
-    constexpr uint32_t WB = 11 * KK * 512;
+    constexpr bool FUSED = MODE != kConv3Global;
+    constexpr uint32_t WB = conv3_wbytes(CIN), SB = conv3_stage_bytes(CIN), CHB = kC3Rows * 16;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* sWin = smem_raw;                         // [NCH][144][8] bf16
-    uint8_t* sW = smem_raw + NCH * kConv3Win * 16;    // [11][KK][2][16][8] bf16
-    Conv3Smem* ss = reinterpret_cast<Conv3Smem*>(sW + WB);
+    uint8_t* sW = smem_raw;                                    // [x][kk][2][64][8]
+    uint8_t* sX = smem_raw + WB;                               // [stage][NCH][kC3Rows][8]
+    Conv3Smem* ss = reinterpret_cast<Conv3Smem*>(sX + kC3Stages * SB);
+    // kConv3RingT: [11][R] row sums; kConv3RingAcc: [R] partial outputs
+    float* ring = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ss) + sizeof(Conv3Smem));
+
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int b = blockIdx.x / t3, u = blockIdx.x % t3;
-    const int p0 = u * 128;
+    const int HP = H * P;
+    const TileRange tr = tile_range(B * tper, blockIdx.x, gridDim.x);
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&ss->bar), 1);
-        mbar_init(smem_u32(&ss->mbar), 1);
+        mbar_init(smem_u32(&ss->wbar), 1);
+        for (int s = 0; s < kC3Stages; ++s) {
+            mbar_init(smem_u32(&ss->xfull[s]), 1);
+            mbar_init(smem_u32(&ss->xempty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&ss->afull[s]), 1);
+            mbar_init(smem_u32(&ss->aempty[s]), 4);
+        }
+        mbar_init(smem_u32(&ss->drain), 1);
         ss->abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 0) {
-        tmem_alloc(smem_u32(&ss->tmem_base), 32);
+    if (warp == 5) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 128);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -975,46 +1065,183 @@ __global__ void __launch_bounds__(128) conv3_rows_kernel(const bf16* __restrict_
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
 
-    if (threadIdx.x == 0) {
-        const uint32_t bar = smem_u32(&ss->bar);
-        mbar_arrive_expect_tx(bar, NCH * kConv3Win * 16 + WB);
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(a2) + (size_t)b * NCH * plane_len * 16;
-        for (int c = 0; c < NCH; ++c)
-            bulk_g2s(smem_u32(sWin + c * kConv3Win * 16), src + ((size_t)c * plane_len + p0) * 16,
-                     kConv3Win * 16, bar);
-        bulk_g2s(smem_u32(sW), w3p, WB, bar);
-        if (mbar_wait(bar, 0, status, &ss->abort_flag)) {
-            tc_fence_after();
-            const uint32_t idesc = idesc_bf16(128, 16);
-            for (int dx = 0; dx < 11; ++dx)
-#pragma unroll
-                for (int kk = 0; kk < KK; ++kk) {
-                    const uint64_t ad = sdesc(smem_u32(sWin + (2 * kk) * kConv3Win * 16 + dx * 16),
-                                              kConv3Win * 16, 128);
-                    const uint64_t bd = sdesc(smem_u32(sW + (dx * KK + kk) * 512), 256, 128);
-                    mma_bf16(tbase, ad, bd, idesc, (dx | kk) ? 1u : 0u);
-                }
-        } else {
-            mbar_wait_drain(bar, 0);
+    if (warp == 4) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            int parity[kC3Stages];
+            for (int s = 0; s < kC3Stages; ++s) parity[s] = -1;
+            conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int b, int pstart, int, int) {
+                const int st = it % kC3Stages, n = it / kC3Stages;
+                if (!mbar_wait(smem_u32(&ss->xempty[st]), (n & 1) ^ 1, status, &ss->abort_flag)) return false;
+                mbar_arrive_expect_tx(smem_u32(&ss->xfull[st]), SB);
+                parity[st] = n & 1;
+                const uint8_t* src = reinterpret_cast<const uint8_t*>(a2) + (size_t)b * NCH * plane_len * 16;
+                for (int c = 0; c < NCH; ++c)
+                    bulk_g2s(smem_u32(sX + st * SB + c * CHB), src + ((size_t)c * plane_len + pstart) * 16, CHB,
+                             smem_u32(&ss->xfull[st]));
+                return true;
+            });
+            for (int s = 0; s < kC3Stages; ++s)
+                if (parity[s] >= 0) mbar_wait_drain(smem_u32(&ss->xfull[s]), parity[s]);
         }
-        mma_commit(smem_u32(&ss->mbar));
-    }
-    bool ok = mbar_wait(smem_u32(&ss->mbar), 0, status, &ss->abort_flag);
-    ok = __all_sync(0xffffffffu, ok && !ss->abort_flag);
-    tc_fence_after();
-    if (ok) {
-        float v[16];
-        tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16), v);
-        const int p = p0 + warp * 32 + lane;
-        float* dst = T + (size_t)b * 11 * tlen + p;
+    } else if (warp == 5) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            bool ok = true;
+            if (tr.lo < tr.hi) {
+                mbar_arrive_expect_tx(smem_u32(&ss->wbar), WB);
+                bulk_g2s(smem_u32(sW), w3p, WB, smem_u32(&ss->wbar));
+                ok = mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag);
+                if (!ok) mbar_wait_drain(smem_u32(&ss->wbar), 0);
+            }
+            const uint32_t idesc = idesc_bf16(128, 64);
+            if (ok)
+                conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int, int, int, int) {
+                    const int s = it & 1, use = it >> 1;
+                    const int st = it % kC3Stages, n = it / kC3Stages;
+                    if (!mbar_wait(smem_u32(&ss->aempty[s]), (use & 1) ^ 1, status, &ss->abort_flag)) return false;
+                    if (!mbar_wait(smem_u32(&ss->xfull[st]), n & 1, status, &ss->abort_flag)) return false;
+                    tc_fence_after();
+                    const uint32_t d = tbase + (uint32_t)(s * 64);
+                    const uint32_t x0 = smem_u32(sX + st * SB);
 #pragma unroll
-        for (int dy = 0; dy < 11; ++dy) dst[(size_t)dy * tlen] = v[dy];
+                    for (int x = 0; x < 3; ++x)
+#pragma unroll
+                        for (int kk = 0; kk < KK; ++kk) {
+                            const uint64_t ad = sdesc(x0 + (2 * kk) * CHB + (4 * x) * 16, CHB, 128);
+                            const uint64_t bd = sdesc(smem_u32(sW + (x * KK + kk) * 2048), 1024, 128);
+                            mma_bf16(d, ad, bd, idesc, (x | kk) ? 1u : 0u);
+                        }
+                    mma_commit(smem_u32(&ss->xempty[st]));
+                    mma_commit(smem_u32(&ss->afull[s]));
+                    return true;
+                });
+            mma_commit(smem_u32(&ss->drain));
+            mbar_wait_drain(smem_u32(&ss->drain), 0);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 0..3)
+        const int m = warp * 32 + lane;                         // row of this thread
+        const bool row_ok = m < kConv3Valid;
+        const float bias = (FUSED && b3) ? __ldg(b3) : 0.f;
+        const int RP = kConv2Reach * P;
+        // fused bookkeeping: ring slot of pstart, and (row, column) of output q = pstart - 10 P + m
+        int base = 0, orow = 0, ocol = 0, cur_b = -1, cur_qa = -1;
+        const int step_r = kConv3Valid / P, step_c = kConv3Valid % P;
+        conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int b, int pstart, int qa, int qb) {
+            const int s = it & 1, use = it >> 1;
+            bool ok = mbar_wait(smem_u32(&ss->afull[s]), use & 1, status, &ss->abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            float v[48];                                        // v[4 dy + e] = D[m][4 dy + e]
+            if (ok) {
+                tc_fence_after();
+                const uint32_t ta = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * 64);
+                tmem_ld48(ta, v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ss->aempty[s]));
+                if (lane < 3) {
+#pragma unroll
+                    for (int dy = 0; dy < 11; ++dy)
+#pragma unroll
+                        for (int e = 1; e < 4; ++e) ss->halo[s][warp][lane][dy][e] = v[4 * dy + e];
+                }
+            }
+            if (lane == 0) ss->vote[s][warp] = ok ? 1 : 0;
+            epi_bar();
+            if (!(ss->vote[s][0] && ss->vote[s][1] && ss->vote[s][2] && ss->vote[s][3])) return false;
+            float tv[11];
+#pragma unroll
+            for (int dy = 0; dy < 11; ++dy) {
+                float t = v[4 * dy];
+#pragma unroll
+                for (int e = 1; e < 4; ++e) {
+                    const float nb = __shfl_down_sync(0xffffffffu, v[4 * dy + e], e);
+                    // rows past this warp come from lanes 0..2 of the next warp (never needed by
+                    // warp 3's valid rows); the index is clamped so that the read stays in bounds
+                    const int hl = lane + e - 32;
+                    const float h = ss->halo[s][warp < 3 ? warp + 1 : 3][hl > 0 ? hl : 0][dy][e];
+                    t += hl < 0 ? nb : h;
+                }
+                tv[dy] = t;
+            }
+            if (!FUSED) {
+                if (row_ok) {
+                    float* dst = T + (size_t)b * 11 * tlen + pstart + m;
+#pragma unroll
+                    for (int dy = 0; dy < 11; ++dy) dst[(size_t)dy * tlen] = tv[dy];
+                }
+                return true;
+            }
+            if (b != cur_b || qa != cur_qa) {
+                // new segment: ring slot of pstart = qa is 0; output q = qa - 10 P + m
+                cur_b = b;
+                cur_qa = qa;
+                base = 0;
+                const int q = qa - RP + m;
+                orow = q >= 0 ? q / P : -((-q + P - 1) / P);
+                ocol = q - orow * P;
+            } else {
+                base += kConv3Valid;
+                if (base >= R) base -= R;
+                orow += step_r;
+                ocol += step_c;
+                if (ocol >= P) {
+                    ocol -= P;
+                    ++orow;
+                }
+            }
+            if (MODE == kConv3RingAcc) {
+                // contribution dy of position p goes to output p - dy P (slot r), in the order dy = 0..10
+                const int p = pstart + m;
+                int r = base + m;
+                if (r >= R) r -= R;
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) {
+                    const int q = p - dy * P;
+                    if (row_ok && q >= qa && q < qb) {
+                        if (dy == 0) {
+                            ring[r] = tv[0];
+                        } else if (dy < 10) {
+                            ring[r] += tv[dy];
+                        } else if (ocol < W) {
+                            const float x = ring[r] + tv[10] + bias;
+                            xhat[((size_t)b * H + orow) * W + ocol] = final_relu ? fmaxf(x, 0.f) : x;
+                        }
+                    }
+                    r -= P;
+                    if (r < 0) r += R;
+                }
+                return true;
+            }
+            if (row_ok) {
+                int w = base + m;
+                if (w >= R) w -= R;
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) ring[dy * R + w] = tv[dy];
+            }
+            epi_bar();
+            const int q = pstart - RP + m;
+            if (row_ok && q >= qa && q < qb && ocol < W) {
+                int r = base + m - RP;
+                if (r < 0) r += R;
+                float x = bias;
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) {
+                    x += ring[dy * R + r];
+                    r += P;
+                    if (r >= R) r -= R;
+                }
+                xhat[((size_t)b * H + orow) * W + ocol] = final_relu ? fmaxf(x, 0.f) : x;
+            }
+            return true;
+        });
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 5) {
         tc_fence_after();
-        tmem_dealloc(tbase, 32);
+        tmem_dealloc(tbase, 128);
     }
 }
 
@@ -1267,36 +1494,92 @@ int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const b
     return launch_conv2<false, false, true>(g2, B, g, w2t, nullptr, nullptr, a1, g1, grid, smem, nslab, status, st);
 }
 
-size_t conv3_scratch_elems(const Geo& g, int B) { return (size_t)B * 11 * g.t3 * 128; }
+
+size_t conv3_chunk(const Geo& g, int B)
+{
+    // images per unfused conv3 pass: the row sums T of one pass stay within ~48 MB of L2
+    const size_t per = (size_t)11 * g.tlen * sizeof(float);
+    size_t c = ((size_t)48 << 20) / per;
+    if (c < 1) c = 1;
+    return c < (size_t)B ? c : (size_t)B;
+}
+
+static int conv3_mode(const Geo& g) { return g.P < kConv3Valid ? kConv3RingT : kConv3RingAcc; }
+
+static size_t conv3_fused_smem(const Geo& g, int cin)
+{
+    const size_t per = conv3_mode(g) == kConv3RingT ? 11 : 1;
+    return conv3_base_smem(cin) + per * conv3_ring(g.P) * sizeof(float);
+}
+
+bool conv3_fused(const Geo& g, int cin) { return conv3_fused_smem(g, cin) <= 227 * 1024; }
+
+size_t conv3_scratch_elems(const Geo& g, int B, int cin)
+{
+    return (B > 0 && !conv3_fused(g, cin)) ? conv3_chunk(g, B) * 11 * g.tlen : 0;
+}
+
+// One pass over B images of `in` ([B][CIN / 8][plane][8]): fused (xhat written)
+// or, for images too wide for the ring, row sums into T.
+template <int CIN>
+static int launch_conv3(const bf16* in, int B, const Geo& g, const bf16* w, float* T, const float* b3,
+                        int final_relu, float* xhat, bool fused, int* status, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    DI_CUDA(cudaGetDevice(&dev));
+    DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = fused ? conv3_fused_smem(g, CIN) : conv3_base_smem(CIN);
+    const int tper = fused ? cdiv(g.HP, kConv3Valid) : g.t3;
+    int occ = (int)((228 * 1024) / (smem + 1024));
+    const int occ_max = CIN == 32 ? 3 : 2;
+    if (occ > occ_max) occ = occ_max;
+    if (occ < 1) occ = 1;
+    const long long ntiles = (long long)B * tper;
+    const int grid = ntiles < (long long)occ * sms ? (int)ntiles : occ * sms;
+    const int R = conv3_ring(g.P);
+    const int mode = fused ? conv3_mode(g) : kConv3Global;
+    auto go = [&](auto kern) -> int {
+        DI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, kC3Threads, smem, st>>>(in, B, g.H, g.W, g.P, g.plane, tper, g.tlen, w, T, b3, final_relu, xhat,
+                                             R, status);
+        return DEEPINV_OK;
+    };
+    if (mode == kConv3RingT) DI_TRY(go(conv3_kernel<CIN, kConv3RingT>));
+    else if (mode == kConv3RingAcc) DI_TRY(go(conv3_kernel<CIN, kConv3RingAcc>));
+    else DI_TRY(go(conv3_kernel<CIN, kConv3Global>));
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+template <int CIN>
+static int conv3_all(const bf16* in, int B, const Geo& g, const bf16* w, const float* b3, float* T, float* out,
+                     int final_relu, int* status, cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    if (conv3_fused(g, CIN)) return launch_conv3<CIN>(in, B, g, w, nullptr, b3, final_relu, out, true, status, st);
+    const int chunk = (int)conv3_chunk(g, B);
+    for (int b0 = 0; b0 < B; b0 += chunk) {
+        const int nb = B - b0 < chunk ? B - b0 : chunk;
+        DI_TRY(launch_conv3<CIN>(in + (size_t)b0 * (CIN / 8) * g.plane * 8, nb, g, w, T, nullptr, 0, nullptr, false,
+                                 status, st));
+        const long long n = (long long)nb * g.H * g.W;
+        conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, nb, g.H, g.W, g.P, g.tlen, b3, final_relu,
+                                                    out + (size_t)b0 * g.H * g.W);
+        DI_LAUNCH_CHECK();
+    }
+    return DEEPINV_OK;
+}
 
 int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* b3, float* T, float* xhat,
              int final_relu, int* status, cudaStream_t st)
 {
-    if (B <= 0) return DEEPINV_OK;
-    const size_t smem = 4 * kConv3Win * 16 + 11264 + sizeof(Conv3Smem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int tlen = g.t3 * 128;
-    conv3_rows_kernel<32><<<B * g.t3, 128, smem, st>>>(a2, g.plane, g.t3, tlen, w3p, T, status);
-    DI_LAUNCH_CHECK();
-    const long long n = (long long)B * g.H * g.W;
-    conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, B, g.H, g.W, g.P, tlen, b3, final_relu, xhat);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
+    return conv3_all<32>(a2, B, g, w3p, b3, T, xhat, final_relu, status, st);
 }
 
 int conv1_dgrad_tc(const bf16* g1, int B, const Geo& g, const bf16* w1t, float* T, float* dxt, int* status,
                    cudaStream_t st)
 {
-    if (B <= 0) return DEEPINV_OK;
-    const size_t smem = 8 * kConv3Win * 16 + 22528 + sizeof(Conv3Smem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(conv3_rows_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int tlen = g.t3 * 128;
-    conv3_rows_kernel<64><<<B * g.t3, 128, smem, st>>>(g1, g.plane, g.t3, tlen, w1t, T, status);
-    DI_LAUNCH_CHECK();
-    const long long n = (long long)B * g.H * g.W;
-    conv3_sum_kernel<<<grid1d(n), 256, 0, st>>>(T, B, g.H, g.W, g.P, tlen, nullptr, 0, dxt);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
+    return conv3_all<64>(g1, B, g, w1t, nullptr, T, dxt, 0, status, st);
 }
 
 int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st)
