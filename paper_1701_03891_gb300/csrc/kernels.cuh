@@ -99,11 +99,6 @@ int conv1_dgrad_tc(const bf16* g1, int B, const Geo& g, const bf16* w1t, float* 
 int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st);
 // Channel sums of a bf16 plane (bias gradients): part [B][C] float64 scratch, out [C].
 int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st);
-// Weight gradient of conv1 (conv1 = true: G = g1 plane, A = x~ plane) or conv3
-// (G = x^ gradient plane, A = a2 plane) into dw [O][I][11][11]; acc is
-// float64 scratch of O * I * 121.
-int small_wgrad(bool conv1, const bf16* G, const bf16* A, int B, const Geo& g, double* acc, float* dw,
-                cudaStream_t st);
 // conv1 (conv1 = true: S = x~ plane, C = g1 plane; also db = conv1's bias
 // gradient) or conv3 (S = x^ gradient plane, C = a2 plane; db unused) weight
 // gradient on the tensor cores; part is float32 scratch of tapwgrad_scratch_floats().

@@ -126,76 +126,6 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, 
     }
 }
 
-// Weight gradient of the layers with one channel on one side (conv1: G has
-// 64 channels, A = x~ one; conv3: G = x^ gradient one channel, A = a2 with
-// 32), over NPOS plane positions of one image per block:
-//   dW[o][i][dy][dx] += sum_u G[u][o] A[u + (dy-5) P + dx - 5][i].
-// Thread (j, dy) owns the 11 taps dx of one kernel row and one channel j of
-// the many-channel side (32 channels per block, blockIdx.y selects them); it
-// slides an 11-value window along u.  Block totals are added into acc
-// (float64) with atomics.
-constexpr int kWgNpos = 256;
-
-template <int O, int I>
-__global__ void __launch_bounds__(352) small_wgrad_kernel(const bf16* __restrict__ G, const bf16* __restrict__ A,
-                                                          int P, int plane_len, int u_begin, int u_count,
-                                                          double* __restrict__ acc)
-{
-    constexpr int J = O > I ? O : I;                 // channels of the many-channel side (64 or 32)
-    static_assert(O == 1 || I == 1, "one side has one channel");
-    const int nblk = (u_count + kWgNpos - 1) / kWgNpos;
-    const int b = blockIdx.x / nblk;
-    const int u0 = u_begin + (blockIdx.x % nblk) * kWgNpos;
-    const int npos = min(kWgNpos, u_begin + u_count - u0);
-    const int wlen = npos + 10 * P + 10;
-    extern __shared__ float sm[];
-    float* sG = sm;                                  // [kWgNpos][O]
-    float* sA = sm + kWgNpos * O;                    // [wlen][I], window starts at u0 - 5 P - 5
-    const int gch = O == 1 ? 1 : O / 8, ach = I == 1 ? 1 : I / 8;
-    for (int k = threadIdx.x; k < npos * O; k += blockDim.x) {
-        const int u = k / O, o = k % O;
-        const size_t pos = (size_t)(u0 + u);
-        sG[k] = O == 1 ? __bfloat162float(G[(size_t)b * plane_len + pos])
-                       : __bfloat162float(G[(((size_t)b * gch + o / 8) * plane_len + pos) * 8 + o % 8]);
-    }
-    for (int k = threadIdx.x; k < wlen * I; k += blockDim.x) {
-        const int u = k / I, i = k % I;
-        const long long pos = (long long)u0 - 5 * P - 5 + u;
-        float v = 0.f;
-        if (pos >= 0 && pos < plane_len)
-            v = I == 1 ? __bfloat162float(A[(size_t)b * plane_len + pos])
-                       : __bfloat162float(A[(((size_t)b * ach + i / 8) * plane_len + pos) * 8 + i % 8]);
-        sA[k] = v;
-    }
-    __syncthreads();
-    const int t = threadIdx.x;
-    if (t < 32 * 11) {
-        const int j = blockIdx.y * 32 + t % 32, dy = t / 32;   // blockIdx.y picks 32 of the J channels
-        const int o = O == 1 ? 0 : j, i = I == 1 ? 0 : j;
-        float w[11], a[11];
-#pragma unroll
-        for (int dx = 0; dx < 11; ++dx) {
-            w[dx] = sA[(dy * P + dx) * I + i];      // u = 0: window index u + dy P + dx
-            a[dx] = 0.f;
-        }
-        for (int u = 0; u < npos; ++u) {
-            const float gv = sG[u * O + o];
-#pragma unroll
-            for (int dx = 0; dx < 11; ++dx) a[dx] = fmaf(gv, w[dx], a[dx]);
-#pragma unroll
-            for (int dx = 0; dx < 10; ++dx) w[dx] = w[dx + 1];
-            w[10] = sA[((u + 1) + dy * P + 10) * I + i];
-        }
-#pragma unroll
-        for (int dx = 0; dx < 11; ++dx) atomicAdd(&acc[((size_t)o * I + i) * 121 + dy * 11 + dx], (double)a[dx]);
-    }
-}
-
-__global__ void d2f_kernel(const double* __restrict__ src, int n, float* __restrict__ dst)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = (float)src[i];
-}
-
 
 // ---------------------------------------------------------------- conv2 weight gradient
 // dW2[co][ci][dy][4 s + g] = sum_u' G[u' - g][co] A1[u' + (dy - 5) P + 4 s - 5][ci]
@@ -261,38 +191,46 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0) {
+        // producer warp: lane 0 waits and arms the stage barrier, then the 16 + 8 npairs
+        // window copies of the stage are issued by all 32 lanes (small bulk copies are
+        // limited by their issue rate per thread)
         int parity[kWgStages] = {-1, -1};
         for (long long k = blk0; k < blk1; ++k) {
             const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
-            if (!mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag)) break;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
             const int b = (int)(k / nb_img);
             const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
             const int npos = min(kWgKB, u_begin + HP16 - u0);
             const uint32_t bytes = (uint32_t)npos * 16;
-            mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (16 + 8 * npairs) * bytes);
+            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (16 + 8 * npairs) * bytes);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             parity[st] = n & 1;
             const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
             const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * 8 * plane_len * 16;
             uint8_t* dA = sA + st * kWgABytes;
             uint8_t* dB = sB + st * kWgBBytes;
-            for (int g = 0; g < 4; ++g)
-                for (int c4 = 0; c4 < 4; ++c4)
+            for (int c = lane; c < 16 + 8 * npairs; c += 32) {
+                if (c < 16) {
+                    const int g = c / 4, c4 = c % 4;
                     bulk_g2s(smem_u32(dA + (g * 4 + c4) * kWgKB * 16),
                              g2b + ((size_t)c4 * plane_len + u0 - g) * 16, bytes, smem_u32(&ss->full[st]));
-            for (int pl = 0; pl < npairs; ++pl) {
-                const int p = quad * 4 + pl, dy = p / 3, s = p % 3;
-                const int off = (dy - 5) * P + 4 * s - 5;
-                for (int c8 = 0; c8 < 8; ++c8)
+                } else {
+                    const int pl = (c - 16) / 8, c8 = (c - 16) % 8;
+                    const int p = quad * 4 + pl, dy = p / 3, s = p % 3;
+                    const int off = (dy - 5) * P + 4 * s - 5;
                     bulk_g2s(smem_u32(dB + (pl * 8 + c8) * kWgKB * 16),
                              a1b + ((size_t)c8 * plane_len + u0 + off) * 16, bytes, smem_u32(&ss->full[st]));
+                }
             }
         }
-        for (int s = 0; s < kWgStages; ++s)
-            if (parity[s] >= 0) {
-                const unsigned long long t0 = globaltimer();
-                while (!mbar_try_wait(smem_u32(&ss->full[s]), parity[s]) && globaltimer() - t0 < 1000000000ull) {}
-            }
+        if (lane == 0)
+            for (int s = 0; s < kWgStages; ++s)
+                if (parity[s] >= 0) {
+                    const unsigned long long t0 = globaltimer();
+                    while (!mbar_try_wait(smem_u32(&ss->full[s]), parity[s]) && globaltimer() - t0 < 1000000000ull) {}
+                }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = idesc_bf16_mn(128, NB);
         bool first = true;
@@ -536,29 +474,6 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 }
 
 // Positions u that can carry a nonzero gradient: the data rows [5P+5, 5P+5+HP).
-int small_wgrad(bool conv1, const bf16* G, const bf16* A, int B, const Geo& g, double* acc, float* dw,
-                cudaStream_t st)
-{
-    const int O = conv1 ? 64 : 1, I = conv1 ? 1 : 32;
-    const int n = O * I * 121;
-    DI_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * sizeof(double), st));
-    const int u_begin = kPad * g.P + kPad, u_count = g.HP;
-    const int nblk = (u_count + kWgNpos - 1) / kWgNpos;
-    const int wlen = kWgNpos + 10 * g.P + 10;
-    const size_t smem = ((size_t)kWgNpos * O + (size_t)(wlen + 1) * I) * sizeof(float);
-    if (conv1) {
-        DI_CUDA(cudaFuncSetAttribute(small_wgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        small_wgrad_kernel<64, 1><<<dim3(B * nblk, 2), 352, smem, st>>>(G, A, g.P, g.plane, u_begin, u_count, acc);
-    } else {
-        DI_CUDA(cudaFuncSetAttribute(small_wgrad_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        small_wgrad_kernel<1, 32><<<B * nblk, 352, smem, st>>>(G, A, g.P, g.plane, u_begin, u_count, acc);
-    }
-    DI_LAUNCH_CHECK();
-    d2f_kernel<<<grid_for(n), 256, 0, st>>>(acc, n, dw);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
-}
-
 size_t wgrad2_scratch_floats() { return (size_t)kWgQuads * kWgSplit * 128 * 256; }
 
 int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
