@@ -625,16 +625,18 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
 // 33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253 valid outputs
 // per tile (the last 3 columns lack their slot-3 partner).
 //
-// Persistent CTAs, 6 warps: warp 0 lane 0 streams the input window (slabs of
-// 128 positions x 64 channels, freed as soon as the last kernel row reading
-// them has been multiplied) and the weights ((dy, s) blocks of 16 KB through a
-// ring); warp 1 owns TMEM (2 accumulators x 256 columns) and issues MMAs;
-// warps 2..5 drain the accumulator of the previous tile.
+// Persistent CTAs, 7 warps: warp 6 streams the input window (slabs of 128
+// positions x 64 channels, freed as soon as the last kernel row reading them
+// has been multiplied) and warp 0 the weights ((dy, s) blocks of 16 KB through
+// a ring), each on its own so that neither waits for the other; warp 1 owns
+// TMEM (2 accumulators x 256 columns) and issues MMAs; warps 2..5 drain the
+// accumulator of the previous tile.
 //
 // Wide images (the window of 10 P + 264 positions does not fit in shared
 // memory) use row mode: the producer streams, for every kernel row dy, just
 // the 264 positions that row's MMAs read, through a ring of kRowSlots pieces.
 constexpr int kW2Stages = 4;
+constexpr int kConv2Threads = 224;
 constexpr int kMaxSlabs = 10;
 
 constexpr int kPiecePx = 16 + kConv2N; // positions one kernel row's MMAs read (row mode; shift <= 10)
@@ -668,7 +670,7 @@ __host__ __device__ inline int conv2_dylast(int j, int P)
 }
 
 template <bool ROWS, bool FP8, bool DGRAD>
-__global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ a1, int B, int H, int W, int P,
+__global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __restrict__ a1, int B, int H, int W, int P,
                                                        int plane_len, int t2, int nslab,
                                                        const void* __restrict__ w2p,
                                                        const float* __restrict__ b2,
@@ -728,13 +730,14 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
 
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ producer
+    if (warp == 6 && lane == 0) {
+        // ------------------------------------------------ window producer
+        // Runs ahead on its own: the slabs of the next tile are loaded as soon as the
+        // kernel rows that read the previous tile's slabs have been multiplied, not in
+        // step with the weight stream.
         int slab_parity[kMaxSlabs];
-        int w_parity[kW2Stages];
         for (int j = 0; j < kMaxSlabs; ++j) slab_parity[j] = -1;
-        for (int s = 0; s < kW2Stages; ++s) w_parity[s] = -1;
-        int it = 0, wst = 0, pc = 0;
+        int it = 0, pc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
@@ -763,6 +766,18 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                                  src_img + ((size_t)c * plane_len + q0 + j * kSlabPx) * 16, kSlabPx * 16,
                                  smem_u32(&ss->full[j]));
                 }
+            }
+        }
+        for (int j = 0; j < nslab; ++j)
+            if (slab_parity[j] >= 0) mbar_wait_drain(smem_u32(&ss->full[j]), slab_parity[j]);
+    } else if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ weight producer
+        int w_parity[kW2Stages];
+        for (int s = 0; s < kW2Stages; ++s) w_parity[s] = -1;
+        int wst = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int dy = 0; dy < 11 && ok; ++dy) {
                 for (int s = 0; s < GROUPS && ok; ++s, ++wst) {
                     const int slot = wst % kW2Stages, n = wst / kW2Stages;
                     if (!mbar_wait(smem_u32(&ss->wempty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
@@ -774,8 +789,6 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
                 }
             }
         }
-        for (int j = 0; j < nslab; ++j)
-            if (slab_parity[j] >= 0) mbar_wait_drain(smem_u32(&ss->full[j]), slab_parity[j]);
         for (int s = 0; s < kW2Stages; ++s)
             if (w_parity[s] >= 0) mbar_wait_drain(smem_u32(&ss->wfull[s]), w_parity[s]);
     } else if (warp == 1 && lane == 0) {
@@ -836,7 +849,7 @@ __global__ void __launch_bounds__(192, 1) conv2_kernel(const void* __restrict__ 
         }
         mma_commit(smem_u32(&ss->drain));
         mbar_wait_drain(smem_u32(&ss->drain), 0);
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < 6) {
         // ------------------------------------------------ epilogue
         const int quarter = warp % 4;                         // TMEM lane quarter
         const int g = DGRAD ? quarter / 2 : quarter;          // tap slot of this warp's rows
@@ -1453,7 +1466,7 @@ static int launch_conv2(const void* a1, int B, const Geo& g, const void* w2p, co
 {
     DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, FP8, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-    conv2_kernel<ROWS, FP8, DGRAD><<<grid, 192, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2,
+    conv2_kernel<ROWS, FP8, DGRAD><<<grid, kConv2Threads, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2,
                                                             oscale, mask_src, a2, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
