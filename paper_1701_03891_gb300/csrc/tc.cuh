@@ -89,6 +89,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     }
 }
 
+// Wait that ignores the abort flag: used on exit to let copies in flight land.
+__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > 1000000000ull) return;
+    }
+}
+
 // ---------------------------------------------------------------- bulk copy
 // Global -> shared copy on the TMA engine, completing `bytes` of transaction
 // count on `bar`.  Both addresses 16-byte aligned, bytes a multiple of 16.

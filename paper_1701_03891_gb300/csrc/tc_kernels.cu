@@ -52,14 +52,6 @@ __device__ __forceinline__ uint4 pack16_e4m3(const float* v, float scale)
     return r;
 }
 
-// Wait that ignores the abort flag: used on exit to let copies in flight land.
-__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity)
-{
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > 1000000000ull) return;
-    }
-}
 
 // ---------------------------------------------------------------- packing
 __global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, long long cs, int R,
