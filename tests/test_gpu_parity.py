@@ -108,6 +108,49 @@ def test_forward_bf16_wide(di, n1, n2, ratio, B):
     assert _maxrel(xhat, ref) <= TOL["bf16"]
 
 
+@pytest.mark.parametrize("n1,n2,ratio,B", [
+    (6, 119, 0.10, 2),      # pitch 124: conv3 keeps row sums in its shared-memory ring
+    (6, 120, 0.10, 2),      # pitch 125: conv3 keeps partial outputs instead
+    (1, 4960, 0.10, 2),     # too wide for either ring: row sums through global scratch
+])
+def test_forward_bf16_conv3_modes(di, n1, n2, ratio, B):
+    phi, params, x = _case(n1, n2, ratio, B)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
+    y = net.measure(_cuda(x))
+    xhat = net.forward(y).cpu().numpy()
+    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
+    assert np.all(np.isfinite(xhat))
+    assert _maxrel(xhat, ref) <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("n1,n2,M,B", [
+    (4, 130, 52, 2),        # pitch 135: conv1's input gradient in the partial-output ring
+    (1, 4250, 425, 2),      # too wide for the 64-channel ring: global row-sum scratch
+])
+def test_backward_bf16_wide_train_fc(di, n1, n2, M, B):
+    """bf16 backward with the FC layer trained (conv1's input gradient runs through
+    the fused conv3 kernel over 64 channels) on wide images."""
+    N = n1 * n2
+    phi = synth.gaussian_phi(M, N, seed=7)
+    params = synth.he_params(seed=8, bias_std=0.02)
+    x = synth.dct_sparse_images(B, n1, n2, K=max(4, N // 40), seed=9)
+    y = oracle.measure(phi, x).astype(np.float32)
+    loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi, train_fc=True)
+    net = di.Net(phi, params, n1, n2, prec="bf16", train_fc=True)
+    yd, xd = _cuda(y), _cuda(x)
+    saved = net.new_saved(B)
+    net.forward(yd, saved=saved)
+    loss, dW, db, dWfc = net.backward(yd, xd, saved)
+    assert abs(float(loss) - loss_ref) <= 2e-2 * abs(loss_ref)
+    for i in range(3):
+        for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
+            ref = g[name]
+            err = float(np.linalg.norm(got.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30))
+            assert err <= 5e-2, (name, err)
+    err = float(np.linalg.norm(dWfc.cpu().numpy() - g["wfc"]) / np.linalg.norm(g["wfc"]))
+    assert err <= 5e-2, ("wfc", err)
+
+
 def test_conv2_row_mode_matches_window_mode(di):
     """Both conv2 pipelines (window slabs vs per-row pieces) give identical bits."""
     import subprocess, sys, os, json
