@@ -157,13 +157,14 @@ def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
     import oracle
     oracle.build()
     done, t0 = 0, time.perf_counter()
-    errs = []
+    errs, dps = [], []
     chunk = 4
     while done < x.shape[0] and (time.perf_counter() - t0) < args.cpu_seconds:
         xs = x[done:done + chunk]
         ref = oracle.forward(oracle.measure(phi, xs), params, n, n, phi=phi)
         if gpu_xhat is not None:
             errs.append(oracle.rel_l2(gpu_xhat[done:done + chunk], ref))
+            dps.append(np.abs(oracle.psnr(gpu_xhat[done:done + chunk], xs) - oracle.psnr(ref, xs)))
         done += xs.shape[0]
     dt = time.perf_counter() - t0
     out = {"value": done / dt, "unit": "images/s", "cores": oracle.num_threads(), "kind": "oracle",
@@ -171,6 +172,7 @@ def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
                      % (done, x.shape[0], dt)}
     if errs:
         out["bf16_vs_oracle_max_rel_l2"] = float(np.max(np.concatenate(errs)))
+        out["bf16_vs_oracle_max_psnr_diff_db"] = float(np.max(np.concatenate(dps)))
     return out
 
 
