@@ -149,6 +149,15 @@ int deepinv_net_measure(deepinv_net* net, const float* x, int B, float* y, void*
 /* Bytes of the buffer deepinv_forward fills for deepinv_backward at batch B. */
 size_t deepinv_saved_bytes(const deepinv_net* net, int B);
 
+/* Activation budget, in bytes, of a deepinv_backward called without a saved
+ * buffer: it recomputes the forward pass in chunks of as many images as have
+ * activations (deepinv_saved_bytes) within `bytes` (at least one image per
+ * chunk; 0, the default, means the whole batch at once).  The library keeps
+ * one chunk's activations and, with more than one chunk, scratch for one set
+ * of gradients.  Trades one extra forward pass for memory when B x image size
+ * would not fit. */
+int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes);
+
 /* x^ = M(y, Omega) (Sec. 4): FC layer, reshape to n1 x n2, conv1 + ReLU,
  * conv2 + ReLU, conv3 (+ ReLU when final_relu).
  * y [B][M] -> xhat [B][N].  `saved` is NULL for inference, or a device buffer
@@ -172,8 +181,11 @@ int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, flo
 
 /* Gradient of L(Omega) = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4) by
  * backpropagation.  y [B][M] and x [B][N] are the batch; `saved` is the
- * buffer a deepinv_forward of this same y filled.  Writes dW[l] (shape of
- * w[l]), db[l] (shape of b[l]), dWfc [N][M] (only when train_fc; else pass
+ * buffer a deepinv_forward of this same y filled, or NULL: then the forward
+ * activations are recomputed here, in chunks of images whose activations fit
+ * the network's activation budget (deepinv_net_set_act_budget; one chunk when
+ * it is 0), the chunks' gradients added in chunk order.  Writes dW[l] (shape
+ * of w[l]), db[l] (shape of b[l]), dWfc [N][M] (only when train_fc; else pass
  * NULL) and *loss (one device double).  All outputs are overwritten. */
 int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
                      float* const dW[3], float* const db[3], float* dWfc, double* loss,

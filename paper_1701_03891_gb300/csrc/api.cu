@@ -108,6 +108,13 @@ struct deepinv_net {
     char* bws = nullptr;
     size_t bws_bytes = 0;
     int bws_B = 0;
+    // activation recomputation: budget for the activations of one chunk, the
+    // chunk's saved-activation buffer and the gradient scratch of later chunks
+    size_t act_budget = 0;
+    char* rsaved = nullptr;
+    size_t rsaved_bytes = 0;
+    char* gacc = nullptr;
+    size_t gacc_bytes = 0;
     // profiler: event pool and (stage, start event, end event) spans
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -342,6 +349,8 @@ void free_net(deepinv_net* n)
     cudaFree(n->w1t);
     cudaFree(n->ws);
     cudaFree(n->bws);
+    cudaFree(n->rsaved);
+    cudaFree(n->gacc);
     for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
     delete n;
 }
@@ -495,8 +504,10 @@ BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
     return w;
 }
 
-int backward_tc(deepinv_net* n, const float* y, const float* x, int B, const Saved& sv, float* const dW[3],
-                float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+// Bnorm: the batch the loss is normalised by, (1 / Bnorm) sum_b ||x^_b - x_b||^2
+// (B itself, or the whole batch when these B images are one chunk of it).
+int backward_tc(deepinv_net* n, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
+                float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
 {
     const Geo& g = n->geo;
     const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2;
@@ -521,7 +532,7 @@ int backward_tc(deepinv_net* n, const float* y, const float* x, int B, const Sav
     int* status = device_status_word();
     DI_REQUIRE(status, "no device status word");
     // dL/dz3 = 2 (x^ - x) / B (times [x^ > 0] with final_relu) and the loss in float64
-    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, B, n->d.final_relu, w.g3, w.lpart, loss, st));
+    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, Bnorm, n->d.final_relu, w.g3, w.lpart, loss, st));
     DI_TRY(grad_plane(w.g3, B, g, w.g3p, st));
     // conv3: bias and weight gradients, input gradient times [a2 > 0] -> g2
     DI_TRY(plane_channel_sums(w.g3p, B, 1, g, w.bpart, db[2], st));
@@ -595,6 +606,165 @@ void net_ws_staging(const deepinv_net* n, char* ws, int max_B, float** y_dev, fl
 }  // namespace di
 
 // ================================================================ C ABI
+namespace {
+
+// Backward of the float32 path (NCHW activations in `sv`); Bnorm as in backward_tc.
+int backward_f32(deepinv_net* net, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
+                 float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+{
+    const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
+    const int l1 = net->d.l1, l2 = net->d.l2;
+    size_t maxw = 0;
+    for (int l = 0; l < 3; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;
+    auto carve_bwd = [&](char* base, float** g3, float** gA, float** gB, float** dxt, float** fxt, float** fa1,
+                         float** fa2, float** wt, double** wpart, double** lpart) {
+        Arena a{base, 0};
+        *g3 = a.take<float>((size_t)B * N);
+        *gA = a.take<float>((size_t)B * l2 * N);
+        *gB = a.take<float>((size_t)B * l1 * N);
+        *dxt = a.take<float>((size_t)B * N);
+        if (net->tc) {
+            *fxt = a.take<float>((size_t)B * N);
+            *fa1 = a.take<float>((size_t)B * l1 * N);
+            *fa2 = a.take<float>((size_t)B * l2 * N);
+        } else {
+            *fxt = sv.fxt;
+            *fa1 = sv.fa1;
+            *fa2 = sv.fa2;
+        }
+        *wt = a.take<float>(maxw);
+        *wpart = a.take<double>((size_t)kWgradChunks * maxw);
+        *lpart = a.take<double>(kLossBlocks);
+        return align_up(a.off, 256);
+    };
+    float *g3, *gA, *gB, *dxt, *fxt, *fa1, *fa2, *wt;
+    double *wpart, *lpart;
+    const size_t need = carve_bwd(nullptr, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+    if (need > net->bws_bytes) {
+        DI_CUDA(cudaStreamSynchronize(st));
+        cudaFree(net->bws);
+        net->bws = nullptr;
+        net->bws_bytes = 0;
+        if (cudaMalloc(&net->bws, need) != cudaSuccess) {
+            cudaGetLastError();
+            net->bws = nullptr;
+            set_error("backward workspace of %zu bytes: out of device memory", need);
+            return DEEPINV_ENOMEM;
+        }
+        net->bws_bytes = need;
+    }
+    carve_bwd(net->bws, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+
+    if (net->tc) {
+        DI_TRY(plane_to_nchw(sv.xt, B, 1, net->geo, fxt, st));
+        DI_TRY(plane_to_nchw(sv.a1, B, l1, net->geo, fa1, st));
+        DI_TRY(plane_to_nchw(sv.a2, B, l2, net->geo, fa2, st));
+    }
+    // dL/dz3 = 2 (x^ - x) / B, and the loss in float64
+    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, Bnorm, net->d.final_relu, g3, lpart, loss, st));
+    // conv3
+    DI_TRY(conv_wgrad_f32(fa2, g3, B, l2, H, W, 1, k, wpart, dW[2], db[2], st));
+    DI_TRY(conv_dgrad_f32(g3, B, 1, H, W, net->w[2], l2, k, wt, gA, st));
+    DI_TRY(relu_mask_f32(gA, fa2, (long long)B * l2 * N, st));
+    // conv2
+    DI_TRY(conv_wgrad_f32(fa1, gA, B, l1, H, W, l2, k, wpart, dW[1], db[1], st));
+    DI_TRY(conv_dgrad_f32(gA, B, l2, H, W, net->w[1], l1, k, wt, gB, st));
+    DI_TRY(relu_mask_f32(gB, fa1, (long long)B * l1 * N, st));
+    // conv1
+    DI_TRY(conv_wgrad_f32(fxt, gB, B, 1, H, W, l1, k, wpart, dW[0], db[0], st));
+    if (net->d.train_fc) {
+        DI_TRY(conv_dgrad_f32(gB, B, l1, H, W, net->w[0], 1, k, wt, dxt, st));
+        // dWfc[j][i] = sum_b dx~[b][j] y[b][i]
+        DI_TRY(sgemm(N, M, B, dxt, 1, N, y, M, 1, dWfc, M, st));
+    }
+    return DEEPINV_OK;
+}
+
+int backward_run(deepinv_net* net, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
+                 float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+{
+    if (net->tc) return backward_tc(net, y, x, B, Bnorm, sv, dW, db, dWfc, loss, st);
+    return backward_f32(net, y, x, B, Bnorm, sv, dW, db, dWfc, loss, st);
+}
+
+// Grow a library-owned device buffer to at least `need` bytes (synchronises when it grows).
+int grow(char** buf, size_t* bytes, size_t need, const char* what, cudaStream_t st)
+{
+    if (need <= *bytes && *buf) return DEEPINV_OK;
+    DI_CUDA(cudaStreamSynchronize(st));
+    cudaFree(*buf);
+    *buf = nullptr;
+    *bytes = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        set_error("%s of %zu bytes: out of device memory", what, need);
+        return DEEPINV_ENOMEM;
+    }
+    *bytes = need;
+    return DEEPINV_OK;
+}
+
+// Backward without a saved buffer: the forward activations are recomputed in
+// chunks of images whose activations fit the network's activation budget (one
+// chunk when the budget is 0), each chunk's gradients added to the first
+// chunk's in chunk order (deterministic).  The loss and its gradient stay
+// normalised by the whole batch.
+int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, float* const dW[3],
+                       float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+{
+    const int N = net->N, M = net->d.M;
+    int Bc = B;
+    if (net->act_budget) {
+        const size_t per = carve_saved(net, 1, nullptr).bytes;
+        Bc = (int)(net->act_budget / per < (size_t)B ? net->act_budget / per : (size_t)B);
+        if (Bc < 1) Bc = 1;
+        while (Bc > 1 && carve_saved(net, Bc, nullptr).bytes > net->act_budget) --Bc;
+    }
+    DI_TRY(grow(&net->rsaved, &net->rsaved_bytes, carve_saved(net, Bc, nullptr).bytes, "recomputation buffer", st));
+    DI_TRY(ensure_ws(net, Bc, st));
+    const FwdWs fw = carve_fwd(net, net->ws_B, net->ws);
+    // gradient scratch of the chunks after the first: dW[3], db[3], dWfc, loss
+    float* gW[3];
+    float* gB[3];
+    float* gFc = nullptr;
+    double* gL = nullptr;
+    if (Bc < B) {
+        Arena a{nullptr, 0};
+        for (int l = 0; l < 3; ++l) a.take<float>(wsize(net, l));
+        for (int l = 0; l < 3; ++l) a.take<float>(bsize(net, l));
+        if (net->d.train_fc) a.take<float>((size_t)N * M);
+        a.take<double>(1);
+        DI_TRY(grow(&net->gacc, &net->gacc_bytes, align_up(a.off, 256), "gradient scratch", st));
+        Arena g{net->gacc, 0};
+        for (int l = 0; l < 3; ++l) gW[l] = g.take<float>(wsize(net, l));
+        for (int l = 0; l < 3; ++l) gB[l] = g.take<float>(bsize(net, l));
+        if (net->d.train_fc) gFc = g.take<float>((size_t)N * M);
+        gL = g.take<double>(1);
+    }
+    for (int b0 = 0; b0 < B; b0 += Bc) {
+        const int nb = B - b0 < Bc ? B - b0 : Bc;
+        const float* yc = y + (size_t)b0 * M;
+        const float* xc = x + (size_t)b0 * N;
+        DI_TRY(forward_impl(net, yc, nb, fw.xhd, net->rsaved, st));
+        const Saved sv = carve_saved(net, nb, net->rsaved);
+        if (b0 == 0) {
+            DI_TRY(backward_run(net, yc, xc, nb, B, sv, dW, db, dWfc, loss, st));
+            continue;
+        }
+        DI_TRY(backward_run(net, yc, xc, nb, B, sv, gW, gB, gFc, gL, st));
+        for (int l = 0; l < 3; ++l) {
+            DI_TRY(accumulate_f32(dW[l], gW[l], (long long)wsize(net, l), st));
+            DI_TRY(accumulate_f32(db[l], gB[l], (long long)bsize(net, l), st));
+        }
+        if (net->d.train_fc) DI_TRY(accumulate_f32(dWfc, gFc, (long long)N * M, st));
+        DI_TRY(accumulate_f64(loss, gL, 1, st));
+    }
+    return DEEPINV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* deepinv_last_error(void) { return di::g_err; }
@@ -811,13 +981,20 @@ int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, flo
     return DEEPINV_OK;
 }
 
+int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes)
+{
+    DI_REQUIRE(net, "net is NULL");
+    net->act_budget = bytes;
+    return DEEPINV_OK;
+}
+
 int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
                      float* const dW[3], float* const db[3], float* dWfc, double* loss, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 1, "bad batch %d", B);
-    DI_REQUIRE(y && x && saved && dW && db && loss, "null pointer");
+    DI_REQUIRE(y && x && dW && db && loss, "null pointer");
     for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
     if (net->fp8) {
@@ -825,75 +1002,9 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
         return DEEPINV_EUNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
-    const int l1 = net->d.l1, l2 = net->d.l2;
+    if (!saved) return backward_recompute(net, y, x, B, dW, db, dWfc, loss, st);
     const Saved sv = carve_saved(net, B, static_cast<char*>(const_cast<void*>(saved)));
-    if (net->tc) return backward_tc(net, y, x, B, sv, dW, db, dWfc, loss, st);
-
-    size_t maxw = 0;
-    for (int l = 0; l < 3; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;
-    auto carve_bwd = [&](char* base, float** g3, float** gA, float** gB, float** dxt, float** fxt, float** fa1,
-                         float** fa2, float** wt, double** wpart, double** lpart) {
-        Arena a{base, 0};
-        *g3 = a.take<float>((size_t)B * N);
-        *gA = a.take<float>((size_t)B * l2 * N);
-        *gB = a.take<float>((size_t)B * l1 * N);
-        *dxt = a.take<float>((size_t)B * N);
-        if (net->tc) {
-            *fxt = a.take<float>((size_t)B * N);
-            *fa1 = a.take<float>((size_t)B * l1 * N);
-            *fa2 = a.take<float>((size_t)B * l2 * N);
-        } else {
-            *fxt = sv.fxt;
-            *fa1 = sv.fa1;
-            *fa2 = sv.fa2;
-        }
-        *wt = a.take<float>(maxw);
-        *wpart = a.take<double>((size_t)kWgradChunks * maxw);
-        *lpart = a.take<double>(kLossBlocks);
-        return align_up(a.off, 256);
-    };
-    float *g3, *gA, *gB, *dxt, *fxt, *fa1, *fa2, *wt;
-    double *wpart, *lpart;
-    const size_t need = carve_bwd(nullptr, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
-    if (need > net->bws_bytes) {
-        DI_CUDA(cudaStreamSynchronize(st));
-        cudaFree(net->bws);
-        net->bws = nullptr;
-        net->bws_bytes = 0;
-        if (cudaMalloc(&net->bws, need) != cudaSuccess) {
-            cudaGetLastError();
-            net->bws = nullptr;
-            set_error("backward workspace of %zu bytes: out of device memory", need);
-            return DEEPINV_ENOMEM;
-        }
-        net->bws_bytes = need;
-    }
-    carve_bwd(net->bws, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
-
-    if (net->tc) {
-        DI_TRY(plane_to_nchw(sv.xt, B, 1, net->geo, fxt, st));
-        DI_TRY(plane_to_nchw(sv.a1, B, l1, net->geo, fa1, st));
-        DI_TRY(plane_to_nchw(sv.a2, B, l2, net->geo, fa2, st));
-    }
-    // dL/dz3 = 2 (x^ - x) / B, and the loss in float64
-    DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, B, net->d.final_relu, g3, lpart, loss, st));
-    // conv3
-    DI_TRY(conv_wgrad_f32(fa2, g3, B, l2, H, W, 1, k, wpart, dW[2], db[2], st));
-    DI_TRY(conv_dgrad_f32(g3, B, 1, H, W, net->w[2], l2, k, wt, gA, st));
-    DI_TRY(relu_mask_f32(gA, fa2, (long long)B * l2 * N, st));
-    // conv2
-    DI_TRY(conv_wgrad_f32(fa1, gA, B, l1, H, W, l2, k, wpart, dW[1], db[1], st));
-    DI_TRY(conv_dgrad_f32(gA, B, l2, H, W, net->w[1], l1, k, wt, gB, st));
-    DI_TRY(relu_mask_f32(gB, fa1, (long long)B * l1 * N, st));
-    // conv1
-    DI_TRY(conv_wgrad_f32(fxt, gB, B, 1, H, W, l1, k, wpart, dW[0], db[0], st));
-    if (net->d.train_fc) {
-        DI_TRY(conv_dgrad_f32(gB, B, l1, H, W, net->w[0], 1, k, wt, dxt, st));
-        // dWfc[j][i] = sum_b dx~[b][j] y[b][i]
-        DI_TRY(sgemm(N, M, B, dxt, 1, N, y, M, 1, dWfc, M, st));
-    }
-    return DEEPINV_OK;
+    return backward_run(net, y, x, B, B, sv, dW, db, dWfc, loss, st);
 }
 
 int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float* const db[3], const float* dWfc,

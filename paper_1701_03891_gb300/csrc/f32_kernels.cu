@@ -304,6 +304,14 @@ __global__ void mse_final_kernel(const double* __restrict__ part, int nb, int B,
     }
 }
 
+// dst[i] += src[i] (gradients of later recomputation chunks, added in chunk order).
+template <typename T>
+__global__ void accumulate_kernel(T* __restrict__ dst, const T* __restrict__ src, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+
 __global__ void sgd_momentum_kernel(float* __restrict__ w, float* __restrict__ v,
                                     const float* __restrict__ g, long long n, float lr, float mu)
 {
@@ -364,6 +372,22 @@ int mse_loss_grad(const float* xhat, const float* x, long long n, int B, int fin
     mse_partial_kernel<<<kLossBlocks, 256, 0, st>>>(xhat, x, n, B, final_relu, g, part);
     DI_LAUNCH_CHECK();
     mse_final_kernel<<<1, 32, 0, st>>>(part, kLossBlocks, B, loss);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int accumulate_f32(float* dst, const float* src, long long n, cudaStream_t st)
+{
+    if (n <= 0) return DEEPINV_OK;
+    accumulate_kernel<float><<<grid_for(n), 256, 0, st>>>(dst, src, n);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int accumulate_f64(double* dst, const double* src, long long n, cudaStream_t st)
+{
+    if (n <= 0) return DEEPINV_OK;
+    accumulate_kernel<double><<<grid_for(n), 256, 0, st>>>(dst, src, n);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

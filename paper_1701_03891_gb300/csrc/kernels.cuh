@@ -24,6 +24,9 @@ int relu_mask_f32(float* g, const float* a, long long n, cudaStream_t st);
 int mse_loss_grad(const float* xhat, const float* x, long long n, int B, int final_relu, float* g,
                   double* part, double* loss, cudaStream_t st);
 int transpose_f32(const float* src, int R, int C, float* dst, cudaStream_t st);
+// dst += src, element-wise.
+int accumulate_f32(float* dst, const float* src, long long n, cudaStream_t st);
+int accumulate_f64(double* dst, const double* src, long long n, cudaStream_t st);
 int sgd_momentum_f32(float* w, float* v, const float* g, long long n, float lr, float mu,
                      cudaStream_t st);
 

@@ -77,6 +77,7 @@ SIGNATURES = {
     "deepinv_net_calibrate": (_I, [_P, _P, _I, _P]),
     "deepinv_net_get_desc": (_I, [_P, ctypes.POINTER(NetDesc)]),
     "deepinv_net_reserve": (_I, [_P, _I, _P]),
+    "deepinv_net_set_act_budget": (_I, [_P, ctypes.c_size_t]),
     "deepinv_net_measure": (_I, [_P, _P, _I, _P, _P]),
     "deepinv_saved_bytes": (ctypes.c_size_t, [_P, _I]),
     "deepinv_forward": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -272,8 +273,14 @@ class Net:
                 if self.desc.train_fc else None)
         return dW, db, dWfc
 
-    def backward(self, y, x, saved, grads=None, stream=None):
-        """Gradient of L = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4).  Returns (loss tensor, dW, db, dWfc)."""
+    def set_act_budget(self, nbytes: int):
+        """Activation budget of backward(saved=None): the forward activations are
+        recomputed in chunks of images whose activations fit nbytes (0: one chunk)."""
+        _check(lib().deepinv_net_set_act_budget(self._h, int(nbytes)))
+
+    def backward(self, y, x, saved=None, grads=None, stream=None):
+        """Gradient of L = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4).  Returns (loss tensor, dW, db, dWfc).
+        saved: the buffer forward(..., saved=) filled, or None to recompute the activations."""
         import torch
         _need_f32_cuda(y, "y")
         _need_f32_cuda(x, "x")

@@ -305,6 +305,48 @@ def test_backward_bf16_shapes(di, n1, n2, M, B):
             assert err <= 5e-2, (name, err)
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_backward_recompute(di, prec):
+    """backward without a saved buffer recomputes the activations: with no budget
+    (one chunk) it is bit-identical to the saved path; with a budget of three
+    images' activations it runs three chunks (3 + 3 + 1) whose gradients agree
+    with the saved path up to summation order, and with the oracle."""
+    n1 = n2 = 24
+    N, M, B = n1 * n2, 144, 7
+    phi = synth.gaussian_phi(M, N, seed=10)
+    params = synth.he_params(seed=11, bias_std=0.02)
+    x = synth.dct_sparse_images(B, n1, n2, K=20, seed=12)
+    y = oracle.measure(phi, x).astype(np.float32)
+    net = di.Net(phi, params, n1, n2, prec=prec, train_fc=True)
+    yd, xd = _cuda(y), _cuda(x)
+    saved = net.new_saved(B)
+    net.forward(yd, saved=saved)
+    ref = [t.clone() if t is not None else None for t in _flat(net.backward(yd, xd, saved))]
+    one = _flat(net.backward(yd, xd))                            # recompute, one chunk
+    for a, b in zip(ref, one):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    net.set_act_budget(3 * net.saved_bytes(1) + 4096)            # chunks of 3 images
+    assert net.saved_bytes(3) <= 3 * net.saved_bytes(1) + 4096 < net.saved_bytes(4)
+    chunked = _flat(net.backward(yd, xd))
+    for a, b in zip(ref, chunked):
+        a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - b) <= 1e-5 * max(np.linalg.norm(a), 1e-30)
+    loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi, train_fc=True)
+    tol = 1e-4 if prec == "f32" else 5e-2
+    names = ["loss", "w1", "w2", "w3", "b1", "b2", "b3", "wfc"]
+    for name, got in zip(names, chunked):
+        want = loss_ref if name == "loss" else g[name]
+        got = got.cpu().numpy()
+        err = float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30))
+        assert err <= tol, (name, err)
+    net.close()
+
+
+def _flat(res):
+    loss, dW, db, dWfc = res
+    return [loss] + list(dW) + list(db) + [dWfc]
+
+
 def test_sgd_momentum_step(di):
     n1, n2, phi, params, x, y = _train_case(False)
     net = di.Net(phi, params, n1, n2, prec="f32")
