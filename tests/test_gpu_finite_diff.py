@@ -85,4 +85,4 @@ def test_f32_backward_matches_finite_differences(di):
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - flat[i]) <= 1e-2 * max(scale, abs(flat[i])), (name, int(i), fd, flat[i])
             checked += 1
-    assert checked == 6 * 7
+    assert checked == sum(min(6, g.size) for g in grads.values())
