@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--serve-rates", default="20000,80000,200000",
                     help="offered request rates (requests/s) of the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window per rate")
+    ap.add_argument("--eval", action="store_true",
+                    help="also train 32x32 networks at M/N 0.05/0.10/0.25, clean and 20 dB SNR, and report "
+                         "the recovered images' PSNR and success rate (about 40 s)")
     return ap.parse_args()
 
 
@@ -525,6 +528,13 @@ def run_native(args):
     if rank == 0 and not args.no_train:
         train = train_bench(args)
 
+    evaluation = None
+    if rank == 0 and args.eval:
+        from paper_1701_03891_gb300 import evaluate
+        evaluation = {"workload": "32x32 Voronoi images, 512 training / 64 test, 6000 SGD-momentum steps of 64 "
+                                  "(bf16, FC = Phi^T), step 1e-3 / first loss",
+                      "points": evaluate.sweep(32, ratios=(0.05, 0.10, 0.25), snrs=(None, 20.0))}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, phi, params, x, n, gpu_xhat=bf16_out)
@@ -539,7 +549,8 @@ def run_native(args):
             "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
-            "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "eval_32": evaluation,
+            "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)
