@@ -179,16 +179,30 @@ def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
     return out
 
 
+CONV2_SOURCES = ("tc_kernels.cu", "tc.cuh", "common.cuh")
+CONV2_BEGIN = "// ---------------------------------------------------------------- conv2\n"
+CONV2_END = "// ---------------------------------------------------------------- conv3\n"
+
+
+def conv2_source_hash():
+    """Hash of the conv2 kernel's code: its section of tc_kernels.cu and the headers it uses."""
+    h = hashlib.sha256()
+    for name in CONV2_SOURCES:
+        with open(os.path.join(ROOT, "paper_1701_03891_gb300", "csrc", name)) as f:
+            text = f.read()
+        if name == "tc_kernels.cu":
+            text = text[text.index(CONV2_BEGIN):text.index(CONV2_END)]
+        h.update(text.encode())
+    return h.hexdigest()[:16]
+
+
 def traffic_record():
-    """ncu DRAM bytes per conv2 image from profiles/, valid only for the current kernel source."""
-    src = os.path.join(ROOT, "paper_1701_03891_gb300", "csrc", "tc_kernels.cu")
+    """ncu DRAM bytes per conv2 image from profiles/, valid only while conv2's code is unchanged."""
     rec = os.path.join(ROOT, "profiles", "conv2_traffic.json")
     try:
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
         with open(rec) as f:
             d = json.load(f)
-        if d.get("kernel_sha") == h:
+        if d.get("kernel_sha") == conv2_source_hash():
             return float(d["dram_bytes_per_image"])
     except Exception:
         pass

@@ -1,16 +1,17 @@
 // bfloat16 tcgen05 tensor-core kernels of libdeepinv (sm_103a).
 //
 //  * tc_gemm   -- y = Phi x (Sec. 1) and the FC layer x~ = Phi^T y (Sec. 4).
-//  * conv1_tc  -- Eq. (1), layer 1 (1 -> 64 filters of 11 x 11) as an
-//                 im2col GEMM: M = 128 positions, N = 64 filters, K = 121 taps.
+//  * conv1_tc  -- Eq. (1), layer 1 (1 -> 64 filters of 11 x 11): per kernel
+//                 row one GEMM with M = 128 positions, N = 64 filters, K = 16
+//                 columns, the A operand read straight from an expanded window.
 //  * conv2_tc  -- layer 2 (64 -> 32), 95 % of the network's flops, as a
 //                 tap-stacked implicit GEMM (below).
-//  * conv3_tc  -- layer 3 (32 -> 1): per-row partial sums T by GEMM
-//                 (M = 128 positions, N = 11 kernel rows, K = 11 columns x 32
-//                 channels), then a sum over the 11 kernel rows.
+//  * conv3_tc  -- layer 3 (32 -> 1): per-row partial sums by GEMM (N = kernel
+//                 row x column phase), summed over the 11 kernel rows in a
+//                 shared-memory ring in the same kernel.
 //
-// All operands are K-major without swizzle (see tc.cuh), moved by the TMA
-// engine with 1-D bulk copies; accumulators live in TMEM.
+// Operands are K-major without swizzle (see tc.cuh; conv1's A is MN-major),
+// moved by the TMA engine with 1-D bulk copies; accumulators live in TMEM.
 #include <cstdlib>
 
 #include <cuda_fp8.h>
