@@ -618,16 +618,19 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
 // 33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253 valid outputs
 // per tile (the last 3 columns lack their slot-3 partner).
 //
-// Persistent CTAs, 7 warps: warp 6 streams the input window (slabs of 128
-// positions x 64 channels, freed as soon as the last kernel row reading them
-// has been multiplied) and warp 0 the weights ((dy, s) blocks of 16 KB through
-// a ring), each on its own so that neither waits for the other; warp 1 owns
-// TMEM (2 accumulators x 256 columns) and issues MMAs; warps 2..5 drain the
-// accumulator of the previous tile.
+// Persistent CTAs, 7 warps: warp 6 streams the input (below) and warp 0 the
+// weights ((dy, s) blocks of 16 KB through a ring), each on its own so that
+// neither waits for the other; warp 1 owns TMEM (2 accumulators x 256
+// columns) and issues MMAs; warps 2..5 drain the accumulator of the previous
+// tile.
 //
-// Wide images (the window of 10 P + 264 positions does not fit in shared
-// memory) use row mode: the producer streams, for every kernel row dy, just
-// the 264 positions that row's MMAs read, through a ring of kRowSlots pieces.
+// Row mode (the default): the producer streams, for every kernel row dy, just
+// the 272 positions that row's MMAs read, through a ring of kRowSlots pieces.
+// Window mode keeps the whole window of 10 P + 272 positions of a tile as
+// slabs (freed as soon as the last kernel row reading them has been
+// multiplied); it streams a third of the bytes but runs about 12 % slower, and
+// neither 128-byte-aligned operand offsets nor padded channel strides close
+// the gap.
 constexpr int kW2Stages = 4;
 constexpr int kConv2Threads = 224;
 constexpr int kMaxSlabs = 10;
@@ -1436,16 +1439,17 @@ static size_t conv2_smem_bytes(const Geo& g, bool rows, bool fp8)
     return win + (size_t)kW2Stages * wstage + kXBytes + sizeof(Conv2Smem);
 }
 
-// Window mode when the whole input window of a tile fits in shared memory.
-// DEEPINV_CONV2_FORCE_ROWS=1 in the environment selects row mode everywhere
+// Row mode by default (64 x 64, batch 1024: 1.27 ms against 1.42 ms in window
+// mode; wider images fit only row mode).  DEEPINV_CONV2_WINDOW=1 in
+// the environment selects window mode where the window fits in shared memory
 // (both modes give bit-identical results; the tests compare them).
 static bool conv2_window_mode(const Geo& g, bool fp8)
 {
-    static const bool force_rows = [] {
-        const char* e = getenv("DEEPINV_CONV2_FORCE_ROWS");
+    static const bool window = [] {
+        const char* e = getenv("DEEPINV_CONV2_WINDOW");
         return e && e[0] == '1';
     }();
-    return !force_rows && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false, fp8) <= 227 * 1024;
+    return window && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false, fp8) <= 227 * 1024;
 }
 
 bool conv2_tc_supported(const Geo& g)

@@ -164,9 +164,9 @@ def test_conv2_row_mode_matches_window_mode(di):
         "np.save(sys.argv[1], out)" % os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import tempfile
     outs = []
-    for force in ("0", "1"):
+    for window in ("0", "1"):
         f = tempfile.mktemp(suffix=".npy")
-        env = dict(os.environ, DEEPINV_CONV2_FORCE_ROWS=force)
+        env = dict(os.environ, DEEPINV_CONV2_WINDOW=window)
         subprocess.check_call([sys.executable, "-c", code, f], env=env)
         outs.append(np.load(f))
         os.unlink(f)
