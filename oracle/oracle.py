@@ -11,7 +11,9 @@ What it computes, each step citing the paper:
   * ``fc``           x~ = W y, W = Phi^T by default          (Sec. 4, the fixed FC layer)
   * ``conv_same``    Eq. (1) before the ReLU, 'same' size    (Sec. 4, Eq. 1; crop S)
   * ``forward``      x^ = M(y, Omega): FC, reshape n1 x n2, three conv layers,
-                     ReLU after the first two                (Sec. 4, Sec. 5 layer sizes)
+                     ReLU after the first two                (Sec. 4, Sec. 5 layer sizes);
+                     more layers in between when params hold them (the deeper
+                     networks Sec. 5 names as future work)
   * ``mse_loss``     L = (1/l) sum_i ||x^(i) - x(i)||^2      (Sec. 4, the MSE objective)
   * ``backward``     the hand-derived gradient of that loss  (Sec. 4, backpropagation)
   * ``rel_l2``, ``psnr``, ``success``                        (Sec. 5 metrics)
@@ -171,32 +173,44 @@ def relu(z) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- the network
+def num_layers(params: dict) -> int:
+    """Number L of convolutional layers: params holds w1, b1, ..., wL, bL."""
+    L = 0
+    while "w%d" % (L + 1) in params:
+        L += 1
+    return L
+
+
 def forward(y, params: dict, n1: int, n2: int, *, phi=None, wfc=None, final_relu: bool = False,
             keep: bool = False):
     """x^ = M(y, Omega) (Sec. 4).
 
-    y [B][M]; params holds w1,b1,w2,b2,w3,b3 with w_l [l_l][l_{l-1}][k][k].
+    y [B][M]; params holds w1,b1,...,wL,bL with w_l [l_l][l_{l-1}][k][k]
+    (L = 3 is the paper's network; a larger L adds layers in between, the
+    larger-capacity networks Sec. 5 leaves to future work).
     The FC weights are Phi^T (fixed, Sec. 4) unless ``wfc`` [N][M] is given.
-    The proxy x~ = W y is reshaped row-major to n1 x n2 (Sec. 4).  The three
-    convolutional layers follow Eq. (1); ReLU follows conv1 and conv2, and
-    conv3 too only when ``final_relu`` (the paper's literal 'each layer').
-    Returns x^ [B][n1*n2] (and the activations when ``keep``).
+    The proxy x~ = W y is reshaped row-major to n1 x n2 (Sec. 4).  Every
+    convolutional layer follows Eq. (1); ReLU follows every layer but the
+    last, and the last too only when ``final_relu`` (the paper's literal
+    'each layer').  Returns x^ [B][n1*n2] (and, when ``keep``, the proxy
+    xt, a0 = the reshaped proxy and z_l, a_l for every layer).
     """
     y = _f64(y)
     B = y.shape[0]
+    L = num_layers(params)
     if wfc is None:
         wfc = _f64(phi).T
     xt = fc(wfc, y)
-    a0 = xt.reshape(B, 1, n1, n2)
-    z1 = conv_same(a0, params["w1"], params["b1"])
-    a1 = relu(z1)
-    z2 = conv_same(a1, params["w2"], params["b2"])
-    a2 = relu(z2)
-    z3 = conv_same(a2, params["w3"], params["b3"])
-    out = relu(z3) if final_relu else z3
-    xhat = out.reshape(B, n1 * n2)
+    a = xt.reshape(B, 1, n1, n2)
+    c = dict(xt=xt, a0=a)
+    for l in range(1, L + 1):
+        z = conv_same(a, params["w%d" % l], params["b%d" % l])
+        a = relu(z) if (l < L or final_relu) else z
+        c["z%d" % l] = z
+        c["a%d" % l] = a
+    xhat = a.reshape(B, n1 * n2)
     if keep:
-        return xhat, dict(xt=xt, a0=a0, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3)
+        return xhat, c
     return xhat
 
 
@@ -213,33 +227,31 @@ def backward(y, x, params: dict, n1: int, n2: int, *, phi=None, wfc=None,
     """Gradient of ``mse_loss(forward(y), x)`` with respect to every parameter.
 
     Chain rule through Sec. 4's network, layer by layer from the output:
-      g3 = dL/dz3 = 2 (x^ - x) / B        (times [z3 > 0] when final_relu)
-      dW3, db3 from g3 and a2;  da2 = dgrad(g3);  g2 = da2 * [z2 > 0]
-      dW2, db2 from g2 and a1;  da1 = dgrad(g2);  g1 = da1 * [z1 > 0]
-      dW1, db1 from g1 and a0 = x~;  with train_fc: dx~ = dgrad(g1), dWfc = sum_b dx~ y^T.
+      g_L = dL/dz_L = 2 (x^ - x) / B        (times [z_L > 0] when final_relu)
+      for l = L .. 1:  dW_l, db_l from g_l and a_{l-1};
+                       for l > 1:  g_{l-1} = dgrad(g_l) * [z_{l-1} > 0]
+      with train_fc: dx~ = dgrad(g_1), dWfc = sum_b dx~ y^T.
     The ReLU derivative at 0 is taken as 0.
     Returns (loss, grads dict).
     """
     y, x = _f64(y), _f64(x)
     B = y.shape[0]
+    L = num_layers(params)
     if wfc is None:
         wfc = _f64(phi).T
     xhat, c = forward(y, params, n1, n2, wfc=wfc, final_relu=final_relu, keep=True)
     loss = mse_loss(xhat, x)
     k = params["w1"].shape[-1]
-    g3 = (2.0 / B) * (xhat - x.reshape(B, -1)).reshape(c["z3"].shape)
+    g = (2.0 / B) * (xhat - x.reshape(B, -1)).reshape(c["z%d" % L].shape)
     if final_relu:
-        g3 = g3 * (c["z3"] > 0)
-    dw3, db3 = conv_same_wgrad(c["a2"], g3, k)
-    da2 = conv_same_dgrad(g3, params["w3"], n1, n2)
-    g2 = da2 * (c["z2"] > 0)
-    dw2, db2 = conv_same_wgrad(c["a1"], g2, k)
-    da1 = conv_same_dgrad(g2, params["w2"], n1, n2)
-    g1 = da1 * (c["z1"] > 0)
-    dw1, db1 = conv_same_wgrad(c["a0"], g1, k)
-    grads = dict(w1=dw1, b1=db1, w2=dw2, b2=db2, w3=dw3, b3=db3)
+        g = g * (c["z%d" % L] > 0)
+    grads = {}
+    for l in range(L, 0, -1):
+        grads["w%d" % l], grads["b%d" % l] = conv_same_wgrad(c["a%d" % (l - 1)], g, k)
+        if l > 1:
+            g = conv_same_dgrad(g, params["w%d" % l], n1, n2) * (c["z%d" % (l - 1)] > 0)
     if train_fc:
-        dxt = conv_same_dgrad(g1, params["w1"], n1, n2).reshape(B, n1 * n2)
+        dxt = conv_same_dgrad(g, params["w1"], n1, n2).reshape(B, n1 * n2)
         grads["wfc"] = fc_wgrad(dxt, y)
     return loss, grads
 

@@ -35,13 +35,15 @@ def gaussian_phi(M: int, N: int, seed: int = 0) -> np.ndarray:
 
 
 def he_params(l1: int = 64, l2: int = 32, l3: int = 1, k: int = 11, seed: int = 1,
-              bias_std: float = 0.0) -> dict:
+              bias_std: float = 0.0, hidden: int = 0) -> dict:
     """w_l [l_l][l_{l-1}][k][k] ~ N(0, 2 / (l_{l-1} k^2)), l_0 = 1; biases N(0, bias_std^2)
-    (zero by default).  float32."""
+    (zero by default).  float32.  ``hidden`` inserts that many l2 -> l2 layers
+    between conv2 and the last layer (keys w1..wL in network order, L = 3 + hidden);
+    with hidden = 0 the draws are those of the three-layer network."""
     rng = np.random.default_rng(seed)
     out = {}
-    cins = [1, l1, l2]
-    couts = [l1, l2, l3]
+    cins = [1, l1] + [l2] * hidden + [l2]
+    couts = [l1, l2] + [l2] * hidden + [l3]
     for i, (ci, co) in enumerate(zip(cins, couts), start=1):
         std = math.sqrt(2.0 / (ci * k * k))
         out["w%d" % i] = (rng.standard_normal((co, ci, k, k)) * std).astype(np.float32)

@@ -125,23 +125,25 @@ def test_conv_linearity(orc):
 
 
 # ------------------------------------------------------------------ the network (Sec. 4)
-def _small_net(seed=0, l1=3, l2=2, l3=1, k=3, bias_std=0.1):
-    return synth.he_params(l1, l2, l3, k, seed=seed, bias_std=bias_std)
+def _small_net(seed=0, l1=3, l2=2, l3=1, k=3, bias_std=0.1, hidden=0):
+    return synth.he_params(l1, l2, l3, k, seed=seed, bias_std=bias_std, hidden=hidden)
 
 
-def test_forward_all_positive_is_linear_chain(orc):
+@pytest.mark.parametrize("hidden", [0, 2])
+def test_forward_all_positive_is_linear_chain(orc, hidden):
     """With every weight, bias and input >= 0 no ReLU clips, so the network is
-    the composition of the linear maps (checked with scipy's correlate2d)."""
+    the composition of the linear maps (checked with scipy's correlate2d), for
+    the three-layer network and one with two extra hidden layers."""
     from scipy.signal import correlate2d
     rng = np.random.default_rng(6)
     n1, n2, M = 6, 5, 7
     phi = np.abs(rng.standard_normal((M, n1 * n2)))
     y = np.abs(rng.standard_normal((2, M)))
-    p = {k: np.abs(v).astype(float) for k, v in _small_net().items()}
+    p = {k: np.abs(v).astype(float) for k, v in _small_net(hidden=hidden).items()}
     xhat = orc.forward(y, p, n1, n2, phi=phi)
     for b in range(2):
         a = (phi.T @ y[b]).reshape(1, n1, n2)
-        for l in (1, 2, 3):
+        for l in range(1, 4 + hidden):
             w, bb = p["w%d" % l], p["b%d" % l]
             a = np.stack([bb[co] + sum(correlate2d(a[ci], w[co, ci], mode="same") for ci in range(w.shape[1]))
                           for co in range(w.shape[0])])
@@ -157,6 +159,40 @@ def test_forward_negative_bias_gives_exactly_b3(orc):
     phi = rng.standard_normal((5, 20))
     xhat = orc.forward(rng.standard_normal((3, 5)), p, 4, 5, phi=phi)
     assert np.all(xhat == 0.25)
+
+
+def test_forward_identity_hidden_layers_reduce_to_three_layers(orc):
+    """Hidden layers with centred-delta kernels (W[co][ci] = delta(co, ci) at the
+    centre tap) and zero bias pass their input unchanged: the input is already
+    >= 0 (a ReLU output), so the ReLU after them changes nothing, and the deeper
+    network equals the three-layer one built from the same conv1/conv2/conv3."""
+    rng = np.random.default_rng(15)
+    n1, n2, M = 7, 6, 9
+    phi = rng.standard_normal((M, n1 * n2))
+    y = rng.standard_normal((3, M))
+    p3 = _small_net(seed=5, bias_std=0.1)
+    deep = {"w1": p3["w1"], "b1": p3["b1"], "w2": p3["w2"], "b2": p3["b2"]}
+    l2, k = p3["w2"].shape[0], p3["w2"].shape[-1]
+    eye = np.zeros((l2, l2, k, k))
+    for c in range(l2):
+        eye[c, c, k // 2, k // 2] = 1.0
+    for l in (3, 4):
+        deep["w%d" % l], deep["b%d" % l] = eye, np.zeros(l2)
+    deep["w5"], deep["b5"] = p3["w3"], p3["b3"]
+    np.testing.assert_allclose(orc.forward(y, deep, n1, n2, phi=phi), orc.forward(y, p3, n1, n2, phi=phi),
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_forward_negative_bias_in_last_hidden_layer_gives_exactly_bL(orc):
+    """A large negative bias in the last hidden layer zeroes its output, so x^ is
+    exactly the last layer's bias everywhere."""
+    rng = np.random.default_rng(16)
+    p = _small_net(hidden=2)
+    p["b4"] = np.full(2, -1e6)
+    p["b5"] = np.array([-0.5])
+    phi = rng.standard_normal((5, 20))
+    xhat = orc.forward(rng.standard_normal((3, 5)), p, 4, 5, phi=phi)
+    assert np.all(xhat == -0.5)
 
 
 def test_forward_final_relu_flag(orc):
@@ -213,7 +249,7 @@ def _fd_check(orc, y, x, p, n1, n2, wfc, final_relu, train_fc, coords, h=1e-5, t
 
     def masks(pp, ww):
         _, c = orc.forward(y, pp, n1, n2, wfc=ww, final_relu=final_relu, keep=True)
-        return [c["z1"] > 0, c["z2"] > 0, c["z3"] > 0]
+        return [c["z%d" % l] > 0 for l in range(1, orc.num_layers(pp) + 1)]
 
     checked = 0
     for name, idx in coords:
@@ -251,6 +287,25 @@ def test_gradients_every_coordinate_small_net(orc, final_relu, train_fc):
     if train_fc:
         coords += [("wfc", idx) for idx in np.ndindex(wfc.shape)]
     n = _fd_check(orc, y, x, p, n1, n2, wfc, final_relu, train_fc, coords)
+    assert n >= 0.9 * len(coords)
+
+
+@pytest.mark.parametrize("hidden", [1, 2])
+def test_gradients_every_coordinate_deeper_net(orc, hidden):
+    """Central differences for every parameter of a reduced net with extra hidden
+    layers (k=3, 3/2/(2)/1 filters, 6x5 image, FC trained): pins the layer loop of
+    the backward pass (each layer's mask, its input activation, the order)."""
+    rng = np.random.default_rng(14 + hidden)
+    n1, n2, M, B = 6, 5, 9, 2
+    phi = rng.standard_normal((M, n1 * n2)) / 3
+    y = rng.standard_normal((B, M))
+    x = rng.uniform(0, 1, (B, n1 * n2))
+    p = {k: v.astype(float) for k, v in _small_net(seed=4, bias_std=0.2, hidden=hidden).items()}
+    assert orc.num_layers(p) == 3 + hidden
+    wfc = phi.T.copy()
+    coords = [(n, idx) for n in sorted(p) for idx in np.ndindex(p[n].shape)]
+    coords += [("wfc", idx) for idx in np.ndindex(wfc.shape)]
+    n = _fd_check(orc, y, x, p, n1, n2, wfc, False, True, coords)
     assert n >= 0.9 * len(coords)
 
 
