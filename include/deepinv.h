@@ -67,7 +67,15 @@ typedef struct {
     int final_relu;  /* 1: ReLU after conv3 as well (the paper's "each layer") */
     int train_fc;    /* 1: the FC weights are a trainable copy initialised to Phi^T */
     int prec;        /* deepinv_precision */
+    int hidden;      /* extra l2 -> l2 conv layers (k x k, ReLU) between conv2 and
+                        conv3, 0..DEEPINV_MAX_HIDDEN; 0 is the paper's network.
+                        The network then has L = 3 + hidden conv layers, and every
+                        per-layer array below has L entries in network order:
+                        conv1, conv2, hidden 1..hidden, conv3 (the deeper networks
+                        of larger capacity that Sec. 5 leaves to future work). */
 } deepinv_net_desc;
+
+#define DEEPINV_MAX_HIDDEN 16
 
 typedef struct deepinv_net deepinv_net;       /* opaque; owns weights and workspace */
 
@@ -116,12 +124,14 @@ int deepinv_measure_noalloc(const float* phi, int M, int N, const float* x, int 
                             void* stream);
 
 /* Create a network (Sec. 4).  phi [M][N] is copied (it defines the FC layer,
- * x~ = Phi^T y); w[l] is [l_l][l_{l-1}][k][k] and b[l] is [l_l] for l = 0,1,2
- * (conv1..conv3, l_0 = 1), all device float32, copied into float32 master
- * weights plus the kernel layouts of desc->prec.  Synchronises `stream`.
- * On success *out owns device memory until deepinv_net_destroy. */
+ * x~ = Phi^T y); w[l] is [c_out][c_in][k][k] and b[l] is [c_out] for the
+ * L = 3 + desc->hidden layers l = 0 .. L-1 in network order (conv1: 1 -> l1,
+ * conv2: l1 -> l2, each hidden layer: l2 -> l2, conv3: l2 -> l3), all device
+ * float32, copied into float32 master weights plus the kernel layouts of
+ * desc->prec.  Synchronises `stream`.  On success *out owns device memory
+ * until deepinv_net_destroy. */
 int deepinv_net_create(const deepinv_net_desc* desc, const float* phi,
-                       const float* const w[3], const float* const b[3],
+                       const float* const w[], const float* const b[],
                        void* stream, deepinv_net** out);
 
 /* Fix the activation scale of a DEEPINV_FP8_E4M3 network: run the FC layer
@@ -159,7 +169,7 @@ size_t deepinv_saved_bytes(const deepinv_net* net, int B);
 int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes);
 
 /* x^ = M(y, Omega) (Sec. 4): FC layer, reshape to n1 x n2, conv1 + ReLU,
- * conv2 + ReLU, conv3 (+ ReLU when final_relu).
+ * conv2 + ReLU, each hidden layer + ReLU, conv3 (+ ReLU when final_relu).
  * y [B][M] -> xhat [B][N].  `saved` is NULL for inference, or a device buffer
  * of deepinv_saved_bytes(net, B) bytes that receives the activations the
  * backward pass needs.  Uses the network's workspace (grown if B exceeds the
@@ -188,19 +198,19 @@ int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, flo
  * of w[l]), db[l] (shape of b[l]), dWfc [N][M] (only when train_fc; else pass
  * NULL) and *loss (one device double).  All outputs are overwritten. */
 int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
-                     float* const dW[3], float* const db[3], float* dWfc, double* loss,
+                     float* const dW[], float* const db[], float* dWfc, double* loss,
                      void* stream);
 
 /* One SGD-with-momentum step on the float32 master weights:
  * v <- mu v + g ; w <- w - lr v (momentum buffers live in the network, zero at
  * creation), then refresh the kernel-layout copies.  dWfc is used only when
  * train_fc. */
-int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float* const db[3],
+int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float* const db[],
                          const float* dWfc, float lr, float mu, void* stream);
 
 /* Copy the float32 master weights out (any pointer may be NULL to skip it);
  * wfc is [N][M] and is only available when train_fc. */
-int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc,
+int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[], float* wfc,
                        void* stream);
 
 /* ------------------------------------------------------------------ serving
@@ -272,13 +282,14 @@ int deepinv_serve_get_stats(deepinv_server* s, deepinv_serve_stats* st);
 int deepinv_serve_close(deepinv_server* s);
 
 /* Stages of the forward pass timed by the profiler. */
-#define DEEPINV_NSTAGES 5
+#define DEEPINV_NSTAGES 6
 enum {
     DEEPINV_STAGE_MEASURE = 0, /* y = Phi x (deepinv_net_measure) */
     DEEPINV_STAGE_FC = 1,      /* x~ = Phi^T y, written in the conv1 input layout */
     DEEPINV_STAGE_CONV1 = 2,
     DEEPINV_STAGE_CONV2 = 3,
-    DEEPINV_STAGE_CONV3 = 4
+    DEEPINV_STAGE_CONV3 = 4,
+    DEEPINV_STAGE_HIDDEN = 5   /* all hidden layers of a deeper network */
 };
 
 /* Profiling of the network's calls by CUDA events.  While enabled,

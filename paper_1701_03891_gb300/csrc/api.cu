@@ -73,13 +73,16 @@ struct deepinv_net {
     Geo geo{};
     bool tc = false;   // tensor-core path (bf16, or e4m3 conv2)
     bool fp8 = false;  // conv2 in e4m3
-    // float32 masters
+    // float32 masters of the L = 3 + hidden conv layers, in network order
+    // (conv1, conv2, hidden 1..hidden, conv3)
+    static constexpr int kMaxLayers = 3 + DEEPINV_MAX_HIDDEN;
+    int L = 3;
     float* phi = nullptr;
-    float* w[3] = {nullptr, nullptr, nullptr};
-    float* b[3] = {nullptr, nullptr, nullptr};
+    float* w[kMaxLayers] = {};
+    float* b[kMaxLayers] = {};
     float* wfc = nullptr;
-    float* vw[3] = {nullptr, nullptr, nullptr};
-    float* vb[3] = {nullptr, nullptr, nullptr};
+    float* vw[kMaxLayers] = {};
+    float* vb[kMaxLayers] = {};
     float* vfc = nullptr;
     // bf16 kernel layouts
     bf16* fcA = nullptr;    // FC: rows = pixel j, K = measurement i
@@ -92,6 +95,8 @@ struct deepinv_net {
     bf16* w2t = nullptr;        // conv2 input-gradient weights (flipped, transposed)
     bf16* w3t = nullptr;        // conv3 input-gradient weights
     bf16* w1t = nullptr;        // conv1 input-gradient weights
+    bf16* whp = nullptr;        // hidden layers' operands, kWhPackElems each
+    bf16* wht = nullptr;        // hidden layers' input-gradient operands (trainable networks)
     // e4m3 conv2: weights, per-filter scales, calibrated activation scale
     uint8_t* w2q = nullptr;
     float* sw = nullptr;        // [32] weight scales
@@ -199,8 +204,9 @@ struct Arena {
 // Forward workspace carve-up for batch B (base == nullptr: size only).
 struct FwdWs {
     bf16 *ypk, *xpk, *xt, *a1, *a2;
+    bf16* h;                // hidden layers: second 32-channel plane (ping-pong with a2)
     float *T;
-    float *fxt, *fa1, *fa2;
+    float *fxt, *fa1, *fa2, *fh;
     float *yd, *xd, *xhd;   // device staging of the host-memory entry points
     float* mpart;           // split-K partials of the measurement GEMM
     size_t bytes;
@@ -219,11 +225,13 @@ FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
         w.xt = a.take<bf16>((size_t)B * g.plane);
         w.a1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
         w.a2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
+        if (n->d.hidden > 0) w.h = a.take<bf16>((size_t)B * 4 * g.plane * 8);
         w.T = a.take<float>(conv3_scratch_elems(g, B, 32));
     } else {
         w.fxt = a.take<float>((size_t)B * N);
         w.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
         w.fa2 = a.take<float>((size_t)B * n->d.l2 * N);
+        if (n->d.hidden > 0) w.fh = a.take<float>((size_t)B * n->d.l2 * N);
     }
     if (n->tc) w.mpart = a.take<float>((size_t)16 * B * M);   // split-K partials of y = Phi x
     w.yd = a.take<float>((size_t)B * M);
@@ -236,9 +244,16 @@ FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
 // Layout of the caller's `saved` buffer at batch B.
 struct Saved {
     bf16 *xt, *a1, *a2;      // bf16 path planes
+    bf16* h;                 // hidden layers' output planes, hstride elements apart
     float *fxt, *fa1, *fa2;  // float32 path NCHW
+    float* fh;               // hidden layers' outputs (float32 path), hstride apart
+    size_t hstride;
     float* xhat;
     size_t bytes;
+    // Activation a_l (the input of layer l, 0-based): a_0 = x~, a_1 = conv1's
+    // output, a_2 = conv2's, a_{2+j} = hidden layer j's (j = 1..hidden).
+    bf16* plane(int l) const { return l == 0 ? xt : l == 1 ? a1 : l == 2 ? a2 : h + (size_t)(l - 3) * hstride; }
+    float* f32(int l) const { return l == 0 ? fxt : l == 1 ? fa1 : l == 2 ? fa2 : fh + (size_t)(l - 3) * hstride; }
 };
 
 Saved carve_saved(const deepinv_net* n, int B, char* base)
@@ -251,10 +266,14 @@ Saved carve_saved(const deepinv_net* n, int B, char* base)
         s.xt = a.take<bf16>((size_t)B * g.plane);
         s.a1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
         s.a2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
+        s.hstride = (size_t)B * 4 * g.plane * 8;
+        if (n->d.hidden > 0) s.h = a.take<bf16>(s.hstride * n->d.hidden);
     } else {
         s.fxt = a.take<float>((size_t)B * N);
         s.fa1 = a.take<float>((size_t)B * n->d.l1 * N);
         s.fa2 = a.take<float>((size_t)B * n->d.l2 * N);
+        s.hstride = (size_t)B * n->d.l2 * N;
+        if (n->d.hidden > 0) s.fh = a.take<float>(s.hstride * n->d.hidden);
     }
     s.xhat = a.take<float>((size_t)B * N);
     s.bytes = align_up(a.off, 256);
@@ -294,6 +313,8 @@ int check_desc(const deepinv_net_desc* d)
     DI_REQUIRE(d->l1 >= 1 && d->l2 >= 1 && d->l3 == 1, "filters (%d, %d, %d): need l1, l2 >= 1, l3 = 1",
                d->l1, d->l2, d->l3);
     DI_REQUIRE(d->k >= 1 && d->k <= 15 && d->k % 2 == 1, "kernel size %d must be odd and <= 15", d->k);
+    DI_REQUIRE(d->hidden >= 0 && d->hidden <= DEEPINV_MAX_HIDDEN, "hidden layers %d: need 0..%d", d->hidden,
+               DEEPINV_MAX_HIDDEN);
     DI_REQUIRE(d->prec == DEEPINV_F32 || d->prec == DEEPINV_BF16 || d->prec == DEEPINV_FP8_E4M3,
                "unknown precision %d", d->prec);
     if (d->prec != DEEPINV_F32) {
@@ -313,8 +334,12 @@ int repack(deepinv_net* n, cudaStream_t st)
 {
     if (!n->tc) return DEEPINV_OK;
     const int N = n->N, M = n->d.M;
-    DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[2], n->w1p, n->w2p, n->w3p, st));
-    if (n->w2t) DI_TRY(pack_dgrad_weights(n->w[0], n->w[1], n->w[2], n->w1t, n->w2t, n->w3t, st));
+    const int last = n->L - 1;
+    DI_TRY(pack_conv_weights(n->w[0], n->w[1], n->w[last], n->w1p, n->w2p, n->w3p, st));
+    if (n->w2t) DI_TRY(pack_dgrad_weights(n->w[0], n->w[1], n->w[last], n->w1t, n->w2t, n->w3t, st));
+    for (int j = 0; j < n->d.hidden; ++j)
+        DI_TRY(pack_hidden_weights(n->w[2 + j], n->whp + (size_t)j * kWhPackElems,
+                                   n->wht ? n->wht + (size_t)j * kWhPackElems : nullptr, st));
     if (n->fp8) {
         DI_TRY(pack_w2_e4m3(n->w[1], n->amax_w, n->w2q, n->sw, st));
         if (n->calibrated) DI_TRY(e4m3_scales(n->amax_a1, n->sw, n->inv_sa, n->oscale, st));
@@ -329,7 +354,7 @@ void free_net(deepinv_net* n)
 {
     if (!n) return;
     cudaFree(n->phi);
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < deepinv_net::kMaxLayers; ++l) {
         cudaFree(n->w[l]);
         cudaFree(n->b[l]);
         cudaFree(n->vw[l]);
@@ -347,6 +372,8 @@ void free_net(deepinv_net* n)
     cudaFree(n->w2t);
     cudaFree(n->w3t);
     cudaFree(n->w1t);
+    cudaFree(n->whp);
+    cudaFree(n->wht);
     cudaFree(n->ws);
     cudaFree(n->bws);
     cudaFree(n->rsaved);
@@ -355,14 +382,16 @@ void free_net(deepinv_net* n)
     delete n;
 }
 
+// Channels into and out of layer l (network order: conv1, conv2, hidden layers, conv3).
+int layer_cin(const deepinv_net* n, int l) { return l == 0 ? 1 : (l == 1 ? n->d.l1 : n->d.l2); }
+int layer_cout(const deepinv_net* n, int l) { return l == 0 ? n->d.l1 : (l == n->L - 1 ? n->d.l3 : n->d.l2); }
+
 size_t wsize(const deepinv_net* n, int l)
 {
-    const int cin = l == 0 ? 1 : (l == 1 ? n->d.l1 : n->d.l2);
-    const int cout = l == 0 ? n->d.l1 : (l == 1 ? n->d.l2 : n->d.l3);
-    return (size_t)cout * cin * n->d.k * n->d.k;
+    return (size_t)layer_cout(n, l) * layer_cin(n, l) * n->d.k * n->d.k;
 }
 
-size_t bsize(const deepinv_net* n, int l) { return (size_t)(l == 0 ? n->d.l1 : (l == 1 ? n->d.l2 : n->d.l3)); }
+size_t bsize(const deepinv_net* n, int l) { return (size_t)layer_cout(n, l); }
 
 template <typename T>
 int dev_alloc(T** p, size_t n)
@@ -426,9 +455,21 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
             if (n->fp8) DI_TRY(conv2_tc(a1, B, g, n->w2q, n->b[1], n->oscale, true, a2, n->num_sms, status, st));
             else DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], nullptr, false, a2, n->num_sms, status, st));
         }
+        bf16* last = a2;
+        if (n->d.hidden > 0) {
+            // hidden layers: into the saved planes, or alternating between the
+            // workspace's two 32-channel planes
+            StageTimer t(n, st, DEEPINV_STAGE_HIDDEN);
+            for (int j = 0; j < n->d.hidden; ++j) {
+                bf16* out = saved ? sv.plane(3 + j) : (j % 2 == 0 ? w.h : w.a2);
+                DI_TRY(hidden_tc(last, B, g, n->whp + (size_t)j * kWhPackElems, n->b[2 + j], out, n->num_sms,
+                                 status, st));
+                last = out;
+            }
+        }
         {
             StageTimer t(n, st, DEEPINV_STAGE_CONV3);
-            DI_TRY(conv3_tc(a2, B, g, n->w3p, n->b[2], w.T, xhat, n->d.final_relu, status, st));
+            DI_TRY(conv3_tc(last, B, g, n->w3p, n->b[n->L - 1], w.T, xhat, n->d.final_relu, status, st));
         }
     } else {
         float* xt = saved ? sv.fxt : w.fxt;
@@ -447,9 +488,19 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
             StageTimer t(n, st, DEEPINV_STAGE_CONV2);
             DI_TRY(conv_f32(a1, B, n->d.l1, H, W, n->w[1], n->b[1], n->d.l2, k, a2, 1, st));
         }
+        float* last = a2;
+        if (n->d.hidden > 0) {
+            StageTimer t(n, st, DEEPINV_STAGE_HIDDEN);
+            for (int j = 0; j < n->d.hidden; ++j) {
+                float* out = saved ? sv.f32(3 + j) : (j % 2 == 0 ? w.fh : w.fa2);
+                DI_TRY(conv_f32(last, B, n->d.l2, H, W, n->w[2 + j], n->b[2 + j], n->d.l2, k, out, 1, st));
+                last = out;
+            }
+        }
         {
             StageTimer t(n, st, DEEPINV_STAGE_CONV3);
-            DI_TRY(conv_f32(a2, B, n->d.l2, H, W, n->w[2], n->b[2], 1, k, xhat, n->d.final_relu, st));
+            DI_TRY(conv_f32(last, B, n->d.l2, H, W, n->w[n->L - 1], n->b[n->L - 1], n->d.l3, k, xhat,
+                            n->d.final_relu, st));
         }
     }
     if (saved) DI_CUDA(cudaMemcpyAsync(sv.xhat, xhat, (size_t)B * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -471,6 +522,7 @@ int forward_impl(deepinv_net* n, const float* y, int B, float* xhat, void* saved
 struct BwdWs {
     float* g3;            // dL/dz3 [B][N]
     bf16 *g3p, *g2, *g1;  // gradient planes (zero borders)
+    bf16* g2b;            // hidden layers: second 32-channel gradient plane
     float* part2;         // conv2 weight-gradient partials
     double *acc, *bpart, *lpart;
     float *T, *dxt;         // train_fc: conv1 input gradient (row sums, result)
@@ -487,6 +539,7 @@ BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
     w.g3p = a.take<bf16>((size_t)B * g.plane);
     w.g2 = a.take<bf16>((size_t)B * 4 * g.plane * 8);
     w.g1 = a.take<bf16>((size_t)B * 8 * g.plane * 8);
+    if (n->d.hidden > 0) w.g2b = a.take<bf16>((size_t)B * 4 * g.plane * 8);
     w.g3 = a.take<float>((size_t)B * N);
     w.part2 = a.take<float>(wgrad2_scratch_floats() > tapwgrad_scratch_floats() ? wgrad2_scratch_floats()
                                                                                  : tapwgrad_scratch_floats());
@@ -507,7 +560,7 @@ BwdWs carve_bwd_tc(const deepinv_net* n, int B, char* base)
 // Bnorm: the batch the loss is normalised by, (1 / Bnorm) sum_b ||x^_b - x_b||^2
 // (B itself, or the whole batch when these B images are one chunk of it).
 int backward_tc(deepinv_net* n, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
-                float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+                float* const dW[], float* const db[], float* dWfc, double* loss, cudaStream_t st)
 {
     const Geo& g = n->geo;
     const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2;
@@ -534,14 +587,29 @@ int backward_tc(deepinv_net* n, const float* y, const float* x, int B, int Bnorm
     // dL/dz3 = 2 (x^ - x) / B (times [x^ > 0] with final_relu) and the loss in float64
     DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, Bnorm, n->d.final_relu, w.g3, w.lpart, loss, st));
     DI_TRY(grad_plane(w.g3, B, g, w.g3p, st));
-    // conv3: bias and weight gradients, input gradient times [a2 > 0] -> g2
-    DI_TRY(plane_channel_sums(w.g3p, B, 1, g, w.bpart, db[2], st));
-    DI_TRY(tap_wgrad_tc(false, w.g3p, sv.a2, B, g, w.part2, dW[2], nullptr, status, st));
-    DI_TRY(conv3_dgrad_tc(w.g3p, B, g, n->w3t, sv.a2, w.g2, status, st));
+    // conv3 (layer L-1, input a_{L-1}): bias and weight gradients, input
+    // gradient times [a_{L-1} > 0] -> the gradient plane of layer L-2
+    const int last = n->L - 1;
+    DI_TRY(plane_channel_sums(w.g3p, B, 1, g, w.bpart, db[last], st));
+    DI_TRY(tap_wgrad_tc(false, w.g3p, sv.plane(last), B, g, w.part2, dW[last], nullptr, status, st));
+    DI_TRY(conv3_dgrad_tc(w.g3p, B, g, n->w3t, sv.plane(last), w.g2, status, st));
+    // hidden layers l = L-2 .. 2 (input a_l): gradients, then the input gradient
+    // times [a_l > 0], alternating between the two 32-channel gradient planes
+    bf16* gcur = w.g2;
+    bf16* gnext = w.g2b;
+    for (int l = last - 1; l >= 2; --l) {
+        const size_t j = (size_t)(l - 2);
+        DI_TRY(plane_channel_sums(gcur, B, 32, g, w.bpart, db[l], st));
+        DI_TRY(wgrad_hidden_tc(gcur, sv.plane(l), B, g, w.part2, dW[l], status, st));
+        DI_TRY(hidden_dgrad_tc(gcur, B, g, n->wht + j * kWhPackElems, sv.plane(l), gnext, n->num_sms, status, st));
+        bf16* t = gcur;
+        gcur = gnext;
+        gnext = t;
+    }
     // conv2
-    DI_TRY(plane_channel_sums(w.g2, B, 32, g, w.bpart, db[1], st));
-    DI_TRY(wgrad2_tc(w.g2, sv.a1, B, g, w.part2, dW[1], status, st));
-    DI_TRY(conv2_dgrad_tc(w.g2, B, g, n->w2t, sv.a1, w.g1, n->num_sms, status, st));
+    DI_TRY(plane_channel_sums(gcur, B, 32, g, w.bpart, db[1], st));
+    DI_TRY(wgrad2_tc(gcur, sv.a1, B, g, w.part2, dW[1], status, st));
+    DI_TRY(conv2_dgrad_tc(gcur, B, g, n->w2t, sv.a1, w.g1, n->num_sms, status, st));
     // conv1
     DI_TRY(tap_wgrad_tc(true, sv.xt, w.g1, B, g, w.part2, dW[0], db[0], status, st));
     if (n->d.train_fc) {
@@ -610,36 +678,28 @@ namespace {
 
 // Backward of the float32 path (NCHW activations in `sv`); Bnorm as in backward_tc.
 int backward_f32(deepinv_net* net, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
-                 float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+                 float* const dW[], float* const db[], float* dWfc, double* loss, cudaStream_t st)
 {
     const int N = net->N, M = net->d.M, H = net->d.n1, W = net->d.n2, k = net->d.k;
-    const int l1 = net->d.l1, l2 = net->d.l2;
+    const int l1 = net->d.l1, l2 = net->d.l2, last = net->L - 1;
     size_t maxw = 0;
-    for (int l = 0; l < 3; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;
-    auto carve_bwd = [&](char* base, float** g3, float** gA, float** gB, float** dxt, float** fxt, float** fa1,
-                         float** fa2, float** wt, double** wpart, double** lpart) {
+    for (int l = 0; l < net->L; ++l) maxw = wsize(net, l) > maxw ? wsize(net, l) : maxw;
+    auto carve_bwd = [&](char* base, float** g3, float** gA, float** gC, float** gB, float** dxt, float** wt,
+                         double** wpart, double** lpart) {
         Arena a{base, 0};
         *g3 = a.take<float>((size_t)B * N);
         *gA = a.take<float>((size_t)B * l2 * N);
+        *gC = net->d.hidden > 0 ? a.take<float>((size_t)B * l2 * N) : nullptr;
         *gB = a.take<float>((size_t)B * l1 * N);
         *dxt = a.take<float>((size_t)B * N);
-        if (net->tc) {
-            *fxt = a.take<float>((size_t)B * N);
-            *fa1 = a.take<float>((size_t)B * l1 * N);
-            *fa2 = a.take<float>((size_t)B * l2 * N);
-        } else {
-            *fxt = sv.fxt;
-            *fa1 = sv.fa1;
-            *fa2 = sv.fa2;
-        }
         *wt = a.take<float>(maxw);
         *wpart = a.take<double>((size_t)kWgradChunks * maxw);
         *lpart = a.take<double>(kLossBlocks);
         return align_up(a.off, 256);
     };
-    float *g3, *gA, *gB, *dxt, *fxt, *fa1, *fa2, *wt;
+    float *g3, *gA, *gC, *gB, *dxt, *wt;
     double *wpart, *lpart;
-    const size_t need = carve_bwd(nullptr, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+    const size_t need = carve_bwd(nullptr, &g3, &gA, &gC, &gB, &dxt, &wt, &wpart, &lpart);
     if (need > net->bws_bytes) {
         DI_CUDA(cudaStreamSynchronize(st));
         cudaFree(net->bws);
@@ -653,25 +713,31 @@ int backward_f32(deepinv_net* net, const float* y, const float* x, int B, int Bn
         }
         net->bws_bytes = need;
     }
-    carve_bwd(net->bws, &g3, &gA, &gB, &dxt, &fxt, &fa1, &fa2, &wt, &wpart, &lpart);
+    carve_bwd(net->bws, &g3, &gA, &gC, &gB, &dxt, &wt, &wpart, &lpart);
 
-    if (net->tc) {
-        DI_TRY(plane_to_nchw(sv.xt, B, 1, net->geo, fxt, st));
-        DI_TRY(plane_to_nchw(sv.a1, B, l1, net->geo, fa1, st));
-        DI_TRY(plane_to_nchw(sv.a2, B, l2, net->geo, fa2, st));
-    }
-    // dL/dz3 = 2 (x^ - x) / B, and the loss in float64
+    // dL/dz_L = 2 (x^ - x) / B, and the loss in float64
     DI_TRY(mse_loss_grad(sv.xhat, x, (long long)B * N, Bnorm, net->d.final_relu, g3, lpart, loss, st));
-    // conv3
-    DI_TRY(conv_wgrad_f32(fa2, g3, B, l2, H, W, 1, k, wpart, dW[2], db[2], st));
-    DI_TRY(conv_dgrad_f32(g3, B, 1, H, W, net->w[2], l2, k, wt, gA, st));
-    DI_TRY(relu_mask_f32(gA, fa2, (long long)B * l2 * N, st));
+    // conv3 (layer L-1, input a_{L-1})
+    DI_TRY(conv_wgrad_f32(sv.f32(last), g3, B, l2, H, W, net->d.l3, k, wpart, dW[last], db[last], st));
+    DI_TRY(conv_dgrad_f32(g3, B, net->d.l3, H, W, net->w[last], l2, k, wt, gA, st));
+    DI_TRY(relu_mask_f32(gA, sv.f32(last), (long long)B * l2 * N, st));
+    // hidden layers l = L-2 .. 2 (input a_l), alternating gA / gC
+    float* gcur = gA;
+    float* gnext = gC;
+    for (int l = last - 1; l >= 2; --l) {
+        DI_TRY(conv_wgrad_f32(sv.f32(l), gcur, B, l2, H, W, l2, k, wpart, dW[l], db[l], st));
+        DI_TRY(conv_dgrad_f32(gcur, B, l2, H, W, net->w[l], l2, k, wt, gnext, st));
+        DI_TRY(relu_mask_f32(gnext, sv.f32(l), (long long)B * l2 * N, st));
+        float* t = gcur;
+        gcur = gnext;
+        gnext = t;
+    }
     // conv2
-    DI_TRY(conv_wgrad_f32(fa1, gA, B, l1, H, W, l2, k, wpart, dW[1], db[1], st));
-    DI_TRY(conv_dgrad_f32(gA, B, l2, H, W, net->w[1], l1, k, wt, gB, st));
-    DI_TRY(relu_mask_f32(gB, fa1, (long long)B * l1 * N, st));
+    DI_TRY(conv_wgrad_f32(sv.fa1, gcur, B, l1, H, W, l2, k, wpart, dW[1], db[1], st));
+    DI_TRY(conv_dgrad_f32(gcur, B, l2, H, W, net->w[1], l1, k, wt, gB, st));
+    DI_TRY(relu_mask_f32(gB, sv.fa1, (long long)B * l1 * N, st));
     // conv1
-    DI_TRY(conv_wgrad_f32(fxt, gB, B, 1, H, W, l1, k, wpart, dW[0], db[0], st));
+    DI_TRY(conv_wgrad_f32(sv.fxt, gB, B, 1, H, W, l1, k, wpart, dW[0], db[0], st));
     if (net->d.train_fc) {
         DI_TRY(conv_dgrad_f32(gB, B, l1, H, W, net->w[0], 1, k, wt, dxt, st));
         // dWfc[j][i] = sum_b dx~[b][j] y[b][i]
@@ -681,7 +747,7 @@ int backward_f32(deepinv_net* net, const float* y, const float* x, int B, int Bn
 }
 
 int backward_run(deepinv_net* net, const float* y, const float* x, int B, int Bnorm, const Saved& sv,
-                 float* const dW[3], float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+                 float* const dW[], float* const db[], float* dWfc, double* loss, cudaStream_t st)
 {
     if (net->tc) return backward_tc(net, y, x, B, Bnorm, sv, dW, db, dWfc, loss, st);
     return backward_f32(net, y, x, B, Bnorm, sv, dW, db, dWfc, loss, st);
@@ -710,8 +776,8 @@ int grow(char** buf, size_t* bytes, size_t need, const char* what, cudaStream_t 
 // chunk when the budget is 0), each chunk's gradients added to the first
 // chunk's in chunk order (deterministic).  The loss and its gradient stay
 // normalised by the whole batch.
-int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, float* const dW[3],
-                       float* const db[3], float* dWfc, double* loss, cudaStream_t st)
+int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, float* const dW[],
+                       float* const db[], float* dWfc, double* loss, cudaStream_t st)
 {
     const int N = net->N, M = net->d.M;
     int Bc = B;
@@ -724,21 +790,21 @@ int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, 
     DI_TRY(grow(&net->rsaved, &net->rsaved_bytes, carve_saved(net, Bc, nullptr).bytes, "recomputation buffer", st));
     DI_TRY(ensure_ws(net, Bc, st));
     const FwdWs fw = carve_fwd(net, net->ws_B, net->ws);
-    // gradient scratch of the chunks after the first: dW[3], db[3], dWfc, loss
-    float* gW[3];
-    float* gB[3];
+    // gradient scratch of the chunks after the first: dW[L], db[L], dWfc, loss
+    float* gW[deepinv_net::kMaxLayers];
+    float* gB[deepinv_net::kMaxLayers];
     float* gFc = nullptr;
     double* gL = nullptr;
     if (Bc < B) {
         Arena a{nullptr, 0};
-        for (int l = 0; l < 3; ++l) a.take<float>(wsize(net, l));
-        for (int l = 0; l < 3; ++l) a.take<float>(bsize(net, l));
+        for (int l = 0; l < net->L; ++l) a.take<float>(wsize(net, l));
+        for (int l = 0; l < net->L; ++l) a.take<float>(bsize(net, l));
         if (net->d.train_fc) a.take<float>((size_t)N * M);
         a.take<double>(1);
         DI_TRY(grow(&net->gacc, &net->gacc_bytes, align_up(a.off, 256), "gradient scratch", st));
         Arena g{net->gacc, 0};
-        for (int l = 0; l < 3; ++l) gW[l] = g.take<float>(wsize(net, l));
-        for (int l = 0; l < 3; ++l) gB[l] = g.take<float>(bsize(net, l));
+        for (int l = 0; l < net->L; ++l) gW[l] = g.take<float>(wsize(net, l));
+        for (int l = 0; l < net->L; ++l) gB[l] = g.take<float>(bsize(net, l));
         if (net->d.train_fc) gFc = g.take<float>((size_t)N * M);
         gL = g.take<double>(1);
     }
@@ -753,7 +819,7 @@ int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, 
             continue;
         }
         DI_TRY(backward_run(net, yc, xc, nb, B, sv, gW, gB, gFc, gL, st));
-        for (int l = 0; l < 3; ++l) {
+        for (int l = 0; l < net->L; ++l) {
             DI_TRY(accumulate_f32(dW[l], gW[l], (long long)wsize(net, l), st));
             DI_TRY(accumulate_f32(db[l], gB[l], (long long)bsize(net, l), st));
         }
@@ -769,7 +835,7 @@ extern "C" {
 
 const char* deepinv_last_error(void) { return di::g_err; }
 
-int deepinv_version(void) { return 100; }
+int deepinv_version(void) { return 200; }
 
 int deepinv_device_status(int reset)
 {
@@ -822,13 +888,13 @@ int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float
     return rc;
 }
 
-int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const float* const w[3],
-                       const float* const b[3], void* stream, deepinv_net** out)
+int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const float* const w[],
+                       const float* const b[], void* stream, deepinv_net** out)
 {
     DI_REQUIRE(out, "out is NULL");
     DI_TRY(check_desc(desc));
     DI_REQUIRE(phi && w && b, "null pointer");
-    for (int l = 0; l < 3; ++l) DI_REQUIRE(w[l] && b[l], "null weight pointer for layer %d", l + 1);
+    for (int l = 0; l < 3 + desc->hidden; ++l) DI_REQUIRE(w[l] && b[l], "null weight pointer for layer %d", l + 1);
     const int dev = device_of(phi);
     DI_REQUIRE(dev >= 0, "phi is not device memory");
     DeviceGuard dg(dev);
@@ -836,6 +902,7 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
     deepinv_net* n = new (std::nothrow) deepinv_net();
     DI_REQUIRE(n, "host allocation failed");
     n->d = *desc;
+    n->L = 3 + desc->hidden;
     n->dev = dev;
     n->N = desc->n1 * desc->n2;
     n->tc = desc->prec != DEEPINV_F32;
@@ -847,7 +914,7 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
     DI_STEP(dev_alloc(&n->phi, (size_t)M * N));
     DI_STEP(cudaMemcpyAsync(n->phi, phi, (size_t)M * N * sizeof(float), cudaMemcpyDeviceToDevice, st) == cudaSuccess
                 ? DEEPINV_OK : DEEPINV_ECUDA);
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < n->L; ++l) {
         DI_STEP(dev_alloc(&n->w[l], wsize(n, l)));
         DI_STEP(dev_alloc(&n->b[l], bsize(n, l)));
         DI_STEP(dev_alloc(&n->vw[l], wsize(n, l)));
@@ -878,6 +945,10 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
             DI_STEP(dev_alloc(&n->w2t, kW2PackElems));
             DI_STEP(dev_alloc(&n->w3t, kW3tPackElems));
             DI_STEP(dev_alloc(&n->w1t, kW1tPackElems));
+        }
+        if (desc->hidden > 0) {
+            DI_STEP(dev_alloc(&n->whp, kWhPackElems * desc->hidden));
+            if (!n->fp8) DI_STEP(dev_alloc(&n->wht, kWhPackElems * desc->hidden));
         }
         if (n->fp8) {
             DI_STEP(dev_alloc(&n->w2q, kW2E4M3Bytes));
@@ -989,13 +1060,13 @@ int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes)
 }
 
 int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, const void* saved,
-                     float* const dW[3], float* const db[3], float* dWfc, double* loss, void* stream)
+                     float* const dW[], float* const db[], float* dWfc, double* loss, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
     DI_REQUIRE(B >= 1, "bad batch %d", B);
     DI_REQUIRE(y && x && dW && db && loss, "null pointer");
-    for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
+    for (int l = 0; l < net->L; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
     if (net->fp8) {
         set_error("e4m3 networks are inference only (train in bf16 or f32)");
@@ -1007,16 +1078,16 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
     return backward_run(net, y, x, B, B, sv, dW, db, dWfc, loss, st);
 }
 
-int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float* const db[3], const float* dWfc,
+int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float* const db[], const float* dWfc,
                          float lr, float mu, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
     DI_REQUIRE(dW && db, "null pointer");
-    for (int l = 0; l < 3; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
+    for (int l = 0; l < net->L; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < net->L; ++l) {
         DI_TRY(sgd_momentum_f32(net->w[l], net->vw[l], dW[l], (long long)wsize(net, l), lr, mu, st));
         DI_TRY(sgd_momentum_f32(net->b[l], net->vb[l], db[l], (long long)bsize(net, l), lr, mu, st));
     }
@@ -1025,12 +1096,12 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[3], const float
     return repack(net, st);
 }
 
-int deepinv_get_params(const deepinv_net* net, float* const w[3], float* const b[3], float* wfc, void* stream)
+int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[], float* wfc, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < net->L; ++l) {
         if (w && w[l]) DI_CUDA(cudaMemcpyAsync(w[l], net->w[l], wsize(net, l) * 4, cudaMemcpyDeviceToDevice, st));
         if (b && b[l]) DI_CUDA(cudaMemcpyAsync(b[l], net->b[l], bsize(net, l) * 4, cudaMemcpyDeviceToDevice, st));
     }

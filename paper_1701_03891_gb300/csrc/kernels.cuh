@@ -46,6 +46,12 @@ constexpr size_t kW3PackElems = 3 * 2 * 2 * 64 * 8;      // [x][kk][2][64][8]
 int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p,
                       bf16* w3p, cudaStream_t st);
 
+// Hidden 32 -> 32 layers: forward and input-gradient operands of one layer
+// (conv2's A layout with 2 chunk pairs, [dy][s][kk][2][128][8]); wht may be
+// NULL (inference-only networks).
+constexpr size_t kWhPackElems = 11 * 3 * 2 * 2 * 128 * 8;
+int pack_hidden_weights(const float* w, bf16* whp, bf16* wht, cudaStream_t st);
+
 enum GemmOut { GEMM_OUT_F32 = 0, GEMM_OUT_PLANE = 1 };
 
 // D[m][n] = sum_k A[m][k] B[n][k] over packed operands (A: TR = 128, B: TR =
@@ -89,6 +95,13 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
                    cudaStream_t st);
 int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
                    int* status, cudaStream_t st);
+// Hidden layer (32 -> 32 channels, planes [B][4][plane][8]): forward with
+// bias and ReLU (zero pad columns), and the input gradient from the output
+// gradient times the ReLU mask [act_in > 0] of the layer's input.
+int hidden_tc(const bf16* in, int B, const Geo& g, const bf16* whp, const float* bias, bf16* out, int num_sms,
+              int* status, cudaStream_t st);
+int hidden_dgrad_tc(const bf16* gout, int B, const Geo& g, const bf16* wht, const bf16* act_in, bf16* gin,
+                    int num_sms, int* status, cudaStream_t st);
 constexpr size_t kW3tPackElems = 11 * 2 * 32 * 8;      // conv3 input-gradient weights [dy'][h][32][8]
 constexpr size_t kW1tPackElems = 3 * 4 * 2 * 64 * 8;   // conv1 input-gradient weights [x][4][2][64][8]
 // w1t, w2t ([dy'][6][2][2][128][8], kW2PackElems) and w3t from the float32 masters.
@@ -114,6 +127,10 @@ int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, 
 size_t wgrad2_scratch_floats();
 int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
               cudaStream_t st);
+// Hidden layer weight gradient: output gradient plane [B][4][plane][8] and the
+// layer's input plane [B][4][plane][8] -> dw [32][32][11][11] (same scratch).
+int wgrad_hidden_tc(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
+                    cudaStream_t st);
 // e4m3 conv2 weights: [dy][s][kk][2][128][16] bytes with per-filter scales sw[32].
 constexpr size_t kW2E4M3Bytes = 11 * 3 * 2 * 2 * 128 * 16;
 int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st);

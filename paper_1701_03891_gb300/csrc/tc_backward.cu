@@ -133,15 +133,23 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, 
 // contiguous in 16-byte chunks, positions 16 bytes apart -- the planes' own
 // layout): A = 128 rows (tap slot g, filter co) read from four windows of the
 // g2 plane shifted by g; B = up to 256 rows (kernel-row group p = (dy, s),
-// channel ci) read from four windows of a1.  33 groups p -> 9 CTAs columns
-// ("quads"); positions are split over kWgSplit CTAs each; every CTA leaves a
-// 128 x 256 float32 partial, summed in float64 in a fixed order.
+// channel ci) read from 256 / CIN windows of the input plane (a1: CIN = 64,
+// four groups; a hidden layer's input: CIN = 32, eight groups).  The 33
+// groups p make WgCfg::COLS CTA columns; positions are split over
+// WgCfg::SPLIT CTAs each; every CTA leaves a 128 x 256 float32 partial,
+// summed in float64 in a fixed order.
 constexpr int kWgKB = 128;           // positions per stage
 constexpr int kWgStages = 2;
-constexpr int kWgQuads = 9;
-constexpr int kWgSplit = 16;          // 9 x 16 = 144 CTAs
 constexpr uint32_t kWgABytes = 16 * kWgKB * 16;     // 16 M-groups
 constexpr uint32_t kWgBBytes = 32 * kWgKB * 16;     // 32 N-groups
+
+template <int CIN>
+struct WgCfg {
+    static constexpr int CPG = CIN / 8;                      // 16-byte chunks per kernel-row group
+    static constexpr int GPC = 256 / CIN;                    // kernel-row groups per CTA column
+    static constexpr int COLS = (33 + GPC - 1) / GPC;        // 9 (CIN = 64) or 5 (CIN = 32)
+    static constexpr int SPLIT = CIN == 64 ? 16 : 30;        // 144 or 150 CTAs
+};
 
 struct WgSmem {
     uint64_t full[kWgStages], empty[kWgStages], acc_full, drain;
@@ -155,21 +163,24 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
+template <int CIN>
 __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
                                                         int B, int P, int HP16, int plane_len,
                                                         float* __restrict__ part, int* status)
 {
+    using C = WgCfg<CIN>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sA = smem_raw;                                        // [stage][16 groups][KB][16 B]
     uint8_t* sB = smem_raw + kWgStages * kWgABytes;                // [stage][32 groups][KB][16 B]
     WgSmem* ss = reinterpret_cast<WgSmem*>(sB + kWgStages * kWgBBytes);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int quad = blockIdx.x % kWgQuads, split = blockIdx.x / kWgQuads;
-    const int npairs = quad < 8 ? 4 : 1;
-    const int NB = npairs * 64;
+    const int col = blockIdx.x % C::COLS, split = blockIdx.x / C::COLS;
+    const int ngroups = min(C::GPC, 33 - col * C::GPC);
+    const int NB = ngroups * CIN;
+    const int ncopy = 16 + C::CPG * ngroups;
     const int nb_img = (HP16 + kWgKB - 1) / kWgKB;
     const long long total = (long long)B * nb_img;
-    const long long blk0 = total * split / kWgSplit, blk1 = total * (split + 1) / kWgSplit;
+    const long long blk0 = total * split / C::SPLIT, blk1 = total * (split + 1) / C::SPLIT;
     const int u_begin = kPad * P + kPad;
 
     if (threadIdx.x == 0) {
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
     const uint32_t tbase = ss->tmem_base;
 
     if (warp == 0) {
-        // producer warp: lane 0 waits and arms the stage barrier, then the 16 + 8 npairs
+        // producer warp: lane 0 waits and arms the stage barrier, then the 16 + CPG ngroups
         // window copies of the stage are issued by all 32 lanes (small bulk copies are
         // limited by their issue rate per thread)
         int parity[kWgStages] = {-1, -1};
@@ -204,23 +215,23 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
             const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
             const int npos = min(kWgKB, u_begin + HP16 - u0);
             const uint32_t bytes = (uint32_t)npos * 16;
-            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (16 + 8 * npairs) * bytes);
+            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (uint32_t)ncopy * bytes);
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             parity[st] = n & 1;
             const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
-            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * 8 * plane_len * 16;
+            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * C::CPG * plane_len * 16;
             uint8_t* dA = sA + st * kWgABytes;
             uint8_t* dB = sB + st * kWgBBytes;
-            for (int c = lane; c < 16 + 8 * npairs; c += 32) {
+            for (int c = lane; c < ncopy; c += 32) {
                 if (c < 16) {
                     const int g = c / 4, c4 = c % 4;
                     bulk_g2s(smem_u32(dA + (g * 4 + c4) * kWgKB * 16),
                              g2b + ((size_t)c4 * plane_len + u0 - g) * 16, bytes, smem_u32(&ss->full[st]));
                 } else {
-                    const int pl = (c - 16) / 8, c8 = (c - 16) % 8;
-                    const int p = quad * 4 + pl, dy = p / 3, s = p % 3;
+                    const int pl = (c - 16) / C::CPG, c8 = (c - 16) % C::CPG;
+                    const int p = col * C::GPC + pl, dy = p / 3, s = p % 3;
                     const int off = (dy - 5) * P + 4 * s - 5;
-                    bulk_g2s(smem_u32(dB + (pl * 8 + c8) * kWgKB * 16),
+                    bulk_g2s(smem_u32(dB + (pl * C::CPG + c8) * kWgKB * 16),
                              a1b + ((size_t)c8 * plane_len + u0 + off) * 16, bytes, smem_u32(&ss->full[st]));
                 }
             }
@@ -279,17 +290,19 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
     }
 }
 
-// dW2[co][ci][dy][dx] = sum over splits of part[quad + 9 split][32 g + co][64 pl + ci],
-// with p = 4 quad + pl = 3 dy + s and dx = 4 s + g (< 11).
+// dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][32 g + co][CIN pl + ci],
+// with p = GPC col + pl = 3 dy + s and dx = 4 s + g (< 11).
+template <int CIN>
 __global__ void wgrad2_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
 {
-    const int n = 32 * 64 * 121;
+    using C = WgCfg<CIN>;
+    const int n = 32 * CIN * 121;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int dx = i % 11, dy = (i / 11) % 11, ci = (i / 121) % 64, co = i / (121 * 64);
-        const int s = dx / 4, g = dx % 4, p = dy * 3 + s, quad = p / 4, pl = p % 4;
+        const int dx = i % 11, dy = (i / 11) % 11, ci = (i / 121) % CIN, co = i / (121 * CIN);
+        const int s = dx / 4, g = dx % 4, p = dy * 3 + s, col = p / C::GPC, pl = p % C::GPC;
         double acc = 0.0;
-        for (int k = 0; k < kWgSplit; ++k)
-            acc += (double)part[((size_t)(quad + kWgQuads * k) * 128 + g * 32 + co) * 256 + pl * 64 + ci];
+        for (int k = 0; k < C::SPLIT; ++k)
+            acc += (double)part[((size_t)(col + C::COLS * k) * 128 + g * 32 + co) * 256 + pl * CIN + ci];
         dw[i] = (float)acc;
     }
 }
@@ -474,19 +487,37 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 }
 
 // Positions u that can carry a nonzero gradient: the data rows [5P+5, 5P+5+HP).
-size_t wgrad2_scratch_floats() { return (size_t)kWgQuads * kWgSplit * 128 * 256; }
+size_t wgrad2_scratch_floats()
+{
+    const size_t c64 = (size_t)WgCfg<64>::COLS * WgCfg<64>::SPLIT, c32 = (size_t)WgCfg<32>::COLS * WgCfg<32>::SPLIT;
+    return (c64 > c32 ? c64 : c32) * 128 * 256;
+}
+
+template <int CIN>
+static int wgrad_launch(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
+                        cudaStream_t st)
+{
+    using C = WgCfg<CIN>;
+    const int HP16 = (g.HP + 15) / 16 * 16;
+    const size_t smem = (size_t)kWgStages * (kWgABytes + kWgBBytes) + sizeof(WgSmem) + 16;
+    DI_CUDA(cudaFuncSetAttribute(wgrad2_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad2_kernel<CIN><<<C::COLS * C::SPLIT, 192, smem, st>>>(G, A, B, g.P, HP16, g.plane, part, status);
+    DI_LAUNCH_CHECK();
+    wgrad2_reduce_kernel<CIN><<<grid_for(32 * CIN * 121), 256, 0, st>>>(part, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
 
 int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
               cudaStream_t st)
 {
-    const int HP16 = (g.HP + 15) / 16 * 16;
-    const size_t smem = (size_t)kWgStages * (kWgABytes + kWgBBytes) + sizeof(WgSmem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(wgrad2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad2_kernel<<<kWgQuads * kWgSplit, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, part, status);
-    DI_LAUNCH_CHECK();
-    wgrad2_reduce_kernel<<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
+    return wgrad_launch<64>(G2, A1, B, g, part, dw, status, st);
+}
+
+int wgrad_hidden_tc(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
+                    cudaStream_t st)
+{
+    return wgrad_launch<32>(G, A, B, g, part, dw, status, st);
 }
 
 size_t tapwgrad_scratch_floats() { return (size_t)kTwCtas * 128 * 64; }

@@ -117,6 +117,34 @@ __global__ void pack_conv_weights_kernel(const float* __restrict__ w1, const flo
     }
 }
 
+// Hidden layer (32 -> 32) operands, conv2's layout with 2 chunk pairs: block
+// (dy, s, kk) holds rows m = 32 g + r (tap slot g, row channel r), K =
+// channels c = 16 kk .. 16 kk + 15; with dx = 4 s + g (zero for dx = 11)
+//   forward (whp):        Wh[r][c][dy][dx]            (r = filter, c = input)
+//   input gradient (wht): Wh[c][r][10 - dy][10 - dx]  (r = input, c = filter).
+__global__ void pack_hidden_weights_kernel(const float* __restrict__ w, bf16* __restrict__ whp,
+                                           bf16* __restrict__ wht)
+{
+    const long long n = kWhPackElems;
+    const long long total = wht ? 2 * n : n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool dgrad = i >= n;
+        const long long j = dgrad ? i - n : i;
+        const int e = (int)(j % 8);
+        const int m = (int)((j / 8) % 128);
+        const int half = (int)((j / (8 * 128)) % 2);
+        const int kk = (int)((j / (8 * 128 * 2)) % 2);
+        const int s = (int)((j / (8 * 128 * 2 * 2)) % 3);
+        const int dy = (int)(j / (8 * 128 * 2 * 2 * 3));
+        const int r = m % 32, g = m / 32, dx = 4 * s + g, c = kk * 16 + half * 8 + e;
+        float v = 0.f;
+        if (dx < 11)
+            v = dgrad ? w[((c * 32 + r) * 11 + (10 - dy)) * 11 + (10 - dx)] : w[((r * 32 + c) * 11 + dy) * 11 + dx];
+        (dgrad ? wht : whp)[j] = __float2bfloat16_rn(v);
+    }
+}
+
 // Per-filter absolute maximum of the conv2 weights: amax[co] = max |W2[co][.][.][.]|.
 __global__ void conv2_absmax_kernel(const float* __restrict__ w2, float* __restrict__ amax)
 {
@@ -631,6 +659,13 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
 // multiplied); it streams a third of the bytes but runs about 12 % slower, and
 // neither 128-byte-aligned operand offsets nor padded channel strides close
 // the gap.
+enum Conv2Variant {
+    kC2Fwd = 0,       // conv2 forward, bf16: 64 -> 32 channels, bias + ReLU
+    kC2FwdE4M3 = 1,   // conv2 forward, e4m3 input and weights
+    kC2Dgrad = 2,     // conv2 input gradient: 32 -> 64 channels, 2 tap slots, mask of a1
+    kHidFwd = 3,      // hidden layer forward: 32 -> 32 channels, bias + ReLU
+    kHidDgrad = 4,    // hidden layer input gradient: 32 -> 32 channels, mask of its input
+};
 constexpr int kW2Stages = 4;
 constexpr int kConv2Threads = 224;
 constexpr int kMaxSlabs = 10;
@@ -665,7 +700,7 @@ __host__ __device__ inline int conv2_dylast(int j, int P)
     return d < 10 ? d : 10;
 }
 
-template <bool ROWS, bool FP8, bool DGRAD>
+template <bool ROWS, int V>
 __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __restrict__ a1, int B, int H, int W, int P,
                                                        int plane_len, int t2, int nslab,
                                                        const void* __restrict__ w2p,
@@ -681,8 +716,15 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
     // gradient with the flipped, transposed weights): 2 tap slots x 64 input
     // channels, taps dx = 2 s + g for s = 0..5, input 32 channels (4 chunks,
     // 2 MMAs per (dy, s)); the epilogue applies the ReLU mask of a1.
-    constexpr int NCH = (FP8 || DGRAD) ? 4 : 8;
-    constexpr int KK = (FP8 || DGRAD) ? 2 : 4;
+    // Hidden layers (32 -> 32, bf16): 4 tap slots x 32 filters like the
+    // forward, input 32 channels (4 chunks, 2 MMAs per (dy, s)); kHidFwd adds
+    // bias and ReLU, kHidDgrad (flipped, transposed weights) applies the ReLU
+    // mask of the layer's input instead.
+    constexpr bool FP8 = V == kC2FwdE4M3;
+    constexpr bool DGRAD = V == kC2Dgrad;                     // 2 tap slots x 64 outputs
+    constexpr bool MASK = V == kC2Dgrad || V == kHidDgrad;     // ReLU-mask epilogue, no bias
+    constexpr int NCH = V == kC2Fwd ? 8 : 4;
+    constexpr int KK = V == kC2Fwd ? 4 : 2;
     constexpr int GROUPS = DGRAD ? 6 : 3;      // column groups s per kernel row
     constexpr int SSTEP = DGRAD ? 2 : 4;       // taps per group (= position shift between groups)
     constexpr int MAXSHIFT = SSTEP * (GROUPS - 1);
@@ -855,7 +897,7 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
         float bias8[8], scale8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            bias8[e] = DGRAD ? 0.f : __ldg(&b2[(le / 32) * 8 + e]);
+            bias8[e] = MASK ? 0.f : __ldg(&b2[(le / 32) * 8 + e]);
             scale8[e] = FP8 ? __ldg(&oscale[(le / 32) * 8 + e]) : 1.f;
         }
         float* xrow = sX + (quarter * 32 + lane) * kXStride;  // exchange row = TMEM lane (32 g + co or 64 g + co)
@@ -908,11 +950,11 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                     if (store) {
                         constexpr int OUTCH = DGRAD ? 8 : 4;
                         bf16* dst = a2 + (((size_t)b * OUTCH + c8) * plane_len + pos) * 8;
-                        if (DGRAD) {
-                            // gradient of a1 times the ReLU mask [a1 > 0]; zero outside the image
+                        if (MASK) {
+                            // input gradient times the ReLU mask [input > 0]; zero outside the image
                             uint4 mk = make_uint4(0, 0, 0, 0);
                             if (data)
-                                mk = *reinterpret_cast<const uint4*>(mask_src + (((size_t)b * 8 + c8) * plane_len + pos) * 8);
+                                mk = *reinterpret_cast<const uint4*>(mask_src + (((size_t)b * OUTCH + c8) * plane_len + pos) * 8);
                             const bf16* mv = reinterpret_cast<const bf16*>(&mk);
 #pragma unroll
                             for (int e = 0; e < 8; ++e) acc[e] = (data && __bfloat162float(mv[e]) > 0.f) ? acc[e] : 0.f;
@@ -1324,6 +1366,14 @@ int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int 
     return DEEPINV_OK;
 }
 
+int pack_hidden_weights(const float* w, bf16* whp, bf16* wht, cudaStream_t st)
+{
+    const long long n = (long long)kWhPackElems * (wht ? 2 : 1);
+    pack_hidden_weights_kernel<<<grid1d(n), 256, 0, st>>>(w, whp, wht);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
 int pack_conv_weights(const float* w1, const float* w2, const float* w3, bf16* w1p, bf16* w2p, bf16* w3p,
                       cudaStream_t st)
 {
@@ -1431,10 +1481,12 @@ int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* osc
     return DEEPINV_OK;
 }
 
-static size_t conv2_smem_bytes(const Geo& g, bool rows, bool fp8)
+// narrow: 4 input chunks per position (e4m3 input, or a 32-channel bf16 input)
+// and 8 KB weight blocks; otherwise 8 chunks and 16 KB blocks.
+static size_t conv2_smem_bytes(const Geo& g, bool rows, bool narrow)
 {
-    const int nch = fp8 ? 4 : 8;
-    const size_t wstage = fp8 ? 8192 : 16384;
+    const int nch = narrow ? 4 : 8;
+    const size_t wstage = narrow ? 8192 : 16384;
     const size_t win = rows ? (size_t)kRowSlots * nch * kPiecePx * 16 : (size_t)nch * g.nslab * kSlabPx * 16;
     return win + (size_t)kW2Stages * wstage + kXBytes + sizeof(Conv2Smem);
 }
@@ -1443,13 +1495,13 @@ static size_t conv2_smem_bytes(const Geo& g, bool rows, bool fp8)
 // mode; wider images fit only row mode).  DEEPINV_CONV2_WINDOW=1 in
 // the environment selects window mode where the window fits in shared memory
 // (both modes give bit-identical results; the tests compare them).
-static bool conv2_window_mode(const Geo& g, bool fp8)
+static bool conv2_window_mode(const Geo& g, bool narrow)
 {
     static const bool window = [] {
         const char* e = getenv("DEEPINV_CONV2_WINDOW");
         return e && e[0] == '1';
     }();
-    return window && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false, fp8) <= 227 * 1024;
+    return window && g.nslab <= kMaxSlabs && conv2_smem_bytes(g, false, narrow) <= 227 * 1024;
 }
 
 bool conv2_tc_supported(const Geo& g)
@@ -1457,51 +1509,62 @@ bool conv2_tc_supported(const Geo& g)
     return conv2_window_mode(g, false) || conv2_smem_bytes(g, true, false) <= 227 * 1024;
 }
 
-template <bool ROWS, bool FP8, bool DGRAD>
-static int launch_conv2(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
-                        const bf16* mask_src, bf16* a2, int grid, size_t smem, int nslab, int* status, cudaStream_t st)
+template <bool ROWS, int V>
+static int launch_conv2_mode(const void* in, int B, const Geo& g, const void* wp, const float* bias,
+                             const float* oscale, const bf16* mask_src, bf16* out, int grid, size_t smem, int nslab,
+                             int* status, cudaStream_t st)
 {
-    DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, FP8, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    conv2_kernel<ROWS, FP8, DGRAD><<<grid, kConv2Threads, smem, st>>>(a1, B, g.H, g.W, g.P, g.plane, g.t2, nslab, w2p, b2,
-                                                            oscale, mask_src, a2, status);
+    DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv2_kernel<ROWS, V><<<grid, kConv2Threads, smem, st>>>(in, B, g.H, g.W, g.P, g.plane, g.t2, nslab, wp, bias,
+                                                             oscale, mask_src, out, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
 
-int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
-             bool fp8, bf16* a2, int num_sms, int* status, cudaStream_t st)
+// One persistent CTA per SM (at most one per tile), row or window mode.
+template <int V>
+static int launch_conv2(const void* in, int B, const Geo& g, const void* wp, const float* bias, const float* oscale,
+                        const bf16* mask_src, bf16* out, int num_sms, int* status, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
     if (!conv2_tc_supported(g)) {
         set_error("conv2_tc: no kernel configuration for image width %d", g.W);
         return DEEPINV_EUNSUPPORTED;
     }
-    const bool rows = !conv2_window_mode(g, fp8);
-    const size_t smem = conv2_smem_bytes(g, rows, fp8);
+    constexpr bool narrow = V != kC2Fwd;
+    const bool rows = !conv2_window_mode(g, narrow);
+    const size_t smem = conv2_smem_bytes(g, rows, narrow);
     const int ntiles = B * g.t2;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     const int nslab = rows ? kRowSlots : g.nslab;
-    if (rows) {
-        return fp8 ? launch_conv2<true, true, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st)
-                   : launch_conv2<true, false, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st);
-    }
-    return fp8 ? launch_conv2<false, true, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st)
-               : launch_conv2<false, false, false>(a1, B, g, w2p, b2, oscale, nullptr, a2, grid, smem, nslab, status, st);
+    if (rows)
+        return launch_conv2_mode<true, V>(in, B, g, wp, bias, oscale, mask_src, out, grid, smem, nslab, status, st);
+    return launch_conv2_mode<false, V>(in, B, g, wp, bias, oscale, mask_src, out, grid, smem, nslab, status, st);
+}
+
+int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,
+             bool fp8, bf16* a2, int num_sms, int* status, cudaStream_t st)
+{
+    return fp8 ? launch_conv2<kC2FwdE4M3>(a1, B, g, w2p, b2, oscale, nullptr, a2, num_sms, status, st)
+               : launch_conv2<kC2Fwd>(a1, B, g, w2p, b2, nullptr, nullptr, a2, num_sms, status, st);
 }
 
 int conv2_dgrad_tc(const bf16* g2, int B, const Geo& g, const bf16* w2t, const bf16* a1, bf16* g1, int num_sms,
                    int* status, cudaStream_t st)
 {
-    if (B <= 0) return DEEPINV_OK;
-    // the 32-channel gradient uses 4 chunks per position, like the e4m3 input
-    const bool rows = !conv2_window_mode(g, true);
-    const size_t smem = conv2_smem_bytes(g, rows, true);
-    const int ntiles = B * g.t2;
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
-    const int nslab = rows ? kRowSlots : g.nslab;
-    if (rows) return launch_conv2<true, false, true>(g2, B, g, w2t, nullptr, nullptr, a1, g1, grid, smem, nslab, status, st);
-    return launch_conv2<false, false, true>(g2, B, g, w2t, nullptr, nullptr, a1, g1, grid, smem, nslab, status, st);
+    return launch_conv2<kC2Dgrad>(g2, B, g, w2t, nullptr, nullptr, a1, g1, num_sms, status, st);
+}
+
+int hidden_tc(const bf16* in, int B, const Geo& g, const bf16* whp, const float* bias, bf16* out, int num_sms,
+              int* status, cudaStream_t st)
+{
+    return launch_conv2<kHidFwd>(in, B, g, whp, bias, nullptr, nullptr, out, num_sms, status, st);
+}
+
+int hidden_dgrad_tc(const bf16* gout, int B, const Geo& g, const bf16* wht, const bf16* act_in, bf16* gin,
+                    int num_sms, int* status, cudaStream_t st)
+{
+    return launch_conv2<kHidDgrad>(gout, B, g, wht, nullptr, nullptr, act_in, gin, num_sms, status, st);
 }
 
 

@@ -55,7 +55,7 @@ class NetDesc(ctypes.Structure):
     _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("M", ctypes.c_int),
                 ("l1", ctypes.c_int), ("l2", ctypes.c_int), ("l3", ctypes.c_int),
                 ("k", ctypes.c_int), ("final_relu", ctypes.c_int), ("train_fc", ctypes.c_int),
-                ("prec", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("hidden", ctypes.c_int)]
 
 
 _lib = None
@@ -95,8 +95,9 @@ SIGNATURES = {
     "deepinv_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
 }
 
-NSTAGES = 5
-STAGES = ("measure", "fc", "conv1", "conv2", "conv3")
+NSTAGES = 6
+STAGES = ("measure", "fc", "conv1", "conv2", "conv3", "hidden")
+MAX_HIDDEN = 16
 
 
 def lib():
@@ -173,10 +174,19 @@ def measure_noalloc(phi, x, out, stream=None):
     return out
 
 
+def num_layers(params: dict) -> int:
+    """Conv layers L of a parameter dict holding w1, b1, ..., wL, bL."""
+    L = 0
+    while "w%d" % (L + 1) in params:
+        L += 1
+    return L
+
+
 class Net:
     """A DeepInverse network (Sec. 4) held by the library: FC = Phi^T, then
-    three conv layers (Eq. 1).  ``params`` maps w1,b1,w2,b2,w3,b3 to float32
-    tensors (CUDA or CPU; copied)."""
+    conv layers (Eq. 1).  ``params`` maps w1,b1,...,wL,bL (network order;
+    L = 3 is the paper's network, L > 3 adds L - 3 hidden l2 -> l2 layers
+    before the last) to float32 tensors (CUDA or CPU; copied)."""
 
     def __init__(self, phi, params: dict, n1: int, n2: int, *, prec="bf16", final_relu=False,
                  train_fc=False, device="cuda"):
@@ -186,10 +196,14 @@ class Net:
         phi_t = t(phi)
         M, N = phi_t.shape
         assert N == n1 * n2, "phi must be M x (n1*n2)"
-        ws = [t(params["w%d" % i]) for i in (1, 2, 3)]
-        bs = [t(params["b%d" % i]) for i in (1, 2, 3)]
-        self.desc = NetDesc(n1, n2, M, ws[0].shape[0], ws[1].shape[0], ws[2].shape[0], ws[0].shape[-1],
-                            int(final_relu), int(train_fc), PRECISIONS.get(prec, prec))
+        L = num_layers(params)
+        if L < 3:
+            raise DeepInvError(EINVAL, "params need w1..wL, b1..bL with L >= 3")
+        ws = [t(params["w%d" % i]) for i in range(1, L + 1)]
+        bs = [t(params["b%d" % i]) for i in range(1, L + 1)]
+        self.L = L
+        self.desc = NetDesc(n1, n2, M, ws[0].shape[0], ws[1].shape[0], ws[-1].shape[0], ws[0].shape[-1],
+                            int(final_relu), int(train_fc), PRECISIONS.get(prec, prec), L - 3)
         self.n1, self.n2, self.M, self.N = n1, n2, M, N
         self.prec = prec
         self.device = dev
@@ -319,7 +333,9 @@ class Net:
         wp, _k1 = _arr([t.data_ptr() for t in W])
         bp, _k2 = _arr([t.data_ptr() for t in Bv])
         _check(lib().deepinv_get_params(self._h, wp, bp, _ptr(wfc), _stream(stream)))
-        out = {"w1": W[0], "w2": W[1], "w3": W[2], "b1": Bv[0], "b2": Bv[1], "b3": Bv[2]}
+        out = {}
+        for i in range(self.L):
+            out["w%d" % (i + 1)], out["b%d" % (i + 1)] = W[i], Bv[i]
         if wfc is not None:
             out["wfc"] = wfc
         return out
@@ -343,7 +359,7 @@ def _make_autograd():
             saved = net.new_saved(B)
             net.forward(y, saved=saved)
             loss, dW, db, dWfc = net.backward(y, x, saved)
-            grads = [dW[0], db[0], dW[1], db[1], dW[2], db[2]]
+            grads = [g for pair in zip(dW, db) for g in pair]
             if dWfc is not None:
                 grads.append(dWfc)
             ctx.grads = grads
@@ -361,7 +377,7 @@ _autograd_cls = None
 
 
 def mse_loss(net: Net, y, x, params):
-    """Differentiable L(Omega); ``params`` is the list [w1, b1, w2, b2, w3, b3(, wfc)]."""
+    """Differentiable L(Omega); ``params`` is the list [w1, b1, ..., wL, bL(, wfc)]."""
     global _autograd_cls
     if _autograd_cls is None:
         _autograd_cls = _make_autograd()

@@ -47,8 +47,16 @@ def test_binding_covers_every_declared_symbol():
     assert _declared() <= set(deepinv.SIGNATURES)
 
 
+def test_binding_constants_match_header():
+    from paper_1701_03891_gb300 import deepinv
+    with open(os.path.join(ROOT, "include", "deepinv.h")) as f:
+        h = f.read()
+    assert int(re.search(r"#define DEEPINV_NSTAGES (\d+)", h).group(1)) == deepinv.NSTAGES == len(deepinv.STAGES)
+    assert int(re.search(r"#define DEEPINV_MAX_HIDDEN (\d+)", h).group(1)) == deepinv.MAX_HIDDEN
+
+
 def test_version(L):
-    assert L.deepinv_version() == 100
+    assert L.deepinv_version() == 200
 
 
 def test_null_pointers_rejected_on_host(L):
@@ -69,10 +77,12 @@ def test_bad_descriptions_rejected_on_host(L):
         deepinv.NetDesc(8, 8, 4, 64, 32, 1, 10, 0, 0, 0),      # even kernel
         deepinv.NetDesc(8, 8, 4, 64, 32, 2, 11, 0, 0, 0),      # l3 != 1
         deepinv.NetDesc(8, 8, 4, 64, 32, 1, 11, 0, 0, 7),      # unknown precision
+        deepinv.NetDesc(8, 8, 4, 64, 32, 1, 11, 0, 0, 0, -1),  # negative hidden layer count
+        deepinv.NetDesc(8, 8, 4, 64, 32, 1, 11, 0, 0, 0, deepinv.MAX_HIDDEN + 1),   # too many hidden layers
     ]
     for d in bad:
         rc = L.deepinv_net_create(ctypes.byref(d), ctypes.c_void_p(16), None, None, None, ctypes.byref(out))
-        assert rc == deepinv.EINVAL, (d.n1, d.M, d.k, rc)
+        assert rc == deepinv.EINVAL, (d.n1, d.M, d.k, d.hidden, rc)
     d = deepinv.NetDesc(8, 8, 4, 16, 32, 1, 11, 0, 0, deepinv.BF16)  # bf16 needs 64/32/1
     rc = L.deepinv_net_create(ctypes.byref(d), ctypes.c_void_p(16), None, None, None, ctypes.byref(out))
     assert rc == deepinv.EUNSUPPORTED

@@ -32,12 +32,14 @@ def di():
     return deepinv
 
 
-def test_f32_backward_matches_finite_differences(di):
+@pytest.mark.parametrize("hidden", [0, 1])
+def test_f32_backward_matches_finite_differences(di, hidden):
+    """hidden = 1 adds a 32 -> 32 layer between conv2 and conv3 (four conv layers)."""
     import torch
     n1 = n2 = 16
     N, M, B = n1 * n2, 32, 2
     phi = synth.gaussian_phi(M, N, seed=30)
-    params = synth.he_params(seed=31, bias_std=0.05)
+    params = synth.he_params(seed=31, bias_std=0.05, hidden=hidden)
     x = synth.dct_sparse_images(B, n1, n2, K=12, seed=32)
     y = oracle.measure(phi, x).astype(np.float32)
     yd = torch.from_numpy(y).cuda()
@@ -60,7 +62,9 @@ def test_f32_backward_matches_finite_differences(di):
     saved = net.new_saved(B)
     net.forward(yd, saved=saved)
     _, dW, db, dWfc = net.backward(yd, xd, saved)
-    grads = {"w1": dW[0], "w2": dW[1], "w3": dW[2], "b1": db[0], "b2": db[1], "b3": db[2], "wfc": dWfc}
+    grads = {"w%d" % (i + 1): dW[i] for i in range(net.L)}
+    grads.update({"b%d" % (i + 1): db[i] for i in range(net.L)})
+    grads["wfc"] = dWfc
     grads = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
     net.close()
 

@@ -22,13 +22,13 @@ def di():
 SHAPES = [(16, 16, 0.125), (32, 32, 0.10), (24, 40, 0.20)]
 
 
-def _nets(di, prec="bf16"):
+def _nets(di, prec="bf16", hidden=(0, 0, 0)):
     out = []
     for i, (n1, n2, r) in enumerate(SHAPES):
         N = n1 * n2
         M = synth.m_for_ratio(r, N)
         phi = synth.gaussian_phi(M, N, seed=10 + i)
-        p = synth.he_params(seed=20 + i, bias_std=0.01)
+        p = synth.he_params(seed=20 + i, bias_std=0.01, hidden=hidden[i])
         out.append((di.Net(phi, p, n1, n2, prec=prec), phi, p, n1, n2))
     return out
 
@@ -59,10 +59,12 @@ def _drain(srv, n_expected, first=()):
     return got
 
 
-@pytest.mark.parametrize("prec", ["bf16", "f32"])
-def test_mixed_stream_equals_alone(di, prec):
+@pytest.mark.parametrize("prec,hidden", [("bf16", (0, 0, 0)), ("f32", (0, 0, 0)), ("bf16", (0, 1, 2))])
+def test_mixed_stream_equals_alone(di, prec, hidden):
+    """Requests of three networks (the last case mixes 3-, 4- and 5-layer
+    networks) give the same bits batched in the mix as alone."""
     import torch
-    nets = _nets(di, prec)
+    nets = _nets(di, prec, hidden)
     srv = di.Server(hbm_budget_bytes=4 << 30, max_streams=4, max_batch=8)
     ids = [srv.add(n[0]) for n in nets]
     assert ids == [0, 1, 2]
