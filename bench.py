@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-deep", action="store_true")
+    ap.add_argument("--deep-steps", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=10)
     ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--serve-rates", default="20000,80000,200000",
@@ -61,7 +63,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window per rate")
     ap.add_argument("--eval", action="store_true",
                     help="also train 32x32 networks at M/N 0.05/0.10/0.25, clean and 20 dB SNR, and report "
-                         "the recovered images' PSNR and success rate (about 40 s)")
+                         "the recovered images' PSNR and success rate, and 3-, 4- and 5-layer networks at M/N 0.10 (about a minute)")
     return ap.parse_args()
 
 
@@ -313,6 +315,93 @@ def train_bench(args):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
+def deep_bench(args):
+    """Deeper network (two extra 32 -> 32 hidden layers: five conv layers, the
+    larger-capacity networks Sec. 5 leaves to future work) at 64 x 64:
+    sense + recover at M/N = 0.10, batch 1024 (Voronoi images, seed 3, as the
+    headline), and a training step at M/N = 0.25, batch 256 (FC trained).
+    Hidden-layer TFLOP/s from the library's stage events (2 x 32 x 32 x 121
+    FLOP per pixel and layer)."""
+    import numpy as np
+    import torch
+    from paper_1701_03891_gb300 import deepinv, synth
+    n, hidden = 64, 2
+    N = n * n
+    stream = torch.cuda.current_stream()
+    out = {"hidden_layers": hidden, "conv_layers": 3 + hidden}
+    # inference
+    B = 1024
+    M = synth.m_for_ratio(0.10, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    params = synth.he_params(seed=1, hidden=hidden)
+    x = synth.voronoi_images(B, n, n, seed=3)
+    net = deepinv.Net(phi, params, n, n, prec="bf16")
+    net.reserve(B)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty((B, M), device="cuda")
+    xh = torch.empty((B, N), device="cuda")
+    for _ in range(2):
+        net.measure(xd, out=yd)
+        net.forward(yd, out=xh)
+    torch.cuda.synchronize()
+    net.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.deep_steps):
+        net.measure(xd, out=yd)
+        net.forward(yd, out=xh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = net.profile_read()
+    net.profile(False)
+    ms = e0.elapsed_time(e1) / args.deep_steps
+    hid_ms = st["hidden"][0] / max(1, st["hidden"][1])
+    out["inference"] = {"workload": "sense+recover 64x64, M/N=0.10 (M=%d), batch %d, %d conv layers" % (M, B, 3 + hidden),
+                        "images_per_s": B / (ms / 1000.0), "ms_per_step": ms,
+                        "hidden_ms_per_layer": hid_ms / hidden,
+                        "hidden_tflops": 2.0 * 32 * 32 * 121 * B * N * hidden / (hid_ms / 1000.0) / 1e12,
+                        "stage_ms": {k: v[0] / max(1, v[1]) for k, v in st.items()}}
+    net.close()
+    del yd, xh
+    # training
+    B = 256
+    M = synth.m_for_ratio(0.25, N)
+    phi = synth.gaussian_phi(M, N, seed=0)
+    x = synth.voronoi_images(B, n, n, seed=7)
+    net = deepinv.Net(phi, params, n, n, prec="bf16", train_fc=True)
+    net.reserve(B)
+    xd = torch.from_numpy(x).cuda()
+    yd = net.measure(xd)
+    xh = torch.empty((B, N), device="cuda")
+    saved = net.new_saved(B)
+    grads = net.grad_buffers()
+
+    lr = [0.0]
+
+    def step():
+        net.forward(yd, out=xh, saved=saved)
+        loss, dW, db, dWfc = net.backward(yd, xd, saved, grads=grads)
+        if not lr[0]:
+            lr[0] = 1e-3 / float(loss)       # step relative to the first loss (He init, five layers)
+        net.sgd_momentum(dW, db, dWfc, lr=lr[0], mu=0.9)
+        return loss
+
+    first = float(step())
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.deep_steps):
+        loss = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.deep_steps
+    out["training"] = {"workload": "training step 64x64, M/N=0.25 (M=%d), batch %d, %d conv layers, bf16 compute, "
+                                   "fp32 masters, FC trained" % (M, B, 3 + hidden),
+                       "images_per_s": B / (ms / 1000.0), "ms_per_step": ms, "lr": lr[0],
+                       "loss_first": first, "loss_last": float(loss)}
+    net.close()
+    return out
+
+
 SERVE_SIZES = (32, 64, 128)
 SERVE_RATIOS = (0.05, 0.10, 0.25)
 
@@ -541,13 +630,17 @@ def run_native(args):
     train = None
     if rank == 0 and not args.no_train:
         train = train_bench(args)
+    deep = None
+    if rank == 0 and not args.no_deep:
+        deep = deep_bench(args)
 
     evaluation = None
     if rank == 0 and args.eval:
         from paper_1701_03891_gb300 import evaluate
         evaluation = {"workload": "32x32 Voronoi images, 512 training / 64 test, 6000 SGD-momentum steps of 64 "
                                   "(bf16, FC = Phi^T), step 1e-3 / first loss",
-                      "points": evaluate.sweep(32, ratios=(0.05, 0.10, 0.25), snrs=(None, 20.0))}
+                      "points": evaluate.sweep(32, ratios=(0.05, 0.10, 0.25), snrs=(None, 20.0)),
+                      "depth": evaluate.depth_sweep(32, 0.10, hiddens=(0, 1, 2))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -563,7 +656,8 @@ def run_native(args):
             "fp32": {"value": world * B / (f32_ms / 1000.0), "unit": "images/s", "ms_per_step": f32_ms,
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
-            "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "eval_32": evaluation,
+            "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "deep_64": deep,
+            "eval_32": evaluation,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
     if rank == 0:

@@ -44,14 +44,16 @@ def add_noise(y: np.ndarray, snr_db: float | None, seed: int) -> np.ndarray:
 def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voronoi", train_images: int = 512,
                        test_images: int = 64, batch: int = 64, steps: int = 6000, lr: float | None = None,
                        lr_scale: float = 1e-3,
-                       mu: float = 0.9, snr_db: float | None = None, prec: str = "bf16", seed: int = 0) -> dict:
+                       mu: float = 0.9, snr_db: float | None = None, prec: str = "bf16", seed: int = 0,
+                       hidden: int = 0) -> dict:
     """Train an n x n network at measurement ratio M/N (the FC layer fixed to Phi^T)
     with SGD with momentum on the bfloat16 path and evaluate it.  The loss is a
     sum over pixels (Sec. 4), so its scale varies with M/N and the images; the
     step is lr, or lr_scale / (the first batch's loss) when lr is None.  With snr_db,
-    training and test measurements carry Gaussian noise at that SNR.  Returns
-    the mean PSNR and success rate on the test images, before and after
-    training, and the first and last training losses."""
+    training and test measurements carry Gaussian noise at that SNR.  ``hidden``
+    adds that many 32 -> 32 layers before the last (the deeper networks of
+    Sec. 5).  Returns the mean PSNR and success rate on the test images, before
+    and after training, and the first and last training losses."""
     import torch
     from . import deepinv
 
@@ -63,7 +65,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
     xtrain = make(train_images, n, n, seed=seed + 21)
     xtest = make(test_images, n, n, seed=seed + 22)
 
-    net = deepinv.Net(phi, synth.he_params(seed=seed + 1), n, n, prec="bf16")
+    net = deepinv.Net(phi, synth.he_params(seed=seed + 1, hidden=hidden), n, n, prec="bf16")
     xt = torch.from_numpy(xtrain).cuda()
 
     def measure(x, noise_seed):
@@ -102,6 +104,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
         other.close()
     net.close()
     return {"n": n, "ratio": ratio, "M": M, "snr_db": snr_db, "images": images, "steps": steps, "lr": step,
+            "conv_layers": 3 + hidden,
             "psnr_db_before": before[0], "success_before": before[1],
             "psnr_db": after[0], "success": after[1], "loss_first": first, "loss_last": last}
 
@@ -110,3 +113,18 @@ def sweep(n: int = 32, ratios=(0.05, 0.10, 0.25), snrs=(None, 20.0), **kw) -> li
     """PSNR and success rate against M/N, with and without measurement noise
     (the analogue of Sec. 5's quality-versus-ratio experiments on synthetic data)."""
     return [train_and_evaluate(n, r, snr_db=s, **kw) for r in ratios for s in snrs]
+
+
+def depth_sweep(n: int = 32, ratio: float = 0.10, hiddens=(0, 1, 2), **kw) -> list:
+    """PSNR and success rate of networks with 3 + h conv layers (h in hiddens)
+    trained the same way -- the larger-capacity question Sec. 5 leaves open, on
+    synthetic data.  Every network takes the same SGD step: the first one's
+    (lr_scale / its first loss, unless lr is given), since a deeper He-initialised
+    network starts from a larger loss and a step relative to it would be smaller."""
+    lr = kw.pop("lr", None)
+    out = []
+    for h in hiddens:
+        r = train_and_evaluate(n, ratio, hidden=h, lr=lr, **kw)
+        lr = r["lr"]
+        out.append(r)
+    return out

@@ -131,8 +131,8 @@ def _check_grads(net, g, loss_ref, res, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
-@pytest.mark.parametrize("hidden", [1, 2])
-@pytest.mark.parametrize("n1,n2,M,B", [(16, 16, 32, 2), (24, 40, 96, 2)])
+@pytest.mark.parametrize("hidden,n1,n2,M,B", [(1, 16, 16, 32, 2), (2, 16, 16, 32, 2), (1, 24, 40, 96, 2),
+                                              (2, 24, 40, 96, 2), (2, 64, 64, 1024, 2)])
 def test_backward_deeper(di, prec, hidden, n1, n2, M, B):
     """Loss and every gradient (FC trained) of a deeper network against the oracle."""
     N = n1 * n2
