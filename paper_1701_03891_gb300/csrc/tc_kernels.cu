@@ -646,19 +646,24 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
 // 33 (dy, s) pairs x 4 channel chunks = 132 MMAs per tile, 253 valid outputs
 // per tile (the last 3 columns lack their slot-3 partner).
 //
-// Persistent CTAs, 7 warps: warp 6 streams the input (below) and warp 0 the
-// weights ((dy, s) blocks of 16 KB through a ring), each on its own so that
-// neither waits for the other; warp 1 owns TMEM (2 accumulators x 256
-// columns) and issues MMAs; warps 2..5 drain the accumulator of the previous
-// tile.
+// Persistent CTAs, 7 warps: warp 6 streams the input and (row mode) the
+// weights, warp 0 streams the weights in window mode; warp 1 owns TMEM (2
+// accumulators x 256 columns) and issues MMAs; warps 2..5 drain the
+// accumulator of the previous tile.
 //
-// Row mode (the default): the producer streams, for every kernel row dy, just
-// the 272 positions that row's MMAs read, through a ring of kRowSlots pieces.
-// Window mode keeps the whole window of 10 P + 272 positions of a tile as
-// slabs (freed as soon as the last kernel row reading them has been
-// multiplied); it streams a third of the bytes but runs about 12 % slower, and
-// neither 128-byte-aligned operand offsets nor padded channel strides close
-// the gap.
+// Row mode (the default): for every kernel row dy one ring stage holds the
+// 272 positions that row's MMAs read and the row's stacked weights (all its
+// column groups), filled by one producer on one barrier; the ring is as deep
+// as shared memory allows (conv2_row_slots: 2 stages of 82 KB for the bf16
+// forward, 3 for the input gradient, 4 for the 4-chunk variants).  The MMA
+// thread then waits and commits once per kernel row instead of once per
+// (dy, s) weight block: both cost it about as long as an MMA issue, so this
+// took conv2 from 1.27 to 1.20 ms at 64 x 64 and the 66-MMA variants (e4m3,
+// hidden layers) 1.5x faster.
+// Window mode (DEEPINV_CONV2_WINDOW=1, narrow images only) keeps the whole
+// window of 10 P + 272 positions of a tile as slabs, freed as soon as the last
+// kernel row reading them has been multiplied, with the weights in a separate
+// ring of (dy, s) blocks; it streams fewer bytes but runs slower.
 enum Conv2Variant {
     kC2Fwd = 0,       // conv2 forward, bf16: 64 -> 32 channels, bias + ReLU
     kC2FwdE4M3 = 1,   // conv2 forward, e4m3 input and weights
@@ -671,7 +676,7 @@ constexpr int kConv2Threads = 224;
 constexpr int kMaxSlabs = 10;
 
 constexpr int kPiecePx = 16 + kConv2N; // positions one kernel row's MMAs read (row mode; shift <= 10)
-constexpr int kRowSlots = 4;           // row-mode ring of input pieces
+constexpr int kMaxRowSlots = 4;        // row-mode ring depth limit
 constexpr int kXStride = 36;          // floats per row of the slot exchange (32 + 4 pad)
 constexpr int kXBytes = 4 * 32 * kXStride * 4;
 
@@ -729,14 +734,16 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
     constexpr int SSTEP = DGRAD ? 2 : 4;       // taps per group (= position shift between groups)
     constexpr int MAXSHIFT = SSTEP * (GROUPS - 1);
     constexpr uint32_t WSTAGE = KK * 4096;
+    constexpr bool FUSEDW = ROWS;                  // a kernel row's weights share its input piece's stage
+    const int WRING = FUSEDW ? nslab * GROUPS : kW2Stages;   // weight blocks resident in shared memory
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // window mode: [NCH][nslab * 128][16 B]; row mode: [nslab pieces][NCH][kPiecePx][16 B]
     const uint32_t CH = ROWS ? (uint32_t)kPiecePx * 16 : (uint32_t)nslab * kSlabPx * 16;
     const uint32_t win_bytes = ROWS ? (uint32_t)nslab * NCH * CH : NCH * CH;
     uint8_t* sWin = smem_raw;
-    uint8_t* sW = smem_raw + win_bytes;             // [kW2Stages][WSTAGE]
-    float* sX = reinterpret_cast<float*>(sW + kW2Stages * WSTAGE);   // [4 slots][32 filters][kXStride]
-    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + kW2Stages * WSTAGE + kXBytes);
+    uint8_t* sW = smem_raw + win_bytes;             // [WRING][WSTAGE]: row mode [nslab][GROUPS], window mode a ring
+    float* sX = reinterpret_cast<float*>(sW + WRING * WSTAGE);   // [4 slots][32 filters][kXStride]
+    Conv2Smem* ss = reinterpret_cast<Conv2Smem*>(sW + WRING * WSTAGE + kXBytes);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int HP = H * P;
@@ -786,11 +793,15 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                     const int slot = pc % nslab, n = pc / nslab;
                     ++pc;
                     if (!mbar_wait(smem_u32(&ss->empty[slot]), (n & 1) ^ 1, status, &ss->abort_flag)) { ok = false; break; }
-                    mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), NCH * kPiecePx * 16);
+                    mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), NCH * kPiecePx * 16 + (FUSEDW ? GROUPS * WSTAGE : 0));
                     slab_parity[slot] = n & 1;
                     for (int c = 0; c < NCH; ++c)
                         bulk_g2s(smem_u32(sWin + (slot * NCH + c) * CH),
                                  src_img + ((size_t)c * plane_len + q0 + dy * P) * 16, kPiecePx * 16,
+                                 smem_u32(&ss->full[slot]));
+                    if (FUSEDW)
+                        bulk_g2s(smem_u32(sW + slot * GROUPS * WSTAGE),
+                                 reinterpret_cast<const uint8_t*>(w2p) + (size_t)dy * GROUPS * WSTAGE, GROUPS * WSTAGE,
                                  smem_u32(&ss->full[slot]));
                 }
                 const int last = ROWS ? -1 : (dy * P + MAXSHIFT + kConv2N - 1) / kSlabPx;
@@ -808,7 +819,7 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
         }
         for (int j = 0; j < nslab; ++j)
             if (slab_parity[j] >= 0) mbar_wait_drain(smem_u32(&ss->full[j]), slab_parity[j]);
-    } else if (warp == 0 && lane == 0) {
+    } else if (warp == 0 && lane == 0 && !FUSEDW) {
         // ------------------------------------------------ weight producer
         int w_parity[kW2Stages];
         for (int s = 0; s < kW2Stages; ++s) w_parity[s] = -1;
@@ -862,9 +873,11 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                 if (!ok) break;
                 tc_fence_after();
                 for (int s = 0; s < GROUPS; ++s, ++wst) {
-                    const int wslot = wst % kW2Stages, n = wst / kW2Stages;
-                    if (!mbar_wait(smem_u32(&ss->wfull[wslot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
-                    tc_fence_after();
+                    const int wslot = FUSEDW ? slot * GROUPS + s : wst % kW2Stages, n = wst / kW2Stages;
+                    if (!FUSEDW) {
+                        if (!mbar_wait(smem_u32(&ss->wfull[wslot]), n & 1, status, &ss->abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                    }
                     const uint32_t boff = off + (uint32_t)(SSTEP * s) * 16;
 #pragma unroll
                     for (int kk = 0; kk < KK; ++kk) {
@@ -873,7 +886,7 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                         if (FP8) mma_e4m3(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
                         else mma_bf16(d, ad, bd, idesc, (dy | s | kk) ? 1u : 0u);
                     }
-                    mma_commit(smem_u32(&ss->wempty[wslot]));
+                    if (!FUSEDW) mma_commit(smem_u32(&ss->wempty[wslot]));
                 }
                 if (!ok) break;
                 if (ROWS) mma_commit(smem_u32(&ss->empty[slot]));
@@ -1483,15 +1496,28 @@ int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* osc
 
 // narrow: 4 input chunks per position (e4m3 input, or a 32-channel bf16 input)
 // and 8 KB weight blocks; otherwise 8 chunks and 16 KB blocks.
-static size_t conv2_smem_bytes(const Geo& g, bool rows, bool narrow)
+// Row mode: ring stages of one kernel row's input piece and weights; as many
+// as fit next to the slot exchange (at most kMaxRowSlots).
+static size_t conv2_fixed_bytes() { return kXBytes + sizeof(Conv2Smem); }
+static int conv2_row_slots(bool narrow, int groups)
+{
+    const size_t stage = (size_t)(narrow ? 4 : 8) * kPiecePx * 16 + (size_t)groups * (narrow ? 8192 : 16384);
+    const size_t n = (227 * 1024 - conv2_fixed_bytes()) / stage;
+    return (int)(n > kMaxRowSlots ? kMaxRowSlots : n);
+}
+static size_t conv2_smem_bytes(const Geo& g, bool rows, bool narrow, int groups = 3)
 {
     const int nch = narrow ? 4 : 8;
     const size_t wstage = narrow ? 8192 : 16384;
-    const size_t win = rows ? (size_t)kRowSlots * nch * kPiecePx * 16 : (size_t)nch * g.nslab * kSlabPx * 16;
+    if (rows) {
+        const int slots = conv2_row_slots(narrow, groups);
+        return (size_t)slots * (nch * kPiecePx * 16 + groups * wstage) + conv2_fixed_bytes();
+    }
+    const size_t win = (size_t)nch * g.nslab * kSlabPx * 16;
     return win + (size_t)kW2Stages * wstage + kXBytes + sizeof(Conv2Smem);
 }
 
-// Row mode by default (64 x 64, batch 1024: 1.27 ms against 1.42 ms in window
+// Row mode by default (64 x 64, batch 1024: 1.20 ms against 1.42 ms in window
 // mode; wider images fit only row mode).  DEEPINV_CONV2_WINDOW=1 in
 // the environment selects window mode where the window fits in shared memory
 // (both modes give bit-identical results; the tests compare them).
@@ -1533,10 +1559,11 @@ static int launch_conv2(const void* in, int B, const Geo& g, const void* wp, con
     }
     constexpr bool narrow = V != kC2Fwd;
     const bool rows = !conv2_window_mode(g, narrow);
-    const size_t smem = conv2_smem_bytes(g, rows, narrow);
+    constexpr int groups = V == kC2Dgrad ? 6 : 3;
+    const size_t smem = conv2_smem_bytes(g, rows, narrow, groups);
     const int ntiles = B * g.t2;
     const int grid = ntiles < num_sms ? ntiles : num_sms;
-    const int nslab = rows ? kRowSlots : g.nslab;
+    const int nslab = rows ? conv2_row_slots(narrow, groups) : g.nslab;
     if (rows)
         return launch_conv2_mode<true, V>(in, B, g, wp, bias, oscale, mask_src, out, grid, smem, nslab, status, st);
     return launch_conv2_mode<false, V>(in, B, g, wp, bias, oscale, mask_src, out, grid, smem, nslab, status, st);
