@@ -189,6 +189,22 @@ int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xh
 int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, float* xhat_host,
                                void* stream);
 
+/* Asynchronous form of deepinv_sense_recover_host for a stream of batches:
+ * queues the copy of x_host [B][N] to the device, y = Phi x, x^ and the copy of
+ * x^ to xhat_host [B][N], and returns at once with *ticket.  The network keeps
+ * two device staging slots, so a batch's copies overlap the compute of the
+ * batches before and after it; the compute runs on `stream`, the copies on
+ * the network's own streams.  Host buffers must be page-locked and stay
+ * untouched until the ticket completes; all submissions and other calls on
+ * one network must use the same stream.  Errors found while queueing are
+ * returned; a bounded wait that runs out in a kernel shows in
+ * deepinv_device_status(). */
+int deepinv_sense_recover_host_submit(deepinv_net* net, const float* x_host, int B, float* xhat_host,
+                                      void* stream, uint64_t* ticket);
+
+/* Wait until the batch of `ticket` has its x^ in host memory. */
+int deepinv_host_wait(deepinv_net* net, uint64_t ticket);
+
 /* Gradient of L(Omega) = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4) by
  * backpropagation.  y [B][M] and x [B][N] are the batch; `saved` is the
  * buffer a deepinv_forward of this same y filled, or NULL: then the forward

@@ -3,6 +3,7 @@
 // management and the dispatch of the forward, backward and update passes.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -125,6 +126,14 @@ struct deepinv_net {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<int> spans;
+    // host-memory entry points: two staging slots (input and x^), copy streams
+    // and per-slot events, so that a batch's copies overlap its neighbours' compute
+    cudaStream_t cs_in = nullptr, cs_out = nullptr;
+    float* hin[2] = {nullptr, nullptr};
+    float* hout[2] = {nullptr, nullptr};
+    size_t hin_elems = 0, hout_elems = 0;
+    cudaEvent_t ev_h2d[2] = {}, ev_read[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
+    uint64_t hnext = 0;    // ticket of the next submission
 };
 
 namespace {
@@ -379,6 +388,14 @@ void free_net(deepinv_net* n)
     cudaFree(n->rsaved);
     cudaFree(n->gacc);
     for (cudaEvent_t e : n->ev_pool) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(n->hin[k]);
+        cudaFree(n->hout[k]);
+        for (cudaEvent_t e : {n->ev_h2d[k], n->ev_read[k], n->ev_comp[k], n->ev_d2h[k]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (n->cs_in) cudaStreamDestroy(n->cs_in);
+    if (n->cs_out) cudaStreamDestroy(n->cs_out);
     delete n;
 }
 
@@ -829,6 +846,80 @@ int backward_recompute(deepinv_net* net, const float* y, const float* x, int B, 
     return DEEPINV_OK;
 }
 
+// Host-memory entry points: submit one batch (input from host memory, x^ to
+// host memory) without waiting.  Slot t % 2 of the staging buffers serves
+// ticket t: its input copy (stream cs_in) waits until batch t - 2 has read the
+// slot's input, its compute (the caller's stream `st`) waits for the copy and
+// for the device -> host copy of batch t - 2 out of the slot's x^ buffer, and
+// its x^ copy (stream cs_out) follows the compute.  So batch t + 1's input and
+// batch t - 1's result move while batch t computes.  in_host is x [B][N]
+// (measure first) or y [B][M].
+int host_submit(deepinv_net* net, const float* in_host, bool measure, int B, float* xhat_host, cudaStream_t st,
+                uint64_t* ticket)
+{
+    const int N = net->N, M = net->d.M;
+    const size_t in_elems = (size_t)B * (measure ? N : M), out_elems = (size_t)B * N;
+    if (!net->cs_in) {
+        DI_CUDA(cudaStreamCreateWithFlags(&net->cs_in, cudaStreamNonBlocking));
+        DI_CUDA(cudaStreamCreateWithFlags(&net->cs_out, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k)
+            for (cudaEvent_t* e : {&net->ev_h2d[k], &net->ev_read[k], &net->ev_comp[k], &net->ev_d2h[k]})
+                DI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (in_elems > net->hin_elems || out_elems > net->hout_elems) {
+        // grow the staging slots once nothing in flight uses them
+        DI_CUDA(cudaStreamSynchronize(net->cs_in));
+        DI_CUDA(cudaStreamSynchronize(st));
+        DI_CUDA(cudaStreamSynchronize(net->cs_out));
+        for (int k = 0; k < 2; ++k) {
+            if (in_elems > net->hin_elems) {
+                cudaFree(net->hin[k]);
+                net->hin[k] = nullptr;
+                DI_TRY(dev_alloc(&net->hin[k], in_elems));
+            }
+            if (out_elems > net->hout_elems) {
+                cudaFree(net->hout[k]);
+                net->hout[k] = nullptr;
+                DI_TRY(dev_alloc(&net->hout[k], out_elems));
+            }
+        }
+        if (in_elems > net->hin_elems) net->hin_elems = in_elems;
+        if (out_elems > net->hout_elems) net->hout_elems = out_elems;
+    }
+    DI_TRY(ensure_ws(net, B, st));
+    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
+    const uint64_t t = net->hnext++;
+    const int k = (int)(t & 1);
+    DI_CUDA(cudaStreamWaitEvent(net->cs_in, net->ev_read[k], 0));
+    DI_CUDA(cudaMemcpyAsync(net->hin[k], in_host, in_elems * sizeof(float), cudaMemcpyHostToDevice, net->cs_in));
+    DI_CUDA(cudaEventRecord(net->ev_h2d[k], net->cs_in));
+    DI_CUDA(cudaStreamWaitEvent(st, net->ev_h2d[k], 0));
+    DI_CUDA(cudaStreamWaitEvent(st, net->ev_d2h[k], 0));
+    const float* y = net->hin[k];
+    if (measure) {
+        DI_TRY(net_measure_impl(net, net->hin[k], B, w.yd, st));
+        y = w.yd;
+        DI_CUDA(cudaEventRecord(net->ev_read[k], st));
+    }
+    DI_TRY(forward_impl(net, y, B, net->hout[k], nullptr, st));
+    if (!measure) DI_CUDA(cudaEventRecord(net->ev_read[k], st));
+    DI_CUDA(cudaEventRecord(net->ev_comp[k], st));
+    DI_CUDA(cudaStreamWaitEvent(net->cs_out, net->ev_comp[k], 0));
+    DI_CUDA(cudaMemcpyAsync(xhat_host, net->hout[k], out_elems * sizeof(float), cudaMemcpyDeviceToHost, net->cs_out));
+    DI_CUDA(cudaEventRecord(net->ev_d2h[k], net->cs_out));
+    if (ticket) *ticket = t;
+    return DEEPINV_OK;
+}
+
+// Wait until the x^ of `ticket` is in host memory (or a later batch's, which
+// implies it).
+int host_wait(deepinv_net* net, uint64_t ticket)
+{
+    if (!net->cs_out || ticket >= net->hnext) return DEEPINV_OK;
+    DI_CUDA(cudaEventSynchronize(net->ev_d2h[ticket & 1]));
+    return DEEPINV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1024,14 +1115,9 @@ int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xh
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (y_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DI_TRY(ensure_ws(net, B, st));
-    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
-    DI_CUDA(cudaMemcpyAsync(w.yd, y_host, (size_t)B * net->d.M * sizeof(float), cudaMemcpyHostToDevice, st));
-    DI_TRY(forward_impl(net, w.yd, B, w.xhd, nullptr, st));
-    DI_CUDA(cudaMemcpyAsync(xhat_host, w.xhd, (size_t)B * net->N * sizeof(float), cudaMemcpyDeviceToHost, st));
-    DI_CUDA(cudaStreamSynchronize(st));
-    return DEEPINV_OK;
+    uint64_t t = 0;
+    DI_TRY(host_submit(net, y_host, false, B, xhat_host, static_cast<cudaStream_t>(stream), &t));
+    return host_wait(net, t);
 }
 
 int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, float* xhat_host, void* stream)
@@ -1041,15 +1127,25 @@ int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, flo
     DI_REQUIRE(B >= 0, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (x_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DI_TRY(ensure_ws(net, B, st));
-    const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
-    DI_CUDA(cudaMemcpyAsync(w.xd, x_host, (size_t)B * net->N * sizeof(float), cudaMemcpyHostToDevice, st));
-    DI_TRY(net_measure_impl(net, w.xd, B, w.yd, st));
-    DI_TRY(forward_impl(net, w.yd, B, w.xhd, nullptr, st));
-    DI_CUDA(cudaMemcpyAsync(xhat_host, w.xhd, (size_t)B * net->N * sizeof(float), cudaMemcpyDeviceToHost, st));
-    DI_CUDA(cudaStreamSynchronize(st));
-    return DEEPINV_OK;
+    uint64_t t = 0;
+    DI_TRY(host_submit(net, x_host, true, B, xhat_host, static_cast<cudaStream_t>(stream), &t));
+    return host_wait(net, t);
+}
+
+int deepinv_sense_recover_host_submit(deepinv_net* net, const float* x_host, int B, float* xhat_host, void* stream,
+                                      uint64_t* ticket)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
+    DI_REQUIRE(B >= 1 && x_host && xhat_host && ticket, "bad batch %d or null pointer", B);
+    return host_submit(net, x_host, true, B, xhat_host, static_cast<cudaStream_t>(stream), ticket);
+}
+
+int deepinv_host_wait(deepinv_net* net, uint64_t ticket)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DeviceGuard dg(net->dev);
+    return host_wait(net, ticket);
 }
 
 int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes)

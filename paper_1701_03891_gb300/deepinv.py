@@ -83,6 +83,8 @@ SIGNATURES = {
     "deepinv_forward": (_I, [_P, _P, _I, _P, _P, _P]),
     "deepinv_forward_host": (_I, [_P, _P, _I, _P, _P]),
     "deepinv_sense_recover_host": (_I, [_P, _P, _I, _P, _P]),
+    "deepinv_sense_recover_host_submit": (_I, [_P, _P, _I, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "deepinv_host_wait": (_I, [_P, ctypes.c_uint64]),
     "deepinv_backward": (_I, [_P, _P, _P, _I, _P, _PP, _PP, _P, _P, _P]),
     "deepinv_sgd_momentum": (_I, [_P, _PP, _PP, _P, ctypes.c_float, ctypes.c_float, _P]),
     "deepinv_get_params": (_I, [_P, _PP, _PP, _P, _P]),
@@ -274,6 +276,18 @@ class Net:
         _check(lib().deepinv_sense_recover_host(self._h, x_host.data_ptr(), B, xh.data_ptr(),
                                                 _stream(stream)))
         return xh
+
+    def sense_recover_host_submit(self, x_host, out_host, stream=None) -> int:
+        """Queue sense + recover of a pinned host batch x [B][N] into the pinned
+        out_host [B][N] and return a ticket (two batches' copies and compute
+        overlap); keep both buffers alive until host_wait(ticket)."""
+        t = ctypes.c_uint64()
+        _check(lib().deepinv_sense_recover_host_submit(self._h, x_host.data_ptr(), x_host.shape[0],
+                                                       out_host.data_ptr(), _stream(stream), ctypes.byref(t)))
+        return t.value
+
+    def host_wait(self, ticket: int):
+        _check(lib().deepinv_host_wait(self._h, ctypes.c_uint64(ticket)))
 
     def new_saved(self, B: int):
         import torch

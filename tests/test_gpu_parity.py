@@ -250,6 +250,29 @@ def test_host_entry_points(di):
         assert torch.equal(sr, dev)
 
 
+def test_host_submit_overlapped_batches(di):
+    """deepinv_sense_recover_host_submit with up to three batches queued (both
+    staging slots in use and one reused) gives the same bits as the synchronous
+    call for every batch, and host_wait of an older ticket returns too."""
+    import torch
+    n1 = n2 = 32
+    phi, params, x = _case(n1, n2, 0.1, 300, seed=3)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
+    parts = [torch.from_numpy(x[i * 100:(i + 1) * 100]).pin_memory() for i in range(3)]
+    want = [net.sense_recover_host(p, torch.empty((100, n1 * n2)).pin_memory()).clone() for p in parts]
+    outs = [torch.full((100, n1 * n2), float("nan")).pin_memory() for _ in range(3)]
+    tickets = [net.sense_recover_host_submit(p, o) for p, o in zip(parts, outs)]
+    assert tickets == sorted(tickets) and len(set(tickets)) == 3
+    net.host_wait(tickets[0])
+    assert torch.equal(outs[0], want[0])
+    net.host_wait(tickets[2])
+    for o, w in zip(outs, want):
+        assert torch.equal(o, w)
+    ref = oracle.forward(oracle.measure(phi, x[:8]), params, n1, n2, phi=phi)
+    assert _maxrel(outs[0][:8].numpy(), ref) <= TOL["bf16"]
+    net.close()
+
+
 # ------------------------------------------------------------------ backward
 def _train_case(train_fc):
     n1 = n2 = 16
