@@ -295,13 +295,14 @@ __global__ void mse_partial_kernel(const float* __restrict__ xhat, const float* 
     }
 }
 
+// Loss = (sum of the block partials) / B: lane l adds partials l, l + 32, ...
+// in turn, then a fixed butterfly over the lanes (one warp).
 __global__ void mse_final_kernel(const double* __restrict__ part, int nb, int B, double* __restrict__ loss)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < nb; ++i) s += part[i];
-        *loss = s / (double)B;
-    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *loss = s / (double)B;
 }
 
 // dst[i] += src[i] (gradients of later recomputation chunks, added in chunk order).

@@ -116,14 +116,15 @@ __global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_
     }
 }
 
-// out[c] = sum_b part[b][c] in a fixed order.
+// out[c] = sum_b part[b][c] in a fixed order: one warp per channel, lane l adds
+// b = l, l + 32, ... in turn, then a fixed butterfly over the lanes.
 __global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, float* __restrict__ out)
 {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < B; ++b) s += part[(size_t)b * C + c];
-        out[c] = (float)s;
-    }
+    const int c = blockIdx.x, lane = threadIdx.x;
+    double s = 0.0;
+    for (int b = lane; b < B; b += 32) s += part[(size_t)b * C + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = (float)s;
 }
 
 
@@ -292,18 +293,20 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
 
 // dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][32 g + co][CIN pl + ci],
 // with p = GPC col + pl = 3 dy + s and dx = 4 s + g (< 11).
+// Consecutive threads take consecutive input channels ci, so that the partials
+// they read are contiguous.
 template <int CIN>
 __global__ void wgrad2_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
 {
     using C = WgCfg<CIN>;
     const int n = 32 * CIN * 121;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int dx = i % 11, dy = (i / 11) % 11, ci = (i / 121) % CIN, co = i / (121 * CIN);
+        const int ci = i % CIN, dx = (i / CIN) % 11, dy = (i / (CIN * 11)) % 11, co = i / (CIN * 121);
         const int s = dx / 4, g = dx % 4, p = dy * 3 + s, col = p / C::GPC, pl = p % C::GPC;
         double acc = 0.0;
         for (int k = 0; k < C::SPLIT; ++k)
             acc += (double)part[((size_t)(col + C::COLS * k) * 128 + g * 32 + co) * 256 + pl * CIN + ci];
-        dw[i] = (float)acc;
+        dw[((co * CIN + ci) * 11 + dy) * 11 + dx] = (float)acc;
     }
 }
 
@@ -442,19 +445,28 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
 }
 
 // conv1: dw[j][t] (= [64][1][11][11]) and db[j] from row 127; conv3: dw[j][t] (= [1][32][11][11]).
+// One block per tap row r (row 127 for the bias); thread (grp, j) adds the
+// partials of CTAs grp, grp + kTwGroups, ... (contiguous over j), then thread
+// (0, j) adds the kTwGroups sums in order: a fixed summation order.
+constexpr int kTwGroups = 8;
 template <int CJ>
 __global__ void tapwgrad_reduce_kernel(const float* __restrict__ part, int nctas, float* __restrict__ dw,
                                        float* __restrict__ db)
 {
-    const int n = CJ * 122;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int j = i / 122, r = i % 122;
-        const int row = r < 121 ? r : 127;
-        if (r == 121 && !db) continue;
-        double acc = 0.0;
-        for (int c = 0; c < nctas; ++c) acc += (double)part[((size_t)c * 128 + row) * CJ + j];
-        if (r < 121) dw[j * 121 + r] = (float)acc;
-        else db[j] = (float)acc;
+    const int r = blockIdx.x;
+    if (r == 121 && !db) return;
+    const int row = r < 121 ? r : 127;
+    const int j = threadIdx.x % CJ, grp = threadIdx.x / CJ;
+    double acc = 0.0;
+    for (int c = grp; c < nctas; c += kTwGroups) acc += (double)part[((size_t)c * 128 + row) * CJ + j];
+    __shared__ double red[kTwGroups][CJ];
+    red[grp][j] = acc;
+    __syncthreads();
+    if (grp == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kTwGroups; ++k) t += red[k][j];
+        if (r < 121) dw[j * 121 + r] = (float)t;
+        else db[j] = (float)t;
     }
 }
 
@@ -481,7 +493,7 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 {
     plane_sum_kernel<<<dim3(B, C == 1 ? 1 : C / 8), 256, 0, st>>>(src, C, geo.plane, part);
     DI_LAUNCH_CHECK();
-    sum_parts_kernel<<<1, 64, 0, st>>>(part, B, C, out);
+    sum_parts_kernel<<<C, 32, 0, st>>>(part, B, C, out);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -538,12 +550,12 @@ int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, 
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         tapwgrad_kernel<64, 1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
         DI_LAUNCH_CHECK();
-        tapwgrad_reduce_kernel<64><<<grid_for(64 * 122), 256, 0, st>>>(part, kTwCtas, dw, db);
+        tapwgrad_reduce_kernel<64><<<122, 64 * kTwGroups, 0, st>>>(part, kTwCtas, dw, db);
     } else {
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         tapwgrad_kernel<32, -1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
         DI_LAUNCH_CHECK();
-        tapwgrad_reduce_kernel<32><<<grid_for(32 * 122), 256, 0, st>>>(part, kTwCtas, dw, nullptr);
+        tapwgrad_reduce_kernel<32><<<122, 32 * kTwGroups, 0, st>>>(part, kTwCtas, dw, nullptr);
     }
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
