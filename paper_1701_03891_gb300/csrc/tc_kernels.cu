@@ -210,7 +210,9 @@ struct GemmSmem {
 
 __device__ __forceinline__ int plane_index(int j, int W, int P) { return (j / W) * P + (j % W) + kPad * P + kPad; }
 
-template <int MODE>
+// MT = 128-row tiles of A per CTA: with MT = 2 each B stage feeds two MMAs
+// (two TMEM accumulators), so B is read once per 256 rows of A.
+template <int MODE, int MT>
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict__ A, const bf16* __restrict__ Bm,
                                                          int Kp, int Mr, int Nc, int NB, uint32_t tmem_cols,
                                                          float* __restrict__ out_f32, long long ldo,
@@ -219,7 +221,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = smem_raw;
-    const uint32_t a_stage = kGemmKS * 4096;
+    const uint32_t a_tile = kGemmKS * 4096;                // one row tile's share of a stage
+    const uint32_t a_stage = MT * a_tile;
     const uint32_t b_stage = (uint32_t)kGemmKS * NB * 32;
     uint8_t* sA = smem;
     uint8_t* sB = smem + kGemmNS * a_stage;
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int mt = blockIdx.x, nt = blockIdx.y;
+    const int mtiles = min(MT, (Mr + 127) / 128 - mt * MT);   // row tiles of this CTA (the last may have one)
     // split-K: this CTA sums MMA steps [s0, s1) of the Kp / 16 and writes slice z
     const int ksplit = gridDim.z, z = blockIdx.z;
     const int nsteps_all = Kp / 16;
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
 
     if (warp == 0 && lane == 0) {
         // producer
-        const bf16* Ablk = A + (size_t)mt * (Kp / 8) * 128 * 8;
+        const bf16* Ablk = A + (size_t)mt * MT * (Kp / 8) * 128 * 8;
         const bf16* Bblk = Bm + (size_t)nt * (Kp / 8) * NB * 8;
         int armed_parity[kGemmNS];
         for (int s = 0; s < kGemmNS; ++s) armed_parity[s] = -1;
@@ -266,10 +270,12 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
             const int k0 = s0 + st * kGemmKS;
             const int ks = min(kGemmKS, s1 - k0);
             const uint32_t abytes = ks * 4096, bbytes = ks * NB * 32;
-            mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), abytes + bbytes);
+            mbar_arrive_expect_tx(smem_u32(&ss->full[slot]), mtiles * abytes + bbytes);
             armed_parity[slot] = n & 1;
-            bulk_g2s(smem_u32(sA + slot * a_stage), Ablk + (size_t)k0 * 2 * 128 * 8, abytes,
-                     smem_u32(&ss->full[slot]));
+            for (int r = 0; r < mtiles; ++r)
+                bulk_g2s(smem_u32(sA + slot * a_stage + r * a_tile),
+                         Ablk + ((size_t)r * (Kp / 8) * 128 + (size_t)k0 * 2 * 128) * 8, abytes,
+                         smem_u32(&ss->full[slot]));
             bulk_g2s(smem_u32(sB + slot * b_stage), Bblk + (size_t)k0 * 2 * NB * 8, bbytes,
                      smem_u32(&ss->full[slot]));
         }
@@ -286,9 +292,11 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
             const int k0 = s0 + st * kGemmKS;
             const int ks = min(kGemmKS, s1 - k0);
             for (int j = 0; j < ks; ++j) {
-                const uint64_t ad = sdesc(smem_u32(sA + slot * a_stage + j * 4096), 2048, 128);
                 const uint64_t bd = sdesc(smem_u32(sB + slot * b_stage + j * NB * 32), NB * 16, 128);
-                mma_bf16(tbase, ad, bd, idesc, (k0 + j) > s0 ? 1u : 0u);
+                for (int r = 0; r < mtiles; ++r) {
+                    const uint64_t ad = sdesc(smem_u32(sA + slot * a_stage + r * a_tile + j * 4096), 2048, 128);
+                    mma_bf16(tbase + (uint32_t)(r * NB), ad, bd, idesc, (k0 + j) > s0 ? 1u : 0u);
+                }
             }
             mma_commit(smem_u32(&ss->empty[slot]));
         }
@@ -301,12 +309,12 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
         bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         tc_fence_after();
-        if (ok) {
-            const int m = mt * 128 + q * 32 + lane;
+        for (int r = 0; r < mtiles && ok; ++r) {
+            const int m = (mt * MT + r) * 128 + q * 32 + lane;
             for (int c0 = 0; c0 < NB; c0 += 16) {
                 float v[16];
                 if (nsteps > 0) {
-                    tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * NB + c0), v);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -1405,13 +1413,34 @@ int tc_gemm_splitk(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB,
         set_error("tc_gemm_splitk: bad tile N=%d or K=%d", NB, Kp);
         return DEEPINV_EINVAL;
     }
+    // two row tiles per CTA when B is too large to stay in L2 (it is then read once)
+    const int mt = (Mr > 128 && (size_t)Nc * Kp * 2 > ((size_t)64 << 20)) ? 2 : 1;
+    if (mt == 2) {
+        // about one wave of CTAs over the halved tile count (the partials buffer holds 16 slices)
+        int nsm = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        const int tiles = cdiv(Mr, 256) * cdiv(Nc, NB), kmax = Kp / 16 / 16;
+        ksplit = nsm / (tiles > 0 ? tiles : 1);
+        if (ksplit > kmax) ksplit = kmax;
+        if (ksplit > 16) ksplit = 16;
+        if (ksplit < 1) ksplit = 1;
+    }
     uint32_t cols = 32;
-    while (cols < (uint32_t)NB) cols <<= 1;
-    const size_t smem = (size_t)kGemmNS * (kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
-    dim3 grid(cdiv(Mr, 128), cdiv(Nc, NB), ksplit);
-    DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tc_gemm_kernel<GEMM_OUT_F32><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, part, Nc, nullptr, 0, 0, 0, 0,
-                                                          status);
+    while (cols < (uint32_t)(mt * NB)) cols <<= 1;
+    const size_t smem = (size_t)kGemmNS * (mt * kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
+    dim3 grid(cdiv(Mr, 128 * mt), cdiv(Nc, NB), ksplit);
+    if (mt == 2) {
+        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        tc_gemm_kernel<GEMM_OUT_F32, 2><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, part, Nc, nullptr, 0, 0,
+                                                                 0, 0, status);
+    } else {
+        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        tc_gemm_kernel<GEMM_OUT_F32, 1><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, part, Nc, nullptr, 0, 0,
+                                                                 0, 0, status);
+    }
     DI_LAUNCH_CHECK();
     const long long n = (long long)Mr * Nc;
     splitk_reduce_kernel<<<grid1d(n), 256, 0, st>>>(part, ksplit, n, out);
@@ -1427,19 +1456,33 @@ int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mo
         set_error("tc_gemm: bad tile N=%d or K=%d", NB, Kp);
         return DEEPINV_EINVAL;
     }
-    uint32_t cols = 32;
-    while (cols < (uint32_t)NB) cols <<= 1;
-    const size_t smem = (size_t)kGemmNS * (kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
-    dim3 grid(cdiv(Mr, 128), cdiv(Nc, NB));
-    if (mode == GEMM_OUT_F32) {
-        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tc_gemm_kernel<GEMM_OUT_F32><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane,
-                                                              geo.H, geo.W, geo.P, geo.plane, status);
-    } else {
-        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<GEMM_OUT_PLANE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tc_gemm_kernel<GEMM_OUT_PLANE><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane,
-                                                                geo.H, geo.W, geo.P, geo.plane, status);
+    // two row tiles per CTA (B read half as often) when there are at least two per SM
+    int nsm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
     }
+    const int mt = cdiv(Mr, 128) >= 2 * nsm * cdiv(Nc, NB) ? 2 : 1;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(mt * NB)) cols <<= 1;
+    const size_t smem = (size_t)kGemmNS * (mt * kGemmKS * 4096 + (size_t)kGemmKS * NB * 32) + sizeof(GemmSmem);
+    dim3 grid(cdiv(Mr, 128 * mt), cdiv(Nc, NB));
+#define DI_GEMM_LAUNCH(MODE_, MT_)                                                                                     \
+    do {                                                                                                               \
+        DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE_, MT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                     (int)smem));                                                                      \
+        tc_gemm_kernel<MODE_, MT_><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane, geo.H,     \
+                                                             geo.W, geo.P, geo.plane, status);                         \
+    } while (0)
+    if (mode == GEMM_OUT_F32) {
+        if (mt == 2) DI_GEMM_LAUNCH(GEMM_OUT_F32, 2);
+        else DI_GEMM_LAUNCH(GEMM_OUT_F32, 1);
+    } else {
+        if (mt == 2) DI_GEMM_LAUNCH(GEMM_OUT_PLANE, 2);
+        else DI_GEMM_LAUNCH(GEMM_OUT_PLANE, 1);
+    }
+#undef DI_GEMM_LAUNCH
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
