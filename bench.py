@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="arrival window per rate")
     ap.add_argument("--eval", action="store_true",
                     help="also train 32x32 networks at M/N 0.05/0.10/0.25, clean and 20 dB SNR, and report "
-                         "the recovered images' PSNR and success rate, and 3-, 4- and 5-layer networks at M/N 0.10 (about a minute)")
+                         "the recovered images' PSNR and success rate, 3-, 4- and 5-layer networks at M/N 0.10, and a 64x64 convergence curve (about a minute)")
     return ap.parse_args()
 
 
@@ -654,7 +654,8 @@ def run_native(args):
         evaluation = {"workload": "32x32 Voronoi images, 512 training / 64 test, 6000 SGD-momentum steps of 64 "
                                   "(bf16, FC = Phi^T), step 1e-3 / first loss",
                       "points": evaluate.sweep(32, ratios=(0.05, 0.10, 0.25), snrs=(None, 20.0)),
-                      "depth": evaluate.depth_sweep(32, 0.10, hiddens=(0, 1, 2))}
+                      "depth": evaluate.depth_sweep(32, 0.10, hiddens=(0, 1, 2)),
+                      "convergence_64": evaluate.train_and_evaluate(64, 0.10, steps=6000, curve_every=1000)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

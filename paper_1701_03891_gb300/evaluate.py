@@ -45,7 +45,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
                        test_images: int = 64, batch: int = 64, steps: int = 6000, lr: float | None = None,
                        lr_scale: float = 1e-3,
                        mu: float = 0.9, snr_db: float | None = None, prec: str = "bf16", seed: int = 0,
-                       hidden: int = 0) -> dict:
+                       hidden: int = 0, curve_every: int | None = None) -> dict:
     """Train an n x n network at measurement ratio M/N (the FC layer fixed to Phi^T)
     with SGD with momentum on the bfloat16 path and evaluate it.  The loss is a
     sum over pixels (Sec. 4), so its scale varies with M/N and the images; the
@@ -53,7 +53,9 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
     training and test measurements carry Gaussian noise at that SNR.  ``hidden``
     adds that many 32 -> 32 layers before the last (the deeper networks of
     Sec. 5).  Returns the mean PSNR and success rate on the test images, before
-    and after training, and the first and last training losses."""
+    and after training, and the first and last training losses; with
+    ``curve_every``, also the test PSNR and success rate every that many steps
+    (the convergence of training, Fig. 5's analogue)."""
     import torch
     from . import deepinv
 
@@ -82,6 +84,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
     saved, grads = net.new_saved(batch), net.grad_buffers()
     first = last = None
     step = lr
+    curve = [(0, before[0], before[1])] if curve_every else None
     for k in range(steps):
         lo = (k * batch) % train_images
         yb, xb = yt[lo:lo + batch].contiguous(), xt[lo:lo + batch].contiguous()
@@ -92,6 +95,8 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
             if step is None:
                 step = lr_scale / first
         net.sgd_momentum(dW, db, None, lr=step, mu=mu)
+        if curve_every and (k + 1) % curve_every == 0:
+            curve.append((k + 1,) + quality(net))
     last = float(loss)
     if prec == "bf16":
         after = quality(net)
@@ -104,7 +109,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
         other.close()
     net.close()
     return {"n": n, "ratio": ratio, "M": M, "snr_db": snr_db, "images": images, "steps": steps, "lr": step,
-            "conv_layers": 3 + hidden,
+            "conv_layers": 3 + hidden, "curve": curve,
             "psnr_db_before": before[0], "success_before": before[1],
             "psnr_db": after[0], "success": after[1], "loss_first": first, "loss_last": last}
 

@@ -45,3 +45,19 @@ def test_training_improves_recovery():
         assert r["psnr_db"] > r["psnr_db_before"] + 5.0, r
         assert 0.0 <= r["success"] <= 1.0
     assert noisy["psnr_db"] <= clean["psnr_db"] + 0.5
+
+
+@pytest.mark.gpu
+def test_convergence_curve_64():
+    """Training a 64 x 64 network records test PSNR every 500 steps; the last point
+    matches the returned result and training has raised it well above the start."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_03891_gb300 import build
+    build.build()
+    r = evaluate.train_and_evaluate(64, 0.10, steps=1500, test_images=16, curve_every=500)
+    steps = [c[0] for c in r["curve"]]
+    assert steps == [0, 500, 1000, 1500]
+    assert abs(r["curve"][-1][1] - r["psnr_db"]) < 1e-9
+    assert r["curve"][-1][1] > r["curve"][0][1] + 5.0, r["curve"]
