@@ -216,7 +216,7 @@ struct FwdWs {
     bf16* h;                // hidden layers: second 32-channel plane (ping-pong with a2)
     float *T;
     float *fxt, *fa1, *fa2, *fh;
-    float *yd, *xd, *xhd;   // device staging of the host-memory entry points
+    float *yd, *xhd;        // y of the host-memory entry points; x^ staging (serving, recomputation)
     float* mpart;           // split-K partials of the measurement GEMM
     size_t bytes;
 };
@@ -244,7 +244,6 @@ FwdWs carve_fwd(const deepinv_net* n, int B, char* base)
     }
     if (n->tc) w.mpart = a.take<float>((size_t)16 * B * M);   // split-K partials of y = Phi x
     w.yd = a.take<float>((size_t)B * M);
-    w.xd = a.take<float>((size_t)B * N);
     w.xhd = a.take<float>((size_t)B * N);
     w.bytes = align_up(a.off, 256);
     return w;
