@@ -90,6 +90,13 @@ int deepinv_version(void);
  * reset.  Synchronises the device.  `reset` != 0 clears it. */
 int deepinv_device_status(int reset);
 
+/* Failure-path check of the device status word (no counterpart in the paper):
+ * launches one kernel on the current device whose bounded wait is never
+ * satisfied; after the wait's time limit (about 1 s) it records a timeout and
+ * returns without a fault, so the context stays usable.  Waits for it.
+ * deepinv_device_status() then reports DEEPINV_ETIMEOUT until reset. */
+int deepinv_selftest_bounded_wait(void* stream);
+
 /* y = Phi x for B signals (Sec. 1).
  * phi [M][N], x [B][N] -> y [B][M], all float32 device memory.
  * prec selects float32 CUDA-core products or bfloat16 tensor-core products

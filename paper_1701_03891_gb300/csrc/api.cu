@@ -951,6 +951,16 @@ int deepinv_device_status(int reset)
     return DEEPINV_OK;
 }
 
+int deepinv_selftest_bounded_wait(void* stream)
+{
+    int* status = device_status_word();
+    DI_REQUIRE(status, "no device status word");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DI_TRY(bounded_wait_probe(status, st));
+    DI_CUDA(cudaStreamSynchronize(st));
+    return DEEPINV_OK;
+}
+
 int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y, int prec, void* stream)
 {
     DI_REQUIRE(M >= 1 && N >= 1 && B >= 0, "bad sizes M=%d N=%d B=%d", M, N, B);

@@ -147,6 +147,9 @@ size_t conv3_scratch_elems(const Geo& g, int B, int cin);
 int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* b3, float* T,
              float* xhat, int final_relu, int* status, cudaStream_t st);
 
+// One kernel whose bounded wait never completes: records DEV_TIMEOUT in `status`.
+int bounded_wait_probe(int* status, cudaStream_t st);
+
 // Layout conversions for the backward pass (bf16 planes -> float32 NCHW).
 int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st);
 

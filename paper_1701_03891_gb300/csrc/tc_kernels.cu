@@ -1638,6 +1638,30 @@ int hidden_dgrad_tc(const bf16* gout, int B, const Geo& g, const bf16* wht, cons
 }
 
 
+// Failure-path check: one thread waits, with the bounded wait every pipeline
+// uses, for an mbarrier phase that nothing completes.  After the wait's time
+// limit it records DEV_TIMEOUT in the status word and the kernel returns; no
+// copy, MMA or TMEM is involved, so nothing is left in flight.
+__global__ void bounded_wait_probe_kernel(int* status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, status, &abort_flag);
+}
+
+int bounded_wait_probe(int* status, cudaStream_t st)
+{
+    bounded_wait_probe_kernel<<<1, 32, 0, st>>>(status);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
 size_t conv3_chunk(const Geo& g, int B)
 {
     // images per unfused conv3 pass: the row sums T of one pass stay within ~48 MB of L2

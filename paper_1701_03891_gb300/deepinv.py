@@ -70,6 +70,7 @@ SIGNATURES = {
     "deepinv_last_error": (ctypes.c_char_p, []),
     "deepinv_version": (_I, []),
     "deepinv_device_status": (_I, [_I]),
+    "deepinv_selftest_bounded_wait": (_I, [_P]),
     "deepinv_measure": (_I, [_P, _I, _I, _P, _I, _P, _I, _P]),
     "deepinv_measure_noalloc": (_I, [_P, _I, _I, _P, _I, _P, _P]),
     "deepinv_net_create": (_I, [ctypes.POINTER(NetDesc), _P, _PP, _PP, _P, ctypes.POINTER(_P)]),
@@ -149,6 +150,12 @@ def _arr(ptrs):
 
 def device_status(reset: bool = False) -> int:
     return lib().deepinv_device_status(1 if reset else 0)
+
+
+def selftest_bounded_wait(stream=None):
+    """Run one kernel whose bounded wait never completes (about 1 s); afterwards
+    device_status() reports ETIMEOUT until reset."""
+    _check(lib().deepinv_selftest_bounded_wait(_stream(stream)))
 
 
 def measure(phi, x, prec="f32", out=None, stream=None):

@@ -403,5 +403,24 @@ def test_autograd_function(di):
     assert err <= 1e-4
 
 
+def test_bounded_wait_timeout_reported_and_context_usable(di):
+    """A wait that nothing satisfies runs out (about 1 s), the kernel returns, the
+    host reads DEEPINV_ETIMEOUT from the status word, and after the reset the
+    device keeps computing correct results."""
+    import time
+    assert di.device_status(reset=True) == 0
+    t0 = time.perf_counter()
+    di.selftest_bounded_wait()
+    assert time.perf_counter() - t0 >= 0.9
+    assert di.device_status(reset=True) == di.ETIMEOUT
+    assert di.device_status() == 0
+    phi, params, x = _case(32, 32, 0.1, 2)
+    net = di.Net(phi, params, 32, 32, prec="bf16")
+    y = _cuda(oracle.measure(phi, x))
+    ref = oracle.forward(y.cpu().numpy(), params, 32, 32, phi=phi)
+    assert _maxrel(net.forward(y).cpu().numpy(), ref) <= TOL["bf16"]
+    assert di.device_status() == 0
+
+
 def test_device_status_clean(di):
     assert di.device_status() == 0
