@@ -569,9 +569,12 @@ def run_native(args):
     clk = clocks.stop()
     stages = net.profile_read()
     net.profile(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    step_times = sorted(a.elapsed_time(b) for a, b in evs)
+    dev_ms = sum(step_times)
     dev_ms, value = aggregate(dev_ms, B, args.steps, world, dist, device="cuda")
     ms_per_step = dev_ms / args.steps
+    step_stats = {"median": step_times[len(step_times) // 2], "min": step_times[0], "max": step_times[-1],
+                  "note": "this rank's per-step CUDA-event times (ms)"}
 
     conv2_ms = stages["conv2"][0] / max(1, stages["conv2"][1])
     conv2_flop = 2.0 * CONV2_MAC_PER_PX * B * n * n
@@ -663,7 +666,8 @@ def run_native(args):
 
     status = deepinv.device_status()
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "step_ms": step_stats,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (seeded Voronoi images standing in for ImageNet 64x64 crops; He-init weights)",
             "config": config(args, n, M, world),

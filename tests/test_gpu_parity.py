@@ -108,6 +108,25 @@ def test_forward_bf16_wide(di, n1, n2, ratio, B):
     assert _maxrel(xhat, ref) <= TOL["bf16"]
 
 
+def test_gemm_two_row_tiles_odd_counts(di):
+    """GEMMs with a large B operand take two 128-row tiles per CTA; with an odd
+    tile count the last CTA has one.  Measurement: Phi 520 x 65536 (68 MB) and
+    260 images = 3 row tiles; FC layer: a 200 x 200 image = 313 pixel tiles."""
+    rng = np.random.default_rng(21)
+    N, M, B = 256 * 256, 520, 260
+    phi = synth.gaussian_phi(M, N, seed=21)
+    x = rng.uniform(0, 1, (B, N)).astype(np.float32)
+    net = di.Net(phi, synth.he_params(seed=1), 256, 256, prec="bf16")
+    y = net.measure(_cuda(x)).cpu().numpy()
+    assert _maxrel(y, oracle.measure(phi, x)) <= TOL["bf16"]
+    net.close()
+    phi2, params, x2 = _case(200, 200, 0.02, 2, seed=4)
+    net2 = di.Net(phi2, params, 200, 200, prec="bf16")
+    y2 = _cuda(oracle.measure(phi2, x2))
+    ref = oracle.forward(y2.cpu().numpy(), params, 200, 200, phi=phi2)
+    assert _maxrel(net2.forward(y2).cpu().numpy(), ref) <= TOL["bf16"]
+
+
 @pytest.mark.parametrize("n1,n2,ratio,B", [
     (6, 119, 0.10, 2),      # pitch 124: conv3 keeps row sums in its shared-memory ring
     (6, 120, 0.10, 2),      # pitch 125: conv3 keeps partial outputs instead
