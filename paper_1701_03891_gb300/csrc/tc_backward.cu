@@ -128,6 +128,21 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, 
 }
 
 
+// ---------------------------------------------------------------- cp.async (16 bytes, L2 only)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Arrive on `bar` once all of this thread's earlier cp.async copies have
+// completed (the barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------- conv2 weight gradient
 // dW2[co][ci][dy][4 s + g] = sum_u' G[u' - g][co] A1[u' + (dy - 5) P + 4 s - 5][ci]
 // as MMAs with K = 16 plane positions u', both operands MN-major (channels
@@ -139,8 +154,15 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int B, int C, 
 // groups p make WgCfg::COLS CTA columns; positions are split over
 // WgCfg::SPLIT CTAs each; every CTA leaves a 128 x 256 float32 partial,
 // summed in float64 in a fixed order.
-constexpr int kWgKB = 128;           // positions per stage
-constexpr int kWgStages = 2;
+//
+// Loading is the limit (every stage pulls 48 small shifted windows from L2):
+// the first half of a stage's windows go by 1-D bulk copy from warp 0, the
+// other half by 16-byte cp.async from the four epilogue warps (idle until
+// the end), both completing the stage's barrier.  Measured at 64 x 64, batch
+// 256: this split with 3 stages of 96 positions beats bulk copies alone
+// (2 x 128: backward 1.95 ms; 3 x 96: 2.28 ms) at 1.87 ms, and 1/3 or 2/3 bulk.
+constexpr int kWgKB = 96;           // positions per stage
+constexpr int kWgStages = 3;
 constexpr uint32_t kWgABytes = 16 * kWgKB * 16;     // 16 M-groups
 constexpr uint32_t kWgBBytes = 32 * kWgKB * 16;     // 32 N-groups
 
@@ -179,6 +201,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
     const int ngroups = min(C::GPC, 33 - col * C::GPC);
     const int NB = ngroups * CIN;
     const int ncopy = 16 + C::CPG * ngroups;
+    const int nbulk = ncopy / 2;                 // windows [0, nbulk) by bulk copy, the rest by cp.async
     const int nb_img = (HP16 + kWgKB - 1) / kWgKB;
     const long long total = (long long)B * nb_img;
     const long long blk0 = total * split / C::SPLIT, blk1 = total * (split + 1) / C::SPLIT;
@@ -186,7 +209,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kWgStages; ++s) {
-            mbar_init(smem_u32(&ss->full[s]), 1);
+            mbar_init(smem_u32(&ss->full[s]), 1 + 128);    // producer (bulk bytes) + 128 cp.async threads
             mbar_init(smem_u32(&ss->empty[s]), 1);
         }
         mbar_init(smem_u32(&ss->acc_full), 1);
@@ -207,7 +230,8 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
         // producer warp: lane 0 waits and arms the stage barrier, then the 16 + CPG ngroups
         // window copies of the stage are issued by all 32 lanes (small bulk copies are
         // limited by their issue rate per thread)
-        int parity[kWgStages] = {-1, -1};
+        int parity[kWgStages];
+        for (int s = 0; s < kWgStages; ++s) parity[s] = -1;
         for (long long k = blk0; k < blk1; ++k) {
             const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
             bool ok = true;
@@ -216,14 +240,14 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
             const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
             const int npos = min(kWgKB, u_begin + HP16 - u0);
             const uint32_t bytes = (uint32_t)npos * 16;
-            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (uint32_t)ncopy * bytes);
+            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (uint32_t)nbulk * bytes);
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             parity[st] = n & 1;
             const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
             const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * C::CPG * plane_len * 16;
             uint8_t* dA = sA + st * kWgABytes;
             uint8_t* dB = sB + st * kWgBBytes;
-            for (int c = lane; c < ncopy; c += 32) {
+            for (int c = lane; c < nbulk; c += 32) {
                 if (c < 16) {
                     const int g = c / 4, c4 = c % 4;
                     bulk_g2s(smem_u32(dA + (g * 4 + c4) * kWgKB * 16),
@@ -243,12 +267,46 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
                     const unsigned long long t0 = globaltimer();
                     while (!mbar_try_wait(smem_u32(&ss->full[s]), parity[s]) && globaltimer() - t0 < 1000000000ull) {}
                 }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp >= 2) {
+        // loaders of windows [nbulk, ncopy): one warp per window, 16 bytes per lane per copy
+        const int lw = warp - 2;
+        for (long long k = blk0; k < blk1; ++k) {
+            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+            const int b = (int)(k / nb_img);
+            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
+            const int npos = min(kWgKB, u_begin + HP16 - u0);
+            const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
+            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * C::CPG * plane_len * 16;
+            const uint32_t dA = smem_u32(sA + st * kWgABytes), dB = smem_u32(sB + st * kWgBBytes);
+            for (int c = nbulk + lw; c < ncopy; c += 4) {
+                uint32_t dst;
+                const uint8_t* src;
+                if (c < 16) {
+                    const int g = c / 4, c4 = c % 4;
+                    dst = dA + (g * 4 + c4) * kWgKB * 16;
+                    src = g2b + ((size_t)c4 * plane_len + u0 - g) * 16;
+                } else {
+                    const int pl = (c - 16) / C::CPG, c8 = (c - 16) % C::CPG;
+                    const int p = col * C::GPC + pl, dy = p / 3, s = p % 3;
+                    dst = dB + (pl * C::CPG + c8) * kWgKB * 16;
+                    src = a1b + ((size_t)c8 * plane_len + u0 + (dy - 5) * P + 4 * s - 5) * 16;
+                }
+                for (int i = lane; i < npos; i += 32) cp_async16(dst + i * 16, src + (size_t)i * 16);
+            }
+            cp_async_arrive(smem_u32(&ss->full[st]));
+        }
+        cp_async_wait_all();
+    }
+    if (warp == 1 && lane == 0) {
         const uint32_t idesc = idesc_bf16_mn(128, NB);
         bool first = true;
         for (long long k = blk0; k < blk1; ++k) {
             const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
             if (!mbar_wait(smem_u32(&ss->full[st]), n & 1, status, &ss->abort_flag)) break;
+            fence_proxy_async();   // part of the stage was written by cp.async (generic proxy)
             tc_fence_after();
             const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
             const int nsteps = min(kWgKB, u_begin + HP16 - u0) / 16;
@@ -266,7 +324,8 @@ __global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__
         mma_commit(smem_u32(&ss->drain));
         const unsigned long long t0 = globaltimer();
         while (!mbar_try_wait(smem_u32(&ss->drain), 0) && globaltimer() - t0 < 1000000000ull) {}
-    } else if (warp >= 2) {
+    }
+    if (warp >= 2) {
         const int q = warp % 4;
         bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
         ok = __all_sync(0xffffffffu, ok);
