@@ -935,6 +935,21 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
             const int b = tile / t2, q0 = (tile % t2) * kConv2Valid;
             const uint32_t lane_addr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * kConv2N;
             for (int cc = 0; cc < kConv2N; cc += 32) {
+                const int jcol = cc + jl, qq = q0 + jcol;
+                const bool store = jcol < kConv2Valid && qq < HP;
+                const bool data = store && (qq % P) < W;
+                const size_t pos = (size_t)(qq + kPad * P + kPad);
+                constexpr int OUTCH = DGRAD ? 8 : 4;
+                // ReLU masks of this thread's outputs, loaded before the TMEM read and
+                // the slot exchange so that their latency overlaps them
+                uint4 mk[ITEMS];
+#pragma unroll
+                for (int item = 0; item < ITEMS; ++item) {
+                    mk[item] = make_uint4(0, 0, 0, 0);
+                    if (MASK && data)
+                        mk[item] = *reinterpret_cast<const uint4*>(
+                            mask_src + (((size_t)b * OUTCH + le / 32 + 4 * item) * plane_len + pos) * 8);
+                }
                 float v[36];
                 tmem_ld32(lane_addr + cc, v);
                 if (cc + 32 < kConv2N) {
@@ -949,10 +964,6 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                     default: put_shifted<3>(xrow, v); break;
                 }
                 epi_bar();
-                const int jcol = cc + jl, qq = q0 + jcol;
-                const bool store = jcol < kConv2Valid && qq < HP;
-                const bool data = store && (qq % P) < W;
-                const size_t pos = (size_t)(qq + kPad * P + kPad);
 #pragma unroll
                 for (int item = 0; item < ITEMS; ++item) {
                     const int c8 = le / 32 + 4 * item;                // 8-channel group of the output
@@ -969,14 +980,10 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
                         acc[e] = FP8 ? fmaf(t, scale8[e], bias8[e]) : t + bias8[e];
                     }
                     if (store) {
-                        constexpr int OUTCH = DGRAD ? 8 : 4;
                         bf16* dst = a2 + (((size_t)b * OUTCH + c8) * plane_len + pos) * 8;
                         if (MASK) {
                             // input gradient times the ReLU mask [input > 0]; zero outside the image
-                            uint4 mk = make_uint4(0, 0, 0, 0);
-                            if (data)
-                                mk = *reinterpret_cast<const uint4*>(mask_src + (((size_t)b * OUTCH + c8) * plane_len + pos) * 8);
-                            const bf16* mv = reinterpret_cast<const bf16*>(&mk);
+                            const bf16* mv = reinterpret_cast<const bf16*>(&mk[item]);
 #pragma unroll
                             for (int e = 0; e < 8; ++e) acc[e] = (data && __bfloat162float(mv[e]) > 0.f) ? acc[e] : 0.f;
                         } else {
