@@ -1,11 +1,15 @@
 // bfloat16 tcgen05 tensor-core kernels of libdeepinv (sm_103a).
 //
-//  * tc_gemm   -- y = Phi x (Sec. 1) and the FC layer x~ = Phi^T y (Sec. 4).
+//  * tc_gemm   -- y = Phi x (Sec. 1) and the FC layer x~ = Phi^T y (Sec. 4);
+//                 one or two 128-row tiles per CTA, optional split-K.
 //  * conv1_tc  -- Eq. (1), layer 1 (1 -> 64 filters of 11 x 11): per kernel
 //                 row one GEMM with M = 128 positions, N = 64 filters, K = 16
 //                 columns, the A operand read straight from an expanded window.
 //  * conv2_tc  -- layer 2 (64 -> 32), 95 % of the network's flops, as a
-//                 tap-stacked implicit GEMM (below).
+//                 tap-stacked implicit GEMM (below); the same kernel, as
+//                 template variants, computes the e4m3 forward, conv2's input
+//                 gradient and the hidden 32 -> 32 layers of deeper networks
+//                 (forward and input gradient).
 //  * conv3_tc  -- layer 3 (32 -> 1): per-row partial sums by GEMM (N = kernel
 //                 row x column phase), summed over the 11 kernel rows in a
 //                 shared-memory ring in the same kernel.
