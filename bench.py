@@ -487,6 +487,8 @@ def run_reference(args):
     import oracle
     from paper_1701_03891_gb300 import synth
     oracle.build()
+    # rank 0 has the host to itself (a launcher sets OMP_NUM_THREADS=1 for its workers)
+    oracle.set_num_threads(os.cpu_count() or 1)
     n = args.size
     N = n * n
     M = synth.m_for_ratio(args.ratio, N)

@@ -191,6 +191,18 @@ void oracle_fc_wgrad(const double* dxt, const double* y, int B, int N, int M, do
         }
 }
 
+/* Threads of later parallel loops (the timed baselines use every host core;
+ * a launcher may have set OMP_NUM_THREADS=1 for its workers). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of threads the OpenMP runtime will use (reported by the baseline). */
 int oracle_num_threads(void)
 {

@@ -68,6 +68,7 @@ def _get():
             lib.oracle_conv_same_dgrad.argtypes = [dp, dp, i, i, i, i, i, i, dp]
             lib.oracle_fc_wgrad.argtypes = [dp, dp, i, i, i, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_num_threads.argtypes = [i]
             _lib = lib
     return _lib
 
@@ -82,6 +83,11 @@ def _p(a: np.ndarray):
 
 def num_threads() -> int:
     return int(_get().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing only)."""
+    _get().oracle_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- primitives
