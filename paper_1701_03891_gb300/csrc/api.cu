@@ -288,6 +288,28 @@ Saved carve_saved(const deepinv_net* n, int B, char* base)
     return s;
 }
 
+// Zero what the forward kernels never write in a caller's saved buffer: the
+// whole one-channel x~ plane (the FC layer writes its pixels only, not the pad
+// columns) and, of every multi-channel plane, the positions before its first
+// pixel row and after its last (conv1, conv2 and the hidden layers write every
+// position in between, pad columns included).
+int clear_saved_borders(const deepinv_net* n, const Saved& sv, int B, cudaStream_t st)
+{
+    const Geo& g = n->geo;
+    const size_t head = (size_t)kPad * g.P + kPad, tail0 = (size_t)g.HP + head, tail = (size_t)g.plane - tail0;
+    const size_t pitch = (size_t)g.plane * 16;
+    DI_CUDA(cudaMemsetAsync(sv.xt, 0, (size_t)B * g.plane * sizeof(bf16), st));
+    auto borders = [&](bf16* base, size_t nplanes) -> int {
+        DI_CUDA(cudaMemset2DAsync(base, pitch, 0, head * 16, nplanes, st));
+        DI_CUDA(cudaMemset2DAsync(reinterpret_cast<char*>(base) + tail0 * 16, pitch, 0, tail * 16, nplanes, st));
+        return DEEPINV_OK;
+    };
+    DI_TRY(borders(sv.a1, (size_t)B * 8));
+    DI_TRY(borders(sv.a2, (size_t)B * 4));
+    if (n->d.hidden > 0) DI_TRY(borders(sv.h, (size_t)B * 4 * n->d.hidden));
+    return DEEPINV_OK;
+}
+
 int ensure_ws(deepinv_net* n, int B, cudaStream_t st)
 {
     if (B <= n->ws_B && n->ws) return DEEPINV_OK;
@@ -446,7 +468,7 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
     Saved sv{};
     if (saved) {
         sv = carve_saved(n, B, static_cast<char*>(saved));
-        DI_CUDA(cudaMemsetAsync(saved, 0, sv.bytes, st));
+        if (n->tc) DI_TRY(clear_saved_borders(n, sv, B, st));   // float32 arrays are written in full
     }
     if (n->tc) {
         const Geo& g = n->geo;
