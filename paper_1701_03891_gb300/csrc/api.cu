@@ -1214,12 +1214,15 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float*
     for (int l = 0; l < net->L; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // every tensor in one launch (2 L + 1 <= kSgdMaxTensors)
+    SgdTensors t{};
     for (int l = 0; l < net->L; ++l) {
-        DI_TRY(sgd_momentum_f32(net->w[l], net->vw[l], dW[l], (long long)wsize(net, l), lr, mu, st));
-        DI_TRY(sgd_momentum_f32(net->b[l], net->vb[l], db[l], (long long)bsize(net, l), lr, mu, st));
+        t.w[t.count] = net->w[l], t.v[t.count] = net->vw[l], t.g[t.count] = dW[l], t.n[t.count++] = (long long)wsize(net, l);
+        t.w[t.count] = net->b[l], t.v[t.count] = net->vb[l], t.g[t.count] = db[l], t.n[t.count++] = (long long)bsize(net, l);
     }
     if (net->d.train_fc)
-        DI_TRY(sgd_momentum_f32(net->wfc, net->vfc, dWfc, (long long)net->N * net->d.M, lr, mu, st));
+        t.w[t.count] = net->wfc, t.v[t.count] = net->vfc, t.g[t.count] = dWfc, t.n[t.count++] = (long long)net->N * net->d.M;
+    DI_TRY(sgd_momentum_multi(t, lr, mu, st));
     return repack(net, st);
 }
 

@@ -324,6 +324,24 @@ __global__ void sgd_momentum_kernel(float* __restrict__ w, float* __restrict__ v
     }
 }
 
+// The same step for several tensors in one launch: tensor k owns blocks
+// [t.boff[k], t.boff[k + 1]) of the grid.
+__global__ void sgd_momentum_multi_kernel(SgdTensors t, float lr, float mu)
+{
+    int k = 0;
+    while (k + 1 < t.count && (int)blockIdx.x >= t.boff[k + 1]) ++k;
+    float* __restrict__ w = t.w[k];
+    float* __restrict__ v = t.v[k];
+    const float* __restrict__ g = t.g[k];
+    const long long n = t.n[k];
+    const long long nb = t.boff[k + 1] - t.boff[k];
+    for (long long i = ((long long)blockIdx.x - t.boff[k]) * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) {
+        const float vn = mu * v[i] + g[i];
+        v[i] = vn;
+        w[i] = w[i] - lr * vn;
+    }
+}
+
 inline int grid_for(long long n, int threads = 256)
 {
     long long b = (n + threads - 1) / threads;
@@ -389,6 +407,24 @@ int accumulate_f64(double* dst, const double* src, long long n, cudaStream_t st)
 {
     if (n <= 0) return DEEPINV_OK;
     accumulate_kernel<double><<<grid_for(n), 256, 0, st>>>(dst, src, n);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int sgd_momentum_multi(SgdTensors t, float lr, float mu, cudaStream_t st)
+{
+    if (t.count <= 0) return DEEPINV_OK;
+    // blocks per tensor: about 4 elements per thread, at most 2432
+    int total = 0;
+    for (int k = 0; k < t.count; ++k) {
+        t.boff[k] = total;
+        long long nb = (t.n[k] + 1023) / 1024;
+        if (nb < 1) nb = 1;
+        if (nb > 2432) nb = 2432;
+        total += (int)nb;
+    }
+    t.boff[t.count] = total;
+    sgd_momentum_multi_kernel<<<total, 256, 0, st>>>(t, lr, mu);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

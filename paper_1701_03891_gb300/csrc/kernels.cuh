@@ -29,6 +29,17 @@ int accumulate_f32(float* dst, const float* src, long long n, cudaStream_t st);
 int accumulate_f64(double* dst, const double* src, long long n, cudaStream_t st);
 int sgd_momentum_f32(float* w, float* v, const float* g, long long n, float lr, float mu,
                      cudaStream_t st);
+// One launch of the same step over up to kSgdMaxTensors tensors (passed by value).
+constexpr int kSgdMaxTensors = 40;
+struct SgdTensors {
+    float* w[kSgdMaxTensors];
+    float* v[kSgdMaxTensors];
+    const float* g[kSgdMaxTensors];
+    long long n[kSgdMaxTensors];
+    int boff[kSgdMaxTensors + 1];   // first grid block of each tensor (set by the launcher)
+    int count;
+};
+int sgd_momentum_multi(SgdTensors t, float lr, float mu, cudaStream_t st);
 
 // ---------------------------------------------------------------- bfloat16 tensor-core path (tc_kernels.cu)
 // Packed K-major operand: dst holds ceil(R / TR) row tiles, each Kp / 8
