@@ -313,17 +313,6 @@ __global__ void accumulate_kernel(T* __restrict__ dst, const T* __restrict__ src
         dst[i] += src[i];
 }
 
-__global__ void sgd_momentum_kernel(float* __restrict__ w, float* __restrict__ v,
-                                    const float* __restrict__ g, long long n, float lr, float mu)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float vn = mu * v[i] + g[i];
-        v[i] = vn;
-        w[i] = w[i] - lr * vn;
-    }
-}
-
 // The same step for several tensors in one launch: tensor k owns blocks
 // [t.boff[k], t.boff[k + 1]) of the grid.
 __global__ void sgd_momentum_multi_kernel(SgdTensors t, float lr, float mu)
@@ -425,15 +414,6 @@ int sgd_momentum_multi(SgdTensors t, float lr, float mu, cudaStream_t st)
     }
     t.boff[t.count] = total;
     sgd_momentum_multi_kernel<<<total, 256, 0, st>>>(t, lr, mu);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
-}
-
-int sgd_momentum_f32(float* w, float* v, const float* g, long long n, float lr, float mu,
-                     cudaStream_t st)
-{
-    if (n <= 0) return DEEPINV_OK;
-    sgd_momentum_kernel<<<grid_for(n), 256, 0, st>>>(w, v, g, n, lr, mu);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

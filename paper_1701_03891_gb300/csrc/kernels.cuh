@@ -27,9 +27,8 @@ int transpose_f32(const float* src, int R, int C, float* dst, cudaStream_t st);
 // dst += src, element-wise.
 int accumulate_f32(float* dst, const float* src, long long n, cudaStream_t st);
 int accumulate_f64(double* dst, const double* src, long long n, cudaStream_t st);
-int sgd_momentum_f32(float* w, float* v, const float* g, long long n, float lr, float mu,
-                     cudaStream_t st);
-// One launch of the same step over up to kSgdMaxTensors tensors (passed by value).
+// SGD with momentum, v <- mu v + g; w <- w - lr v, over up to kSgdMaxTensors
+// tensors in one launch (passed by value).
 constexpr int kSgdMaxTensors = 40;
 struct SgdTensors {
     float* w[kSgdMaxTensors];
@@ -161,7 +160,5 @@ int conv3_tc(const bf16* a2, int B, const Geo& g, const bf16* w3p, const float* 
 // One kernel whose bounded wait never completes: records DEV_TIMEOUT in `status`.
 int bounded_wait_probe(int* status, cudaStream_t st);
 
-// Layout conversions for the backward pass (bf16 planes -> float32 NCHW).
-int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st);
 
 }  // namespace di

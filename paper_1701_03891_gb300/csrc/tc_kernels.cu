@@ -1346,25 +1346,6 @@ __global__ void conv3_sum_kernel(const float* __restrict__ T, int B, int H, int 
     }
 }
 
-// bf16 planes -> float32 NCHW (C == 1: [B][plane]; C % 8 == 0: [B][C/8][plane][8]).
-__global__ void plane_to_nchw_kernel(const bf16* __restrict__ src, int B, int C, int H, int W, int P,
-                                     int plane_len, float* __restrict__ dst)
-{
-    const long long n = (long long)B * C * H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % W);
-        const int r = (int)((i / W) % H);
-        const int ch = (int)((i / ((long long)W * H)) % C);
-        const long long b = i / ((long long)W * H * C);
-        const long long pos = (long long)r * P + c + kPad * P + kPad;
-        size_t off;
-        if (C == 1) off = (size_t)b * plane_len + pos;
-        else off = (((size_t)b * (C / 8) + ch / 8) * plane_len + pos) * 8 + (ch % 8);
-        dst[i] = __bfloat162float(src[off]);
-    }
-}
-
 // y[m][n] = sum_z part[z][m][n] (fixed order) for the split-K GEMM.
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, long long n, float* __restrict__ y)
 {
@@ -1758,15 +1739,6 @@ int conv1_dgrad_tc(const bf16* g1, int B, const Geo& g, const bf16* w1t, float* 
                    cudaStream_t st)
 {
     return conv3_all<64>(g1, B, g, w1t, nullptr, T, dxt, 0, status, st);
-}
-
-int plane_to_nchw(const bf16* src, int B, int C, const Geo& g, float* dst, cudaStream_t st)
-{
-    const long long n = (long long)B * C * g.H * g.W;
-    if (n <= 0) return DEEPINV_OK;
-    plane_to_nchw_kernel<<<grid1d(n), 256, 0, st>>>(src, B, C, g.H, g.W, g.P, g.plane, dst);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
 }
 
 }  // namespace di
