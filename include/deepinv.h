@@ -231,6 +231,18 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
 int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float* const db[],
                          const float* dWfc, float lr, float mu, void* stream);
 
+/* Checkpoint / resume of training.  save_state writes the float32 master
+ * weights, their SGD momentum buffers and (with train_fc) the FC weights and
+ * momentum to a binary file under `path` (a header with the network's
+ * description, then the arrays); it synchronises the device.  load_state reads
+ * such a file into a network created with the same description (the precision
+ * may differ), refreshes the kernel layouts and synchronises `stream`; a file
+ * of another network or a truncated file returns DEEPINV_EINVAL and may leave
+ * the network partly updated.  Training resumed from a saved state continues
+ * bit for bit as if it had not stopped. */
+int deepinv_net_save_state(deepinv_net* net, const char* path);
+int deepinv_net_load_state(deepinv_net* net, const char* path, void* stream);
+
 /* Copy the float32 master weights out (any pointer may be NULL to skip it);
  * wfc is [N][M] and is only available when train_fc. */
 int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[], float* wfc,

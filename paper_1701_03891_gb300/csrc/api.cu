@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 
 namespace di {
@@ -178,11 +180,28 @@ int prof_event(deepinv_net* n, cudaStream_t st)
 }
 
 // Marks the start of a stage; its destructor records the end and the span.
+// NVTX range for the duration of a host call (visible to profilers; nearly free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+const char* stage_name(int stage)
+{
+    static const char* names[DEEPINV_NSTAGES] = {"deepinv measure", "deepinv fc", "deepinv conv1", "deepinv conv2",
+                                                "deepinv conv3", "deepinv hidden"};
+    return stage >= 0 && stage < DEEPINV_NSTAGES ? names[stage] : "deepinv";
+}
+
+// Marks a stage: an NVTX range, and with the profiler on, CUDA events whose span
+// the destructor records.
 struct StageTimer {
     deepinv_net* n;
     cudaStream_t st;
     int stage, e0;
-    StageTimer(deepinv_net* n_, cudaStream_t st_, int stage_) : n(n_), st(st_), stage(stage_), e0(-1)
+    NvtxRange range;
+    StageTimer(deepinv_net* n_, cudaStream_t st_, int stage_)
+        : n(n_), st(st_), stage(stage_), e0(-1), range(stage_name(stage_))
     {
         if (n->prof) e0 = prof_event(n, st);
     }
@@ -941,6 +960,52 @@ int host_wait(deepinv_net* net, uint64_t ticket)
     return DEEPINV_OK;
 }
 
+// Training state file: "DINVSTAT", uint32 version, the network's deepinv_net_desc,
+// then per layer (network order) w, its momentum, b, its momentum, then with
+// train_fc the FC weights and their momentum; every array float32, preceded by
+// its element count (uint64).
+const char kStateMagic[8] = {'D', 'I', 'N', 'V', 'S', 'T', 'A', 'T'};
+const uint32_t kStateVersion = 1;
+
+int state_io(deepinv_net* net, FILE* f, bool save)
+{
+    std::vector<float> host;
+    auto one = [&](float* dev, size_t n) -> int {
+        uint64_t cnt = n;
+        if (save) {
+            host.resize(n);
+            DI_CUDA(cudaMemcpy(host.data(), dev, n * 4, cudaMemcpyDeviceToHost));
+            if (fwrite(&cnt, 8, 1, f) != 1 || fwrite(host.data(), 4, n, f) != n) {
+                set_error("state file: write failed");
+                return DEEPINV_EINVAL;
+            }
+        } else {
+            if (fread(&cnt, 8, 1, f) != 1 || cnt != n) {
+                set_error("state file: array of %llu elements where the network has %zu",
+                          (unsigned long long)cnt, n);
+                return DEEPINV_EINVAL;
+            }
+            host.resize(n);
+            if (fread(host.data(), 4, n, f) != n) {
+                set_error("state file: truncated");
+                return DEEPINV_EINVAL;
+            }
+            DI_CUDA(cudaMemcpy(dev, host.data(), n * 4, cudaMemcpyHostToDevice));
+        }
+        return DEEPINV_OK;
+    };
+    for (int l = 0; l < net->L; ++l) {
+        DI_TRY(one(net->w[l], wsize(net, l)));
+        DI_TRY(one(net->vw[l], wsize(net, l)));
+        DI_TRY(one(net->b[l], bsize(net, l)));
+        DI_TRY(one(net->vb[l], bsize(net, l)));
+    }
+    if (net->d.train_fc) {
+        DI_TRY(one(net->wfc, (size_t)net->N * net->d.M));
+        DI_TRY(one(net->vfc, (size_t)net->N * net->d.M));
+    }
+    return DEEPINV_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1200,6 +1265,7 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
         return DEEPINV_EUNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    NvtxRange range("deepinv backward");
     if (!saved) return backward_recompute(net, y, x, B, dW, db, dWfc, loss, st);
     const Saved sv = carve_saved(net, B, static_cast<char*>(const_cast<void*>(saved)));
     return backward_run(net, y, x, B, B, sv, dW, db, dWfc, loss, st);
@@ -1214,6 +1280,7 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float*
     for (int l = 0; l < net->L; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    NvtxRange range("deepinv sgd_momentum");
     // every tensor in one launch (2 L + 1 <= kSgdMaxTensors)
     SgdTensors t{};
     for (int l = 0; l < net->L; ++l) {
@@ -1224,6 +1291,59 @@ int deepinv_sgd_momentum(deepinv_net* net, const float* const dW[], const float*
         t.w[t.count] = net->wfc, t.v[t.count] = net->vfc, t.g[t.count] = dWfc, t.n[t.count++] = (long long)net->N * net->d.M;
     DI_TRY(sgd_momentum_multi(t, lr, mu, st));
     return repack(net, st);
+}
+
+int deepinv_net_save_state(deepinv_net* net, const char* path)
+{
+    DI_REQUIRE(net && path, "null pointer");
+    DeviceGuard dg(net->dev);
+    DI_CUDA(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "wb");
+    DI_REQUIRE(f, "cannot open %s for writing", path);
+    int rc = DEEPINV_OK;
+    if (fwrite(kStateMagic, 1, 8, f) != 8 || fwrite(&kStateVersion, 4, 1, f) != 1 ||
+        fwrite(&net->d, sizeof(net->d), 1, f) != 1) {
+        set_error("state file: write failed");
+        rc = DEEPINV_EINVAL;
+    }
+    if (rc == DEEPINV_OK) rc = state_io(net, f, true);
+    if (fclose(f) != 0 && rc == DEEPINV_OK) {
+        set_error("state file: close failed");
+        rc = DEEPINV_EINVAL;
+    }
+    return rc;
+}
+
+int deepinv_net_load_state(deepinv_net* net, const char* path, void* stream)
+{
+    DI_REQUIRE(net && path, "null pointer");
+    DeviceGuard dg(net->dev);
+    FILE* f = fopen(path, "rb");
+    DI_REQUIRE(f, "cannot open %s", path);
+    char magic[8];
+    uint32_t version = 0;
+    deepinv_net_desc d{};
+    int rc = DEEPINV_OK;
+    if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kStateMagic, 8) != 0 || fread(&version, 4, 1, f) != 1 ||
+        version != kStateVersion || fread(&d, sizeof(d), 1, f) != 1) {
+        set_error("%s is not a version-%u state file", path, kStateVersion);
+        rc = DEEPINV_EINVAL;
+    } else if (d.n1 != net->d.n1 || d.n2 != net->d.n2 || d.M != net->d.M || d.l1 != net->d.l1 ||
+               d.l2 != net->d.l2 || d.l3 != net->d.l3 || d.k != net->d.k || d.hidden != net->d.hidden ||
+               d.train_fc != net->d.train_fc || d.final_relu != net->d.final_relu) {
+        set_error("state file %s was saved from a different network", path);
+        rc = DEEPINV_EINVAL;
+    }
+    if (rc == DEEPINV_OK) {
+        DI_CUDA(cudaDeviceSynchronize());
+        rc = state_io(net, f, false);
+    }
+    fclose(f);
+    if (rc != DEEPINV_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DI_TRY(repack(net, st));
+    DI_CUDA(cudaStreamSynchronize(st));
+    return DEEPINV_OK;
 }
 
 int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[], float* wfc, void* stream)

@@ -89,6 +89,8 @@ SIGNATURES = {
     "deepinv_backward": (_I, [_P, _P, _P, _I, _P, _PP, _PP, _P, _P, _P]),
     "deepinv_sgd_momentum": (_I, [_P, _PP, _PP, _P, ctypes.c_float, ctypes.c_float, _P]),
     "deepinv_get_params": (_I, [_P, _PP, _PP, _P, _P]),
+    "deepinv_net_save_state": (_I, [_P, ctypes.c_char_p]),
+    "deepinv_net_load_state": (_I, [_P, ctypes.c_char_p, _P]),
     "deepinv_serve_open": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
     "deepinv_serve_add_net": (_I, [_P, _P, ctypes.POINTER(_I)]),
     "deepinv_serve": (_I, [_P, ctypes.POINTER(Request), _I, ctypes.POINTER(Result), _I, ctypes.POINTER(_I), _I]),
@@ -344,6 +346,14 @@ class Net:
         cnt = (ctypes.c_int * NSTAGES)()
         _check(lib().deepinv_profile_read(self._h, ms, cnt))
         return {STAGES[i]: (float(ms[i]), int(cnt[i])) for i in range(NSTAGES)}
+
+    def save_state(self, path: str):
+        """Write the training state (masters, momentum, FC) to ``path``."""
+        _check(lib().deepinv_net_save_state(self._h, os.fsencode(path)))
+
+    def load_state(self, path: str, stream=None):
+        """Read a training state saved from a network of the same description."""
+        _check(lib().deepinv_net_load_state(self._h, os.fsencode(path), _stream(stream)))
 
     def get_params(self, stream=None) -> dict:
         import torch
