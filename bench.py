@@ -7,10 +7,14 @@ seeded synthetic piecewise-smooth images standing in for the 64 x 64 ImageNet
 crops of Sec. 5.  One step = sense and recover one batch: y = Phi x, then
 x^ = M(y, Omega), on the bfloat16 tensor-core path (float32 accumulation).
 
-Also reported: the float32 CUDA-core path on the same batch (images/s and the
+Also reported: per-stage and per-step times, the conv2 roofline fraction and
+DRAM traffic, the float32 CUDA-core path on the same batch (images/s and the
 rel-L2 between the two paths), the end-to-end rate through the host-memory
-entry point, the conv2 roofline fraction, the clocks seen during the timed
-region, and the FP64 CPU oracle's rate on a bounded sample of the batch.
+entry points (two batches in flight, and one at a time), continuous-batching
+serving latency, 256 x 256 bf16 and e4m3 recovery, a training step, a
+five-layer network (inference and training), the clocks seen during the timed
+region, and the FP64 CPU oracle's rate on a bounded sample of the batch;
+--eval adds recovery quality of networks trained by the library.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
