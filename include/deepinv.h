@@ -7,13 +7,17 @@
  * y = Phi x in R^M (Sec. 1) with the network of Sec. 4: a fully connected
  * layer fixed to Phi^T (x~ = Phi^T y, reshaped to n1 x n2), then three
  * convolutional layers, Eq. (1), with 64, 32 and 1 filters of 11 x 11
- * (Sec. 5).  It also trains that network on the MSE loss of Sec. 4.
+ * (Sec. 5), optionally with more 32-filter layers before the last (the
+ * deeper networks Sec. 5 leaves to future work).  It also trains that network
+ * on the MSE loss of Sec. 4.
  *
  * Conventions shared by every call:
  *  - Tensor arguments are DEVICE pointers owned by the caller, contiguous,
  *    row-major float32 unless stated otherwise.  Images are stored row-major,
  *    pixel j = r * n2 + c (the reshape of Sec. 4).  The library never frees
- *    caller memory and never keeps a caller pointer after the call returns.
+ *    caller memory and keeps no caller pointer after a call returns, except
+ *    deepinv_sense_recover_host_submit's host buffers until their ticket
+ *    completes.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
  *    call is asynchronous on that stream unless its comment says otherwise.
  *  - Arguments are checked before any launch.  A negative return value is a
