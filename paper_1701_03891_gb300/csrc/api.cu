@@ -179,7 +179,6 @@ int prof_event(deepinv_net* n, cudaStream_t st)
     return i;
 }
 
-// Marks the start of a stage; its destructor records the end and the span.
 // NVTX range for the duration of a host call (visible to profilers; nearly free otherwise).
 struct NvtxRange {
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
@@ -899,32 +898,38 @@ int host_submit(deepinv_net* net, const float* in_host, bool measure, int B, flo
 {
     const int N = net->N, M = net->d.M;
     const size_t in_elems = (size_t)B * (measure ? N : M), out_elems = (size_t)B * N;
-    if (!net->cs_in) {
-        DI_CUDA(cudaStreamCreateWithFlags(&net->cs_in, cudaStreamNonBlocking));
-        DI_CUDA(cudaStreamCreateWithFlags(&net->cs_out, cudaStreamNonBlocking));
-        for (int k = 0; k < 2; ++k)
-            for (cudaEvent_t* e : {&net->ev_h2d[k], &net->ev_read[k], &net->ev_comp[k], &net->ev_d2h[k]})
-                DI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    }
+    // copy streams and slot events, created on first use (each one that is
+    // still missing, so that a failed creation is retried by the next call)
+    if (!net->cs_in) DI_CUDA(cudaStreamCreateWithFlags(&net->cs_in, cudaStreamNonBlocking));
+    if (!net->cs_out) DI_CUDA(cudaStreamCreateWithFlags(&net->cs_out, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t* e : {&net->ev_h2d[k], &net->ev_read[k], &net->ev_comp[k], &net->ev_d2h[k]})
+            if (!*e) DI_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     if (in_elems > net->hin_elems || out_elems > net->hout_elems) {
         // grow the staging slots once nothing in flight uses them
         DI_CUDA(cudaStreamSynchronize(net->cs_in));
         DI_CUDA(cudaStreamSynchronize(st));
         DI_CUDA(cudaStreamSynchronize(net->cs_out));
-        for (int k = 0; k < 2; ++k) {
-            if (in_elems > net->hin_elems) {
+        // (a size is recorded only once both slots hold it, so that a failed
+        // allocation leaves no null slot behind a nonzero size)
+        if (in_elems > net->hin_elems) {
+            net->hin_elems = 0;
+            for (int k = 0; k < 2; ++k) {
                 cudaFree(net->hin[k]);
                 net->hin[k] = nullptr;
-                DI_TRY(dev_alloc(&net->hin[k], in_elems));
             }
-            if (out_elems > net->hout_elems) {
+            for (int k = 0; k < 2; ++k) DI_TRY(dev_alloc(&net->hin[k], in_elems));
+            net->hin_elems = in_elems;
+        }
+        if (out_elems > net->hout_elems) {
+            net->hout_elems = 0;
+            for (int k = 0; k < 2; ++k) {
                 cudaFree(net->hout[k]);
                 net->hout[k] = nullptr;
-                DI_TRY(dev_alloc(&net->hout[k], out_elems));
             }
+            for (int k = 0; k < 2; ++k) DI_TRY(dev_alloc(&net->hout[k], out_elems));
+            net->hout_elems = out_elems;
         }
-        if (in_elems > net->hin_elems) net->hin_elems = in_elems;
-        if (out_elems > net->hout_elems) net->hout_elems = out_elems;
     }
     DI_TRY(ensure_ws(net, B, st));
     const FwdWs w = carve_fwd(net, net->ws_B, net->ws);
@@ -1139,7 +1144,7 @@ int deepinv_net_create(const deepinv_net_desc* desc, const float* phi, const flo
         }
         if (n->fp8) {
             DI_STEP(dev_alloc(&n->w2q, kW2E4M3Bytes));
-            DI_STEP(dev_alloc(&n->sw, 32 * 4 + 1 + 1 + 32));   // sw | oscale | inv_sa | amax_a1 | amax_w
+            DI_STEP(dev_alloc(&n->sw, 32 + 32 + 1 + 1 + 32));   // sw | oscale | inv_sa | amax_a1 | amax_w
             n->oscale = n->sw + 32;
             n->inv_sa = n->sw + 64;
             n->amax_a1 = n->sw + 65;

@@ -144,7 +144,6 @@ Lease* acquire(deepinv_server* s, int net, cudaStream_t st)
 
 void finish_slot(deepinv_server* s, Slot& sl, int status)
 {
-    const auto now = Clock::now();
     const int N = net_N(s->nets[sl.net]);
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
         Req& r = sl.reqs[i];
@@ -161,7 +160,6 @@ void finish_slot(deepinv_server* s, Slot& sl, int status)
         else s->stats.failed++;
         s->outstanding--;
     }
-    (void)now;
     sl.reqs.clear();
     s->cache[sl.net].push_back(sl.lease);
     sl.lease = nullptr;
@@ -252,7 +250,8 @@ void scheduler(deepinv_server* s)
                 continue;
             }
             s->waiting_admission = false;
-            launch(s, sl, best, l);
+            // a batch that failed to launch has already queued its failed results
+            if (launch(s, sl, best, l) != DEEPINV_OK) s->cv_done.notify_all();
             progressed = true;
         }
         bool any_busy = false, any_pending = false;

@@ -139,10 +139,42 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _need_f32_cuda(t, name):
+# The library cannot see the extent of a buffer it is handed, so the binding
+# checks every tensor's kind and size before the call: a short buffer would
+# otherwise be read or written past its end.
+def _need_f32_cuda(t, name, numel=None):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise DeepInvError(EINVAL, "%s must be a contiguous float32 CUDA tensor" % name)
+    if numel is not None and t.numel() != numel:
+        raise DeepInvError(EINVAL, "%s has %d elements, expected %d" % (name, t.numel(), numel))
+
+
+def _need_f32_host(t, name, numel):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise DeepInvError(EINVAL, "%s must be a contiguous float32 CPU tensor" % name)
+    if t.numel() != numel:
+        raise DeepInvError(EINVAL, "%s has %d elements, expected %d" % (name, t.numel(), numel))
+
+
+def _batch(t, name, cols):
+    """Rows B of a tensor holding B rows of `cols` values ([B][cols] or any
+    shape with B leading and cols values per row)."""
+    B = t.shape[0] if t.dim() >= 1 else 0
+    if t.numel() != B * cols:
+        raise DeepInvError(EINVAL, "%s: %d elements are not %d rows of %d" % (name, t.numel(), B, cols))
+    return B
+
+
+def _need_cuda_bytes(t, name, nbytes):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise DeepInvError(EINVAL, "%s must be a contiguous CUDA tensor" % name)
+    if t.numel() * t.element_size() < nbytes:
+        raise DeepInvError(EINVAL, "%s holds %d bytes, the call needs %d"
+                           % (name, t.numel() * t.element_size(), nbytes))
 
 
 def _arr(ptrs):
@@ -166,8 +198,9 @@ def measure(phi, x, prec="f32", out=None, stream=None):
     _need_f32_cuda(phi, "phi")
     _need_f32_cuda(x, "x")
     M, N = phi.shape
-    B = x.shape[0]
+    B = _batch(x, "x", N)
     y = out if out is not None else torch.empty((B, M), device=x.device, dtype=torch.float32)
+    _need_f32_cuda(y, "out", B * M)
     _check(lib().deepinv_measure(_ptr(phi), M, N, _ptr(x), B, _ptr(y), PRECISIONS.get(prec, prec),
                                  _stream(stream)))
     return y
@@ -179,9 +212,10 @@ def measure_noalloc(phi, x, out, stream=None):
     ``out`` [B][M] must be supplied by the caller."""
     _need_f32_cuda(phi, "phi")
     _need_f32_cuda(x, "x")
-    _need_f32_cuda(out, "out")
     M, N = phi.shape
-    _check(lib().deepinv_measure_noalloc(_ptr(phi), M, N, _ptr(x), x.shape[0], _ptr(out), _stream(stream)))
+    B = _batch(x, "x", N)
+    _need_f32_cuda(out, "out", B * M)
+    _check(lib().deepinv_measure_noalloc(_ptr(phi), M, N, _ptr(x), B, _ptr(out), _stream(stream)))
     return out
 
 
@@ -205,13 +239,28 @@ class Net:
         dev = torch.device(device)
         t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(dev).contiguous()
         phi_t = t(phi)
+        if phi_t.dim() != 2 or phi_t.shape[1] != n1 * n2:
+            raise DeepInvError(EINVAL, "phi must be M x (n1*n2), got %s" % (tuple(phi_t.shape),))
         M, N = phi_t.shape
-        assert N == n1 * n2, "phi must be M x (n1*n2)"
         L = num_layers(params)
         if L < 3:
             raise DeepInvError(EINVAL, "params need w1..wL, b1..bL with L >= 3")
         ws = [t(params["w%d" % i]) for i in range(1, L + 1)]
         bs = [t(params["b%d" % i]) for i in range(1, L + 1)]
+        # layer l maps cin -> cout channels with k x k kernels: w [cout][cin][k][k],
+        # b [cout]; the hidden layers (between the second and the last) keep the
+        # second layer's channel count
+        k = ws[0].shape[-1]
+        cin = 1
+        for i, (w, b) in enumerate(zip(ws, bs)):
+            cout = w.shape[0] if w.dim() == 4 else -1
+            if 2 <= i < L - 1 and cout != ws[1].shape[0]:
+                raise DeepInvError(EINVAL, "hidden layer %d has %d filters, the second layer %d"
+                                   % (i + 1, cout, ws[1].shape[0]))
+            if tuple(w.shape) != (cout, cin, k, k) or tuple(b.shape) != (cout,):
+                raise DeepInvError(EINVAL, "layer %d: w %s and b %s, expected w [cout][%d][%d][%d] and b [cout]"
+                                   % (i + 1, tuple(w.shape), tuple(b.shape), cin, k, k))
+            cin = cout
         self.L = L
         self.desc = NetDesc(n1, n2, M, ws[0].shape[0], ws[1].shape[0], ws[-1].shape[0], ws[0].shape[-1],
                             int(final_relu), int(train_fc), PRECISIONS.get(prec, prec), L - 3)
@@ -243,7 +292,7 @@ class Net:
     def calibrate(self, y, stream=None):
         """Fix the e4m3 activation scale from a calibration batch y [B][M] (no-op otherwise)."""
         _need_f32_cuda(y, "y")
-        _check(lib().deepinv_net_calibrate(self._h, _ptr(y), y.shape[0], _stream(stream)))
+        _check(lib().deepinv_net_calibrate(self._h, _ptr(y), _batch(y, "y", self.M), _stream(stream)))
 
     def reserve(self, max_B: int, stream=None):
         _check(lib().deepinv_net_reserve(self._h, max_B, _stream(stream)))
@@ -251,8 +300,9 @@ class Net:
     def measure(self, x, out=None, stream=None):
         import torch
         _need_f32_cuda(x, "x")
-        B = x.shape[0]
+        B = _batch(x, "x", self.N)
         y = out if out is not None else torch.empty((B, self.M), device=x.device, dtype=torch.float32)
+        _need_f32_cuda(y, "out", B * self.M)
         _check(lib().deepinv_net_measure(self._h, _ptr(x), B, _ptr(y), _stream(stream)))
         return y
 
@@ -263,8 +313,11 @@ class Net:
         """x^ = M(y, Omega).  y [B][M] -> x^ [B][N]."""
         import torch
         _need_f32_cuda(y, "y")
-        B = y.shape[0]
+        B = _batch(y, "y", self.M)
         xh = out if out is not None else torch.empty((B, self.N), device=y.device, dtype=torch.float32)
+        _need_f32_cuda(xh, "out", B * self.N)
+        if saved is not None:
+            _need_cuda_bytes(saved, "saved", self.saved_bytes(B))
         _check(lib().deepinv_forward(self._h, _ptr(y), B, _ptr(xh), _ptr(saved), _stream(stream)))
         return xh
 
@@ -273,15 +326,19 @@ class Net:
     def forward_host(self, y_host, out_host=None, stream=None):
         """End to end from host memory (pinned for async copies); returns a CPU tensor."""
         import torch
-        B = y_host.shape[0]
+        _need_f32_host(y_host, "y_host", y_host.numel())
+        B = _batch(y_host, "y_host", self.M)
         xh = out_host if out_host is not None else torch.empty((B, self.N), dtype=torch.float32)
+        _need_f32_host(xh, "out_host", B * self.N)
         _check(lib().deepinv_forward_host(self._h, y_host.data_ptr(), B, xh.data_ptr(), _stream(stream)))
         return xh
 
     def sense_recover_host(self, x_host, out_host=None, stream=None):
         import torch
-        B = x_host.shape[0]
+        _need_f32_host(x_host, "x_host", x_host.numel())
+        B = _batch(x_host, "x_host", self.N)
         xh = out_host if out_host is not None else torch.empty((B, self.N), dtype=torch.float32)
+        _need_f32_host(xh, "out_host", B * self.N)
         _check(lib().deepinv_sense_recover_host(self._h, x_host.data_ptr(), B, xh.data_ptr(),
                                                 _stream(stream)))
         return xh
@@ -290,8 +347,11 @@ class Net:
         """Queue sense + recover of a pinned host batch x [B][N] into the pinned
         out_host [B][N] and return a ticket (two batches' copies and compute
         overlap); keep both buffers alive until host_wait(ticket)."""
+        _need_f32_host(x_host, "x_host", x_host.numel())
+        B = _batch(x_host, "x_host", self.N)
+        _need_f32_host(out_host, "out_host", B * self.N)
         t = ctypes.c_uint64()
-        _check(lib().deepinv_sense_recover_host_submit(self._h, x_host.data_ptr(), x_host.shape[0],
+        _check(lib().deepinv_sense_recover_host_submit(self._h, x_host.data_ptr(), B,
                                                        out_host.data_ptr(), _stream(stream), ctypes.byref(t)))
         return t.value
 
@@ -301,6 +361,16 @@ class Net:
     def new_saved(self, B: int):
         import torch
         return torch.empty(self.saved_bytes(B), dtype=torch.uint8, device=self.device)
+
+    def _check_grads(self, dW, db, dWfc):
+        if len(dW) != self.L or len(db) != self.L:
+            raise DeepInvError(EINVAL, "need %d weight and bias gradients, got %d and %d"
+                               % (self.L, len(dW), len(db)))
+        for i, s in enumerate(self.shapes):
+            _need_f32_cuda(dW[i], "dW[%d]" % i, s[0] * s[1] * s[2] * s[3])
+            _need_f32_cuda(db[i], "db[%d]" % i, s[0])
+        if self.desc.train_fc:
+            _need_f32_cuda(dWfc, "dWfc", self.N * self.M)
 
     def grad_buffers(self):
         import torch
@@ -321,8 +391,12 @@ class Net:
         import torch
         _need_f32_cuda(y, "y")
         _need_f32_cuda(x, "x")
-        B = y.shape[0]
+        B = _batch(y, "y", self.M)
+        _need_f32_cuda(x, "x", B * self.N)
+        if saved is not None:
+            _need_cuda_bytes(saved, "saved", self.saved_bytes(B))
         dW, db, dWfc = grads if grads is not None else self.grad_buffers()
+        self._check_grads(dW, db, dWfc)
         loss = torch.empty((), device=self.device, dtype=torch.float64)
         wp, _k1 = _arr([t.data_ptr() for t in dW])
         bp, _k2 = _arr([t.data_ptr() for t in db])
@@ -331,6 +405,7 @@ class Net:
         return loss, dW, db, dWfc
 
     def sgd_momentum(self, dW, db, dWfc=None, lr=1e-3, mu=0.9, stream=None):
+        self._check_grads(dW, db, dWfc)
         wp, _k1 = _arr([t.data_ptr() for t in dW])
         bp, _k2 = _arr([t.data_ptr() for t in db])
         _check(lib().deepinv_sgd_momentum(self._h, wp, bp, _ptr(dWfc), float(lr), float(mu),
@@ -415,6 +490,19 @@ def mse_loss(net: Net, y, x, params):
     return _autograd_cls.apply(net, y, x, *params)
 
 
+def _need_host_vec(a, name, n):
+    """A float32 host array (numpy or CPU tensor) of exactly n contiguous values."""
+    import numpy as np
+    import torch
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.size == n
+    else:
+        ok = (isinstance(a, torch.Tensor) and a.device.type == "cpu" and a.dtype == torch.float32
+              and a.is_contiguous() and a.numel() == n)
+    if not ok:
+        raise DeepInvError(EINVAL, "%s must be %d contiguous float32 values in host memory" % (name, n))
+
+
 class Server:
     """Continuous-batching recovery server (deepinv_serve_*): host y in, host x^ out."""
 
@@ -435,6 +523,9 @@ class Server:
         n_in = len(requests)
         arr = (Request * max(1, n_in))()
         for i, (nid, y, xh, tag) in enumerate(requests):
+            if 0 <= nid < len(self.nets):   # (an unknown net_id is the library's to reject)
+                _need_host_vec(y, "request %d: y" % i, self.nets[nid].M)
+                _need_host_vec(xh, "request %d: xhat" % i, self.nets[nid].N)
             arr[i] = Request(nid, y.ctypes.data if hasattr(y, "ctypes") else y.data_ptr(),
                              xh.ctypes.data if hasattr(xh, "ctypes") else xh.data_ptr(), tag)
         out = (Result * max(1, max_out))()

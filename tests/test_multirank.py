@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
 def test_bench_aggregation_world_size_2():
     import torch.multiprocessing as mp
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a threaded test process
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0][0] == out[1][0] == 20.0                       # max over ranks
