@@ -21,8 +21,9 @@
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
  *    call is asynchronous on that stream unless its comment says otherwise.
  *  - Arguments are checked before any launch.  A negative return value is a
- *    deepinv_status; the outputs are then untouched and deepinv_last_error()
- *    returns a message for the calling thread.
+ *    deepinv_status and deepinv_last_error() returns a message for the calling
+ *    thread; after DEEPINV_EINVAL or DEEPINV_EUNSUPPORTED the outputs are
+ *    untouched, after DEEPINV_ECUDA their contents are undefined.
  *  - No call aborts the process or traps the GPU.  Waits inside kernels are
  *    bounded; a wait that runs out makes the call report DEEPINV_ETIMEOUT
  *    through deepinv_device_status().
@@ -51,7 +52,7 @@ typedef enum {
     DEEPINV_ECUDA = -3,        /* a CUDA runtime call failed (message in deepinv_last_error) */
     DEEPINV_EUNSUPPORTED = -4, /* valid request this build has no kernel for */
     DEEPINV_ETIMEOUT = -5,     /* a bounded wait ran out (in a kernel or in the server) */
-    DEEPINV_EBUSY = -6         /* admission refused: the request does not fit the budget now */
+    DEEPINV_EBUSY = -6         /* the server has requests in flight (deepinv_serve_add_net) */
 } deepinv_status;
 
 typedef enum {
@@ -62,7 +63,8 @@ typedef enum {
 
 /* Network shape (Sec. 4 and Sec. 5).  The paper's network is
  * l1 = 64, l2 = 32, l3 = 1, k = 11; the BF16 path requires exactly that,
- * the F32 path accepts any l1, l2, l3 >= 1 and odd k <= 15. */
+ * the F32 path accepts any l1, l2 >= 1 and odd k <= 15 (l3 = 1 always: the
+ * output is the one-channel image). */
 typedef struct {
     int n1, n2;      /* image rows and columns, N = n1 * n2 */
     int M;           /* number of measurements, 1 <= M <= N */
@@ -263,8 +265,9 @@ int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[
  * next batch.  Each batch needs a workspace of that network for max_batch
  * images; workspaces are kept for reuse and count against the HBM budget,
  * idle ones of other networks are released when a new one does not fit, and
- * a batch waits while its workspace does not fit.  Results do not depend on
- * the batch a request ran in. */
+ * a batch waits while its workspace does not fit; requests of a network whose
+ * workspace exceeds the whole budget finish with status DEEPINV_ENOMEM.
+ * Results do not depend on the batch a request ran in. */
 typedef struct deepinv_server deepinv_server;  /* opaque */
 
 typedef struct {
