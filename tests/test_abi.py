@@ -90,3 +90,60 @@ def test_bad_descriptions_rejected_on_host(L):
 
 def test_saved_bytes_null_net(L):
     assert L.deepinv_saved_bytes(None, 4) == 0
+
+
+def _declarations():
+    """name -> (return type, [parameter declarations]) of every deepinv_* function in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^([A-Za-z_][\w\s\*]*?)\s*\b(deepinv_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.M | re.S):
+            ret, name, params = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+            out[name] = (ret, [] if params in ("", "void") else [p.strip() for p in params.split(",")])
+    return out
+
+
+def test_binding_signatures_match_header():
+    """Each ctypes prototype has the header's return type, parameter count and,
+    per parameter, the same scalar type or a pointer where the header has one
+    (a mismatch would pass arguments in the wrong registers or widths)."""
+    from paper_1701_03891_gb300 import deepinv
+    ret_types = {"int": ctypes.c_int, "size_t": ctypes.c_size_t, "const char*": ctypes.c_char_p,
+                 "const char *": ctypes.c_char_p}
+    scalars = {"int": ctypes.c_int, "float": ctypes.c_float, "double": ctypes.c_double,
+               "size_t": ctypes.c_size_t, "uint64_t": ctypes.c_uint64}
+    decl = _declarations()
+    assert decl.keys() == _declared()
+    for name, (ret, params) in decl.items():
+        res, args = deepinv.SIGNATURES[name]
+        assert len(args) == len(params), (name, len(args), len(params))
+        assert res is ret_types[ret], (name, ret)
+        for p, a in zip(params, args):
+            if "*" in p or "[" in p:
+                assert a in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(a, ctypes._Pointer), (name, p, a)
+            else:
+                ctype = " ".join(p.replace("const ", "").split()[:-1])
+                assert a is scalars[ctype], (name, p, a)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof and every field's offset of the structs shared with C, compiled
+    from include/deepinv.h by gcc, equal the ctypes mirrors'."""
+    from paper_1701_03891_gb300 import deepinv
+    structs = {"deepinv_net_desc": deepinv.NetDesc, "deepinv_request": deepinv.Request,
+               "deepinv_result": deepinv.Result, "deepinv_serve_stats": deepinv.ServeStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "deepinv.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {k: int(v) for k, v in (line.rsplit(" ", 1) for line in out.splitlines())}
+    for cname, cls in structs.items():
+        assert got[cname] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[cname + "." + f] == getattr(cls, f).offset, (cname, f)
