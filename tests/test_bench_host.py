@@ -1,0 +1,68 @@
+"""Host-side logic of bench.py's roofline object, on the CPU: the peak
+denominators come from the measured-peaks file when it exists (else the stated
+fallback), and the ncu DRAM traffic recorded under profiles/ is reported only
+while conv2's source is the code it was measured on."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_peaks_measured_then_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(
+        {"hbm_gbs": 7000.5, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1750.0}))
+    assert bench.peaks() == dict(hbm=7000.5, bf16=2000.0, bf16_sust=1750.0, src="measured")
+
+
+def test_traffic_only_for_the_measured_conv2_source(tmp_path, monkeypatch):
+    h = bench.conv2_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0 and h == bench.conv2_source_hash()
+    (tmp_path / "profiles").mkdir()
+    rec = tmp_path / "profiles" / "conv2_traffic.json"
+    rec.write_text(json.dumps({"kernel_sha": h, "dram_bytes_per_image": 123456.0}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "conv2_source_hash", lambda: h)
+    assert bench.traffic_record() == 123456.0
+    rec.write_text(json.dumps({"kernel_sha": "0" * 16, "dram_bytes_per_image": 123456.0}))
+    assert bench.traffic_record() is None          # conv2 changed since the counters were taken
+    rec.unlink()
+    assert bench.traffic_record() is None
+
+
+def test_conv2_hash_follows_the_conv2_source(tmp_path, monkeypatch):
+    """An edit inside tc_kernels.cu's conv2 section or in a header it includes
+    changes the hash; an edit elsewhere in tc_kernels.cu does not."""
+    import shutil
+    csrc = tmp_path / "paper_1701_03891_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    real = os.path.join(ROOT, "paper_1701_03891_gb300", "csrc")
+    for name in bench.CONV2_SOURCES:
+        shutil.copy(os.path.join(real, name), csrc / name)
+    h = bench.conv2_source_hash()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.conv2_source_hash() == h
+    tk = csrc / "tc_kernels.cu"
+    text = tk.read_text()
+    i, j = text.index(bench.CONV2_BEGIN), text.index(bench.CONV2_END)
+    assert text.count(bench.CONV2_BEGIN) == 1 and i < j
+    tk.write_text(text + "\n// an edit outside the conv2 section\n")
+    assert bench.conv2_source_hash() == h
+    mid = (i + j) // 2
+    tk.write_text(text[:mid] + " " + text[mid:])
+    assert bench.conv2_source_hash() != h
+    tk.write_text(text)
+    for name in bench.CONV2_SOURCES:
+        if name != "tc_kernels.cu":
+            hdr = csrc / name
+            orig = hdr.read_text()
+            hdr.write_text(orig + "\n")
+            assert bench.conv2_source_hash() != h, name
+            hdr.write_text(orig)
+    assert bench.conv2_source_hash() == h
