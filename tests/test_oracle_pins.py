@@ -54,6 +54,34 @@ def test_fc_is_adjoint_of_measure(orc):
     np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
 
 
+# ------------------------------------------------------------------ whole network, by hand (Sec. 4)
+def test_tiny_network_forward_loss_and_gradients_by_hand(orc):
+    """A two-pixel network with 1 x 1 kernels, two images (one pixel masked by
+    conv1's ReLU), worked by hand: forward, loss and every gradient, FC
+    included, exactly.  A missing 1/B, a missing or misplaced ReLU mask or a
+    sign slip each changes one of these numbers."""
+    g = _golden("tiny_net_hand.json")
+    n1, n2 = g["n1"], g["n2"]
+    phi, x = np.array(g["phi"], float), np.array(g["x"], float)
+    params = {}
+    for l in (1, 2, 3):
+        params["w%d" % l] = np.full((1, 1, 1, 1), float(g["w%d" % l]))
+        params["b%d" % l] = np.array([float(g["b%d" % l])])
+    y = orc.measure(phi, x)
+    assert np.array_equal(y, np.array(g["y"], float))
+    xhat, c = orc.forward(y, params, n1, n2, phi=phi, keep=True)
+    assert np.array_equal(c["xt"], np.array(g["xt"], float))
+    assert np.array_equal(c["z1"].reshape(2, -1), np.array(g["z1"], float))
+    assert np.array_equal(c["z2"].reshape(2, -1), np.array(g["z2"], float))
+    assert np.array_equal(xhat, np.array(g["xhat"], float))
+    assert orc.mse_loss(xhat, x) == g["loss"]
+    loss, grads = orc.backward(y, x, params, n1, n2, phi=phi, train_fc=True)
+    assert loss == g["loss"]
+    assert np.shape(grads["wfc"]) == (n1 * n2, phi.shape[0])        # [N][M]
+    for name, want in g["grads"].items():
+        assert np.array_equal(np.asarray(grads[name], float).reshape(np.shape(want)), np.array(want, float)), name
+
+
 # ------------------------------------------------------------------ Eq. (1)
 def test_conv_hand_example(orc):
     g = _golden("conv_3x3_hand.json")
