@@ -13,7 +13,8 @@ rel-L2 between the two paths), the end-to-end rate through the host-memory
 entry points (two batches in flight, and one at a time), continuous-batching
 serving latency, 256 x 256 bf16 and e4m3 recovery, a training step, a
 five-layer network (inference and training), the clocks seen during the timed
-region, and the FP64 CPU oracle's rate on a bounded sample of the batch;
+region, and the FP64 CPU oracle's rate on a bounded sample of the batch (with
+the host's thread count and CPU model);
 --eval adds recovery quality of networks trained by the library.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
@@ -160,6 +161,26 @@ def config(args, n, M, world):
             "l2": "flushed (%d MiB write) before every timed step, outside its events" % (L2_FLUSH_BYTES >> 20)}
 
 
+def host_cpu():
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of the batch."""
     import numpy as np
@@ -176,8 +197,8 @@ def cpu_baseline(args, phi, params, x, n, gpu_xhat=None):
             dps.append(np.abs(oracle.psnr(gpu_xhat[done:done + chunk], xs) - oracle.psnr(ref, xs)))
         done += xs.shape[0]
     dt = time.perf_counter() - t0
-    out = {"value": done / dt, "unit": "images/s", "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": "%d of the %d batch images (FP64 oracle, OpenMP over output channels, %.1f s)"
+    out = {"value": done / dt, "unit": "images/s", "cores": oracle.num_threads(), "cpu": host_cpu(),
+           "kind": "oracle", "sample": "%d of the %d batch images (FP64 oracle, OpenMP over output channels, %.1f s)"
                      % (done, x.shape[0], dt)}
     if errs:
         out["bf16_vs_oracle_max_rel_l2"] = float(np.max(np.concatenate(errs)))
@@ -514,8 +535,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Voronoi images standing in for ImageNet 64x64 crops)",
             "config": cfg,
-            "cpu_baseline": {"value": val, "unit": "images/s", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "one image of the batch per step, %d steps" % args.steps},
+            "cpu_baseline": {"value": val, "unit": "images/s", "cores": oracle.num_threads(), "cpu": host_cpu(),
+                             "kind": "oracle", "sample": "one image of the batch per step, %d steps" % args.steps},
             "e2e": {"value": val, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -66,3 +66,8 @@ def test_conv2_hash_follows_the_conv2_source(tmp_path, monkeypatch):
             assert bench.conv2_source_hash() != h, name
             hdr.write_text(orig)
     assert bench.conv2_source_hash() == h
+
+
+def test_host_cpu_names_the_model():
+    name = bench.host_cpu()
+    assert isinstance(name, str) and name and "\n" not in name
