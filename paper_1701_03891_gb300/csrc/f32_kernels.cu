@@ -75,9 +75,14 @@ int sgemm(int Mr, int Nc, int K, const float* A, long long sam, long long sak, c
           long long sbk, long long sbn, float* C, long long ldc, cudaStream_t st)
 {
     if (Mr <= 0 || Nc <= 0) return DEEPINV_OK;
-    dim3 grid(cdiv(Nc, GBN), cdiv(Mr, GBM));
-    sgemm_kernel<<<grid, 256, 0, st>>>(Mr, Nc, K, A, sam, sak, B, sbk, sbn, C, ldc);
-    DI_LAUNCH_CHECK();
+    // gridDim.y is at most 65535 row tiles: taller problems run in row chunks
+    constexpr int kRowsPerLaunch = 65535 * GBM;
+    for (long long r0 = 0; r0 < Mr; r0 += kRowsPerLaunch) {
+        const int mr = (int)(Mr - r0 < kRowsPerLaunch ? Mr - r0 : kRowsPerLaunch);
+        dim3 grid(cdiv(Nc, GBN), cdiv(mr, GBM));
+        sgemm_kernel<<<grid, 256, 0, st>>>(mr, Nc, K, A + r0 * sam, sam, sak, B, sbk, sbn, C + r0 * ldc, ldc);
+        DI_LAUNCH_CHECK();
+    }
     return DEEPINV_OK;
 }
 
@@ -169,10 +174,20 @@ int conv_f32(const float* in, int B, int Cin, int H, int W, const float* w, cons
              int Cout, int k, float* out, int relu, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
-    dim3 grid(cdiv(H, CTR) * cdiv(W, CTC), cdiv(Cout, CCO), B);
-    switch (k) {
+    if (k < 1 || k > 15 || k % 2 == 0) {
+        set_error("conv_f32: unsupported kernel size %d", k);
+        return DEEPINV_EUNSUPPORTED;
+    }
+    // gridDim.z (one image per z) is at most 65535: larger batches run in chunks
+    constexpr int kImagesPerLaunch = 65535;
+    for (long long b0 = 0; b0 < B; b0 += kImagesPerLaunch) {
+        const int nb = (int)(B - b0 < kImagesPerLaunch ? B - b0 : kImagesPerLaunch);
+        const float* inb = in + (size_t)b0 * Cin * H * W;
+        float* outb = out + (size_t)b0 * Cout * H * W;
+        dim3 grid(cdiv(H, CTR) * cdiv(W, CTC), cdiv(Cout, CCO), nb);
+        switch (k) {
 #define DI_CONV_CASE(KS) \
-    case KS: conv_f32_kernel<KS><<<grid, 128, 0, st>>>(in, Cin, H, W, w, bias, Cout, out, relu); break;
+    case KS: conv_f32_kernel<KS><<<grid, 128, 0, st>>>(inb, Cin, H, W, w, bias, Cout, outb, relu); break;
         DI_CONV_CASE(1)
         DI_CONV_CASE(3)
         DI_CONV_CASE(5)
@@ -182,11 +197,9 @@ int conv_f32(const float* in, int B, int Cin, int H, int W, const float* w, cons
         DI_CONV_CASE(13)
         DI_CONV_CASE(15)
 #undef DI_CONV_CASE
-        default:
-            set_error("conv_f32: unsupported kernel size %d", k);
-            return DEEPINV_EUNSUPPORTED;
+        }
+        DI_LAUNCH_CHECK();
     }
-    DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
 
