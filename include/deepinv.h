@@ -106,7 +106,8 @@ int deepinv_selftest_bounded_wait(void* stream);
 /* y = Phi x for B signals (Sec. 1).
  * phi [M][N], x [B][N] -> y [B][M], all float32 device memory.
  * prec selects float32 CUDA-core products or bfloat16 tensor-core products
- * with float32 accumulation.  B >= 0 (B == 0 is a no-op). */
+ * with float32 accumulation.  1 <= M, N <= 2^30 and 0 <= B <= 2^30 (B == 0 is
+ * a no-op); other sizes return DEEPINV_EINVAL. */
 int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y,
                     int prec, void* stream);
 

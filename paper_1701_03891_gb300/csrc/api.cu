@@ -1055,7 +1055,9 @@ int deepinv_selftest_bounded_wait(void* stream)
 
 int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float* y, int prec, void* stream)
 {
-    DI_REQUIRE(M >= 1 && N >= 1 && B >= 0, "bad sizes M=%d N=%d B=%d", M, N, B);
+    // (sizes up to 2^30, so that padded extents stay within int)
+    DI_REQUIRE(M >= 1 && N >= 1 && B >= 0 && M <= (1 << 30) && N <= (1 << 30) && B <= (1 << 30),
+               "bad sizes M=%d N=%d B=%d", M, N, B);
     DI_REQUIRE(B == 0 || (phi && x && y), "null pointer");
     DI_REQUIRE(prec == DEEPINV_F32 || prec == DEEPINV_BF16, "unknown precision %d", prec);
     if (B == 0) return DEEPINV_OK;

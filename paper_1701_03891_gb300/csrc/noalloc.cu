@@ -68,7 +68,9 @@ using namespace di;
 extern "C" int deepinv_measure_noalloc(const float* phi, int M, int N, const float* x, int B, float* y,
                                        void* stream)
 {
-    DI_REQUIRE(M >= 1 && N >= 1 && B >= 0, "bad sizes M=%d N=%d B=%d", M, N, B);
+    // (sizes up to 2^30, so that padded extents stay within int)
+    DI_REQUIRE(M >= 1 && N >= 1 && B >= 0 && M <= (1 << 30) && N <= (1 << 30) && B <= (1 << 30),
+               "bad sizes M=%d N=%d B=%d", M, N, B);
     DI_REQUIRE(B == 0 || (phi && x && y), "null pointer");
     if (B == 0) return DEEPINV_OK;
     const int Kp = up16(N), NB = nb_for(M);

@@ -147,3 +147,13 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[cname] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[cname + "." + f] == getattr(cls, f).offset, (cname, f)
+
+
+def test_measure_sizes_beyond_2_30_rejected_on_host(L):
+    from paper_1701_03891_gb300 import deepinv
+    p = ctypes.c_void_p(16)
+    for M, N, B in ((1 << 30, (1 << 30) + 1, 1), ((1 << 30) + 1, 1 << 30, 1), (4, 8, (1 << 30) + 1),
+                    (2147483647, 2147483647, 1)):
+        assert L.deepinv_measure(p, M, N, p, B, p, 0, None) == deepinv.EINVAL, (M, N, B)
+        assert L.deepinv_measure_noalloc(p, M, N, p, B, p, None) == deepinv.EINVAL, (M, N, B)
+        assert b"bad sizes" in L.deepinv_last_error()
