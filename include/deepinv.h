@@ -20,7 +20,8 @@
  *    completes.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
  *    call is asynchronous on that stream unless its comment says otherwise.
- *  - Arguments are checked before any launch.  A negative return value is a
+ *  - Arguments are checked before any launch; a batch B is at most 2^30
+ *    images.  A negative return value is a
  *    deepinv_status and deepinv_last_error() returns a message for the calling
  *    thread; after DEEPINV_EINVAL or DEEPINV_EUNSUPPORTED the outputs are
  *    untouched, after DEEPINV_ECUDA their contents are undefined.

@@ -51,6 +51,9 @@ static int num_sms_current()
     return n > 0 ? n : 1;
 }
 
+// Largest batch a call accepts (padded batch extents stay within int).
+constexpr int kMaxBatch = 1 << 30;
+
 // Round up to a multiple of 16 (the K granularity of one bf16 MMA).
 static inline int up16(int x) { return (x + 15) / 16 * 16; }
 
@@ -1182,7 +1185,7 @@ int deepinv_net_reserve(deepinv_net* net, int max_B, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(max_B >= 0, "bad batch %d", max_B);
+    DI_REQUIRE(max_B >= 0 && max_B <= kMaxBatch, "bad batch %d", max_B);
     if (max_B == 0) return DEEPINV_OK;
     return ensure_ws(net, max_B, static_cast<cudaStream_t>(stream));
 }
@@ -1191,7 +1194,7 @@ int deepinv_net_measure(deepinv_net* net, const float* x, int B, float* y, void*
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B >= 0 && B <= kMaxBatch, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (x && y), "null pointer");
     return net_measure_impl(net, x, B, y, static_cast<cudaStream_t>(stream));
 }
@@ -1206,7 +1209,7 @@ int deepinv_forward(deepinv_net* net, const float* y, int B, float* xhat, void* 
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B >= 0 && B <= kMaxBatch, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (y && xhat), "null pointer");
     return forward_impl(net, y, B, xhat, saved, static_cast<cudaStream_t>(stream));
 }
@@ -1215,7 +1218,7 @@ int deepinv_forward_host(deepinv_net* net, const float* y_host, int B, float* xh
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B >= 0 && B <= kMaxBatch, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (y_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
     uint64_t t = 0;
@@ -1227,7 +1230,7 @@ int deepinv_sense_recover_host(deepinv_net* net, const float* x_host, int B, flo
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 0, "bad batch %d", B);
+    DI_REQUIRE(B >= 0 && B <= kMaxBatch, "bad batch %d", B);
     DI_REQUIRE(B == 0 || (x_host && xhat_host), "null pointer");
     if (B == 0) return DEEPINV_OK;
     uint64_t t = 0;
@@ -1240,7 +1243,7 @@ int deepinv_sense_recover_host_submit(deepinv_net* net, const float* x_host, int
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 1 && x_host && xhat_host && ticket, "bad batch %d or null pointer", B);
+    DI_REQUIRE(B >= 1 && B <= kMaxBatch && x_host && xhat_host && ticket, "bad batch %d or null pointer", B);
     return host_submit(net, x_host, true, B, xhat_host, static_cast<cudaStream_t>(stream), ticket);
 }
 
@@ -1263,7 +1266,7 @@ int deepinv_backward(deepinv_net* net, const float* y, const float* x, int B, co
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 1, "bad batch %d", B);
+    DI_REQUIRE(B >= 1 && B <= kMaxBatch, "bad batch %d", B);
     DI_REQUIRE(y && x && dW && db && loss, "null pointer");
     for (int l = 0; l < net->L; ++l) DI_REQUIRE(dW[l] && db[l], "null gradient pointer for layer %d", l + 1);
     DI_REQUIRE(!net->d.train_fc || dWfc, "train_fc network needs dWfc");
@@ -1408,7 +1411,7 @@ int deepinv_net_calibrate(deepinv_net* net, const float* y, int B, void* stream)
 {
     DI_REQUIRE(net, "net is NULL");
     DeviceGuard dg(net->dev);
-    DI_REQUIRE(B >= 1 && y, "calibration needs a batch (B >= 1) of measurements");
+    DI_REQUIRE(B >= 1 && B <= kMaxBatch && y, "calibration needs a batch (1 <= B <= 2^30) of measurements");
     if (!net->fp8) return DEEPINV_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DI_TRY(ensure_ws(net, B, st));
