@@ -82,7 +82,7 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
 
     before = quality(net)
     saved, grads = net.new_saved(batch), net.grad_buffers()
-    first = last = None
+    first = last = loss = None
     step = lr
     curve = [(0, before[0], before[1])] if curve_every else None
     for k in range(steps):
@@ -97,7 +97,8 @@ def train_and_evaluate(n: int = 32, ratio: float = 0.25, *, images: str = "voron
         net.sgd_momentum(dW, db, None, lr=step, mu=mu)
         if curve_every and (k + 1) % curve_every == 0:
             curve.append((k + 1,) + quality(net))
-    last = float(loss)
+    if loss is not None:
+        last = float(loss)
     if prec == "bf16":
         after = quality(net)
     else:
