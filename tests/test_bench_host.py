@@ -71,3 +71,11 @@ def test_conv2_hash_follows_the_conv2_source(tmp_path, monkeypatch):
 def test_host_cpu_names_the_model():
     name = bench.host_cpu()
     assert isinstance(name, str) and name and "\n" not in name
+
+
+def test_optional_section_failure_is_recorded(capsys):
+    def boom(_):
+        raise RuntimeError("no GPU here")
+    assert bench.optional("serving", lambda a: {"ok": a}, 3) == {"ok": 3}
+    assert bench.optional("serving", boom, 1) == {"error": "RuntimeError: no GPU here"}
+    assert "section serving failed" in capsys.readouterr().err
