@@ -27,7 +27,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -436,7 +435,6 @@ def serving_bench(args):
     Poisson arrivals (seed 4) of single recoveries drawn uniformly over the 9 classes,
     a continuous-batching server (4 streams, batches <= 64, 40 GB budget); per offered
     rate: latency p50/p99 (scheduled arrival -> result in host memory) and images/s."""
-    import ctypes
     import numpy as np
     from paper_1701_03891_gb300 import deepinv, synth
     nets, pools = [], []

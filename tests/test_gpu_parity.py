@@ -170,9 +170,11 @@ def test_backward_bf16_wide_train_fc(di, n1, n2, M, B):
     assert err <= 5e-2, ("wfc", err)
 
 
-def test_conv2_row_mode_matches_window_mode(di):
+def test_conv2_row_mode_matches_window_mode(di, tmp_path):
     """Both conv2 pipelines (window slabs vs per-row pieces) give identical bits."""
-    import subprocess, sys, os, json
+    import os
+    import subprocess
+    import sys
     code = (
         "import numpy as np, torch, sys; sys.path.insert(0, %r);"
         "from paper_1701_03891_gb300 import deepinv, synth;"
@@ -181,14 +183,12 @@ def test_conv2_row_mode_matches_window_mode(di):
         "net = deepinv.Net(phi, p, 64, 64, prec='bf16');"
         "y = net.measure(torch.from_numpy(x).cuda()); out = net.forward(y).cpu().numpy();"
         "np.save(sys.argv[1], out)" % os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    import tempfile
     outs = []
     for window in ("0", "1"):
-        f = tempfile.mktemp(suffix=".npy")
+        f = str(tmp_path / ("xhat_window%s.npy" % window))
         env = dict(os.environ, DEEPINV_CONV2_WINDOW=window)
         subprocess.check_call([sys.executable, "-c", code, f], env=env)
         outs.append(np.load(f))
-        os.unlink(f)
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
