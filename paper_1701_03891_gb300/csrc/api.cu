@@ -622,7 +622,7 @@ int backward_tc(deepinv_net* n, const float* y, const float* x, int B, int Bnorm
                 float* const dW[], float* const db[], float* dWfc, double* loss, cudaStream_t st)
 {
     const Geo& g = n->geo;
-    const int N = n->N, M = n->d.M, H = n->d.n1, W = n->d.n2;
+    const int N = n->N, M = n->d.M;
     if (B > n->bws_B || !n->bws) {
         const size_t need = carve_bwd_tc(n, B, nullptr).bytes;
         DI_CUDA(cudaStreamSynchronize(st));
