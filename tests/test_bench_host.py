@@ -79,3 +79,35 @@ def test_optional_section_failure_is_recorded(capsys):
     assert bench.optional("serving", lambda a: {"ok": a}, 3) == {"ok": 3}
     assert bench.optional("serving", boom, 1) == {"error": "RuntimeError: no GPU here"}
     assert "section serving failed" in capsys.readouterr().err
+
+
+class _FakeSmi:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_parsed():
+    """Median SM clock, the maximum, and a reason only when nvidia-smi says Active."""
+    c = bench.Clocks(0)
+    c.p = _FakeSmi()
+    rows = [
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1995, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1010.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "garbage line",
+    ]
+    c.f.write("\n".join(rows) + "\n")
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not os.path.exists(c.f.name)
+
+
+def test_clock_sampler_missing_is_reported():
+    c = bench.Clocks(0)
+    c.p = None
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+    assert not os.path.exists(c.f.name)
