@@ -5,4 +5,4 @@ The compute path is ``libdeepinv.so`` (hand-written CUDA behind a C ABI, see
 package does not load the library; the first call through the binding does,
 and raises if the library is missing.
 """
-__all__ = ["synth", "deepinv"]
+__all__ = ["synth", "deepinv", "evaluate"]
