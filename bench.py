@@ -77,9 +77,10 @@ def peaks():
         with open(p) as f:
             d = json.load(f)
         return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
-                    bf16_sust=float(d["bf16_tflops_sustained"]), src="measured")
+                    bf16_sust=float(d["bf16_tflops_sustained"]), src="measured",
+                    sust_mhz=(d.get("clocks_under_load") or {}).get("sm_mhz_median"))
     except Exception:
-        return dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback")
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback", sust_mhz=None)
 
 
 class Clocks:
@@ -238,6 +239,54 @@ def traffic_record():
     return None
 
 
+CONV_FLOP_PER_PX = 2 * (64 * 121 + 64 * 32 * 121 + 32 * 121)   # conv1 + conv2 + conv3 (518 848)
+
+
+def algorithmic_bytes(B, n, M):
+    """Minimum HBM bytes per launch of the four HBM-side stages of one step: each
+    input read once and each output written once (activations bf16, planes
+    counted at their n x n pixels, not their padding)."""
+    N = n * n
+    px = B * N
+    return {"measure": 4 * px + 2 * M * N + 4 * B * M,     # x fp32 in, Phi bf16 once, y fp32 out
+            "fc": 4 * B * M + 2 * M * N + 2 * px,          # y fp32 in, Phi^T bf16 once, x~ bf16 plane out
+            "conv1": 2 * px + 128 * px,                    # x~ in, a1 (64 ch bf16) out
+            "conv3": 64 * px + 4 * px}                     # a2 (32 ch bf16) in, x^ fp32 out
+
+
+def roofline(stage_ms, B, n, M, pk, clk):
+    """The dominant kernel (conv2) against the measured dense-bf16 burst peak (the
+    timed region is tens of ms at full clocks); the three conv layers together
+    (the target is on them); the HBM-side stages against the measured copy
+    bandwidth.  Per-launch work / mean launch time from the library's own
+    CUDA events on the launching stream."""
+    px = B * n * n
+    conv2_flop = 2.0 * CONV2_MAC_PER_PX * px
+    conv2_ms = stage_ms["conv2"]
+    achieved = conv2_flop / (conv2_ms / 1e3) / 1e12
+    src = pk["src"]
+    conv_ms = stage_ms["conv1"] + stage_ms["conv2"] + stage_ms["conv3"]
+    conv_tflops = CONV_FLOP_PER_PX * px / (conv_ms / 1e3) / 1e12
+    hbm = {}
+    for k, nbytes in algorithmic_bytes(B, n, M).items():
+        gbs = nbytes / (stage_ms[k] / 1e3) / 1e9
+        hbm[k] = {"ms": stage_ms[k], "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                  "frac": gbs / pk["hbm"]}
+    dram = traffic_record()
+    return {"bound": "tensor", "kernel": "conv2 (tap-stacked tcgen05 implicit GEMM)",
+            "achieved": achieved, "peak": pk["bf16"], "unit": "TFLOP/s", "frac": achieved / pk["bf16"],
+            "peak_note": "dense bf16 burst peak of %s (MEASURED_PEAKS.json bf16_tflops)" % src,
+            "traffic": (dram * B) if dram is not None else None,
+            "algorithmic_flop_per_launch": conv2_flop,
+            "frac_of_sustained": achieved / pk["bf16_sust"],
+            "sustained_note": "bf16_tflops_sustained of %s was taken power-capped (median %s MHz); this run's "
+                              "median SM clock under load: %s MHz" % (src, pk.get("sust_mhz"), clk.get("sm_mhz")),
+            "conv_layers": {"flop_per_px": CONV_FLOP_PER_PX, "ms": conv_ms, "achieved": conv_tflops,
+                            "peak": pk["bf16"], "unit": "TFLOP/s", "frac": conv_tflops / pk["bf16"],
+                            "note": "conv1 + conv2 + conv3 (the target: >= 0.5 of dense bf16 peak)"},
+            "hbm_stages": {"peak_gbs": pk["hbm"], "peak_note": "hbm_gbs of %s" % src, "stages": hbm}}
+
+
 def large_bench(args):
     """256 x 256 images (N = 65536), M/N = 0.1 (M = 6554), batch 256 of DCT-sparse
     images (K = 2000, seed 5): the bf16 path and the e4m3-conv2 path on the same batch.
@@ -281,8 +330,13 @@ def large_bench(args):
         ms = e0.elapsed_time(e1) / args.large_steps
         c2 = st["conv2"][0] / max(1, st["conv2"][1])
         results[prec] = xh.cpu().numpy()
+        tf = 2.0 * 64 * 32 * 121 * B * N / (c2 / 1000.0) / 1e12
+        # e4m3 against twice the measured bf16 burst peak (the nominal fp8 : bf16 dense ratio)
+        peak = pk["bf16"] * (2.0 if prec == "fp8" else 1.0)
         out[prec] = {"images_per_s": B / (ms / 1000.0), "ms_per_step": ms,
-                     "conv2_ms": c2, "conv2_tflops": 2.0 * 64 * 32 * 121 * B * N / (c2 / 1000.0) / 1e12,
+                     "conv2_ms": c2, "conv2_tflops": tf, "conv2_peak_tflops": peak, "conv2_frac": tf / peak,
+                     "conv2_peak_note": ("2 x the measured bf16 burst peak (nominal e4m3 : bf16 dense ratio)"
+                                         if prec == "fp8" else "measured bf16 burst peak"),
                      "stage_ms": {k: v[0] / max(1, v[1]) for k, v in st.items()}}
         net.close()
         del yd, xh
@@ -584,16 +638,22 @@ def run_native(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = deepinv.launch_count()
+    host_issue = []
     w0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
         evs[k][0].record(stream)
+        h0 = time.perf_counter()
         step()
+        host_issue.append(time.perf_counter() - h0)
         evs[k][1].record(stream)
+    w_issued = time.perf_counter() - w0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     wall = time.perf_counter() - w0
+    launches = deepinv.launch_count() - launches0
     clk = clocks.stop()
     stages = net.profile_read()
     net.profile(False)
@@ -604,18 +664,8 @@ def run_native(args):
     step_stats = {"median": step_times[len(step_times) // 2], "min": step_times[0], "max": step_times[-1],
                   "note": "this rank's per-step CUDA-event times (ms)"}
 
-    conv2_ms = stages["conv2"][0] / max(1, stages["conv2"][1])
-    conv2_flop = 2.0 * CONV2_MAC_PER_PX * B * n * n
-    achieved = conv2_flop / (conv2_ms / 1000.0) / 1e12
-    dram = traffic_record()
-    roof = {"bound": "tensor", "kernel": "conv2 (tap-stacked tcgen05 implicit GEMM)",
-            "achieved": achieved, "peak": pk["bf16_sust"], "unit": "TFLOP/s",
-            "frac": achieved / pk["bf16_sust"],
-            "peak_note": "bf16 sustained of %s (MEASURED_PEAKS.json)" % pk["src"] if pk["src"] == "measured"
-            else "bf16 sustained of fallback",
-            "traffic": (dram * B) if dram is not None else None,
-            "algorithmic_flop_per_launch": conv2_flop}
     stage_ms = {k: v[0] / max(1, v[1]) for k, v in stages.items()}
+    roof = roofline(stage_ms, B, n, M, pk, clk)
 
     bf16_out = xh.cpu().numpy()
     # float32 CUDA-core path on the same batch
@@ -709,7 +759,17 @@ def run_native(args):
             "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "deep_64": deep,
             "eval_32": evaluation,
             "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": 8 * args.steps, "wall_s_timed_region": wall, "device_status": status}
+            "gpu_launches": launches,
+            "gpu_launches_note": "the library's own kernel launches in the timed region, counted by "
+                                 "deepinv_launch_count (the L2-flush fill is torch's and not counted)",
+            "wall_s_timed_region": wall,
+            "host": {"issue_ms_per_step": {"median": 1e3 * sorted(host_issue)[len(host_issue) // 2],
+                                           "max": 1e3 * max(host_issue)},
+                     "issue_s_all_steps": w_issued,
+                     "note": "host time to issue each step's calls (argument checks + launches); the "
+                             "wall time of the timed region also holds the L2-flush fills and the final "
+                             "synchronisation"},
+            "device_status": status}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

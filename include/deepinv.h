@@ -92,10 +92,18 @@ const char* deepinv_last_error(void);
 /* Library ABI version (major * 100 + minor). */
 int deepinv_version(void);
 
-/* Sticky device-side status of the library on the current device: DEEPINV_OK,
- * or DEEPINV_ETIMEOUT if a bounded wait in a kernel ran out since the last
- * reset.  Synchronises the device.  `reset` != 0 clears it. */
+/* Sticky device-side status of the library: DEEPINV_OK, or DEEPINV_ETIMEOUT
+ * if a bounded wait in a kernel ran out since the last reset, on any device
+ * the library has used (the status words of the network and measurement
+ * calls and of deepinv_measure_noalloc).  Synchronises those devices.
+ * `reset` != 0 clears the words. */
 int deepinv_device_status(int reset);
+
+/* Number of kernels the library has launched in this process so far (every
+ * launch of every entry point, counted on the host as it is issued); a
+ * caller takes the difference around a region to count its launches.  No
+ * counterpart in the paper. */
+unsigned long long deepinv_launch_count(void);
 
 /* Failure-path check of the device status word (no counterpart in the paper):
  * launches one kernel on the current device whose bounded wait is never
@@ -128,13 +136,17 @@ int deepinv_measure(const float* phi, int M, int N, const float* x, int B, float
  * NB = ceil16(M / ceil(M / 256)), do not fit are rejected with DEEPINV_EINVAL
  * before anything is launched (M = 410, N = 4096 fits up to B = 3584).
  *
- * The first call on a device looks the array up (cudaGetSymbolAddress) and
- * clears its header, synchronously; make that first call before any stream
- * capture.  All calls on a device share the array and it keeps the last
- * call's contents, so calls whose work overlaps on the GPU (different streams
- * without ordering) race and may return wrong results.  A bounded wait that
- * runs out inside this call is recorded in the array's header and is not
- * reported by deepinv_device_status(). */
+ * phi may also be managed memory; its device is the one the call runs on.
+ *
+ * Every call looks the array's device address up (cudaGetSymbolAddress); the
+ * first call on a device (and the first after a device reset gave the array a
+ * new address) also clears its header, synchronously, so make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents, so calls whose work overlaps on the GPU
+ * (different streams without ordering) race and may return wrong results.  A
+ * bounded wait that runs out inside this call is recorded in the array's
+ * header, and deepinv_device_status() reports it (DEEPINV_ETIMEOUT) like any
+ * other; its reset clears it. */
 int deepinv_measure_noalloc(const float* phi, int M, int N, const float* x, int B, float* y,
                             void* stream);
 

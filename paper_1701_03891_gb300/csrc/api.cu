@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -42,6 +43,20 @@ int* device_status_word()
     }
     return g_status_words[dev];
 }
+
+int device_of(const void* p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ? a.device : -1;
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static int num_sms_current()
 {
@@ -158,16 +173,6 @@ struct DeviceGuard {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
-
-int device_of(const void* p)
-{
-    cudaPointerAttributes a;
-    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return -1;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ? a.device : -1;
-}
 
 // Record an event from the pool on `st`; returns its index or -1.
 int prof_event(deepinv_net* n, cudaStream_t st)
@@ -1020,7 +1025,9 @@ extern "C" {
 
 const char* deepinv_last_error(void) { return di::g_err; }
 
-int deepinv_version(void) { return 200; }
+int deepinv_version(void) { return 201; }
+
+unsigned long long deepinv_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int deepinv_device_status(int reset)
 {
@@ -1029,15 +1036,26 @@ int deepinv_device_status(int reset)
         std::lock_guard<std::mutex> lk(g_status_mu);
         words = g_status_words;
     }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        ndev = 0;
+    }
+    if ((int)words.size() > ndev) ndev = (int)words.size();
     int v = 0;
-    for (int dev = 0; dev < (int)words.size(); ++dev) {
-        if (!words[dev]) continue;
+    for (int dev = 0; dev < ndev; ++dev) {
+        // the library's status word and the allocation-free measurement's one
+        int* w2[2] = {dev < (int)words.size() ? words[dev] : nullptr, noalloc_status_word(dev)};
+        if (!w2[0] && !w2[1]) continue;
         DeviceGuard g(dev);
         DI_CUDA(cudaDeviceSynchronize());
-        int w = 0;
-        DI_CUDA(cudaMemcpy(&w, words[dev], sizeof(int), cudaMemcpyDeviceToHost));
-        if (reset) DI_CUDA(cudaMemset(words[dev], 0, sizeof(int)));
-        if (w) v = w;
+        for (int* p : w2) {
+            if (!p) continue;
+            int w = 0;
+            DI_CUDA(cudaMemcpy(&w, p, sizeof(int), cudaMemcpyDeviceToHost));
+            if (reset) DI_CUDA(cudaMemset(p, 0, sizeof(int)));
+            if (w) v = w;
+        }
     }
     if (v == DEV_TIMEOUT) {
         set_error("a bounded wait inside a kernel ran out");

@@ -17,6 +17,17 @@ void set_error(const char* fmt, ...);
 // Per-device sticky status word that kernels with bounded waits write into.
 int* device_status_word();
 
+// Status word of deepinv_measure_noalloc's static scratch on `dev` (NULL
+// until that entry point has run on the device); deepinv_device_status reads
+// and resets it beside the per-device word above.
+int* noalloc_status_word(int dev);
+
+// Device that owns `p` (device or managed memory), else -1.
+int device_of(const void* p);
+
+// Counts one kernel launch of the library (deepinv_launch_count).
+void count_launch();
+
 #define DI_REQUIRE(cond, ...)                 \
     do {                                      \
         if (!(cond)) {                        \
@@ -35,7 +46,12 @@ int* device_status_word();
         }                                                                           \
     } while (0)
 
-#define DI_LAUNCH_CHECK() DI_CUDA(cudaGetLastError())
+// After every kernel launch: checks the launch and counts it.
+#define DI_LAUNCH_CHECK()                 \
+    do {                                  \
+        DI_CUDA(cudaGetLastError());      \
+        ::di::count_launch();             \
+    } while (0)
 
 #define DI_TRY(expr)                  \
     do {                              \

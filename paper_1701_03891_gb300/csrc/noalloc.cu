@@ -16,16 +16,16 @@ namespace di {
 namespace {
 
 // Scratch for the packed operands: a 256-byte header (word 0 is the status
-// word of the bounded waits in the GEMM kernel) followed by the packed Phi and
-// the packed x.  Every device that loads the library holds these 32 MiB until
-// the process exits.
+// word of the bounded waits in the GEMM kernel, read and reset by
+// deepinv_device_status) followed by the packed Phi and the packed x.  Every
+// device that loads the library holds these 32 MiB until the process exits.
 constexpr size_t kScratchBytes = 32u << 20;
 constexpr size_t kHeaderBytes = 256;
 static __device__ __align__(256) unsigned char g_measure_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_scratch_addr[kMaxDevices];   // device address per device, set up once
+unsigned char* g_scratch_addr[kMaxDevices];   // device address per device, as last looked up
 
 inline int up16(int x) { return (x + 15) / 16 * 16; }
 inline int nb_for(int n)
@@ -35,19 +35,21 @@ inline int nb_for(int n)
 }
 
 // Device address of the static array on `dev` (which must be current).  The
-// first call on a device looks the address up and clears the header.
+// address is looked up on every call; when it differs from the one recorded
+// for the device (the first call, or a new context after a device reset), the
+// header is cleared before the array is used.
 int scratch_on(int dev, unsigned char** out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_measure_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            set_error("deepinv_measure_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
-                      cudaGetErrorString(e));
-            return DEEPINV_ECUDA;
-        }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_measure_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_error("deepinv_measure_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                  cudaGetErrorString(e));
+        return DEEPINV_ECUDA;
+    }
+    if (g_scratch_addr[dev] != p) {
         e = cudaMemset(p, 0, kHeaderBytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -61,6 +63,14 @@ int scratch_on(int dev, unsigned char** out)
 }
 
 }  // namespace
+
+int* noalloc_status_word(int dev)
+{
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return reinterpret_cast<int*>(g_scratch_addr[dev]);
+}
+
 }  // namespace di
 
 using namespace di;
@@ -82,14 +92,9 @@ extern "C" int deepinv_measure_noalloc(const float* phi, int M, int N, const flo
                   M, N, B, phi_bytes + x_bytes, kScratchBytes - kHeaderBytes);
         return DEEPINV_EINVAL;
     }
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, phi) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
-        cudaGetLastError();
-        set_error("deepinv_measure_noalloc: phi is not device memory");
-        return DEEPINV_EINVAL;
-    }
-    const int dev = attr.device;
-    DI_REQUIRE(dev >= 0 && dev < kMaxDevices, "device %d out of range", dev);
+    const int dev = device_of(phi);
+    DI_REQUIRE(dev >= 0, "deepinv_measure_noalloc: phi is not device or managed memory");
+    DI_REQUIRE(dev < kMaxDevices, "device %d out of range", dev);
     int prev = -1;
     DI_CUDA(cudaGetDevice(&prev));
     if (prev != dev) DI_CUDA(cudaSetDevice(dev));

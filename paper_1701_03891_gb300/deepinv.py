@@ -70,6 +70,7 @@ SIGNATURES = {
     "deepinv_last_error": (ctypes.c_char_p, []),
     "deepinv_version": (_I, []),
     "deepinv_device_status": (_I, [_I]),
+    "deepinv_launch_count": (ctypes.c_ulonglong, []),
     "deepinv_selftest_bounded_wait": (_I, [_P]),
     "deepinv_measure": (_I, [_P, _I, _I, _P, _I, _P, _I, _P]),
     "deepinv_measure_noalloc": (_I, [_P, _I, _I, _P, _I, _P, _P]),
@@ -184,6 +185,11 @@ def _arr(ptrs):
 
 def device_status(reset: bool = False) -> int:
     return lib().deepinv_device_status(1 if reset else 0)
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().deepinv_launch_count())
 
 
 def selftest_bounded_wait(stream=None):

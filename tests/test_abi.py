@@ -56,7 +56,14 @@ def test_binding_constants_match_header():
 
 
 def test_version(L):
-    assert L.deepinv_version() == 200
+    assert L.deepinv_version() == 201
+
+
+def test_launch_count_starts_at_zero_without_launches(L):
+    # host-side checks that reject a call launch nothing, so the count does not move
+    before = L.deepinv_launch_count()
+    assert L.deepinv_measure(None, 4, 8, None, 2, None, 0, None) != 0
+    assert L.deepinv_launch_count() == before
 
 
 def test_null_pointers_rejected_on_host(L):
@@ -109,7 +116,7 @@ def test_binding_signatures_match_header():
     (a mismatch would pass arguments in the wrong registers or widths)."""
     from paper_1701_03891_gb300 import deepinv
     ret_types = {"int": ctypes.c_int, "size_t": ctypes.c_size_t, "const char*": ctypes.c_char_p,
-                 "const char *": ctypes.c_char_p}
+                 "const char *": ctypes.c_char_p, "unsigned long long": ctypes.c_ulonglong}
     scalars = {"int": ctypes.c_int, "float": ctypes.c_float, "double": ctypes.c_double,
                "size_t": ctypes.c_size_t, "uint64_t": ctypes.c_uint64}
     decl = _declarations()

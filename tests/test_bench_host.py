@@ -15,10 +15,33 @@ import bench  # noqa: E402
 
 def test_peaks_measured_then_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.peaks() == dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback")
+    assert bench.peaks() == dict(hbm=6800.0, bf16=1900.0, bf16_sust=1700.0, src="fallback", sust_mhz=None)
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(
-        {"hbm_gbs": 7000.5, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1750.0}))
-    assert bench.peaks() == dict(hbm=7000.5, bf16=2000.0, bf16_sust=1750.0, src="measured")
+        {"hbm_gbs": 7000.5, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1750.0,
+         "clocks_under_load": {"sm_mhz_median": 1447.0}}))
+    assert bench.peaks() == dict(hbm=7000.5, bf16=2000.0, bf16_sust=1750.0, src="measured", sust_mhz=1447.0)
+
+
+def test_roofline_uses_the_burst_peak_and_reports_every_stage(monkeypatch):
+    """conv2's fraction is against the dense bf16 burst peak; the three conv layers
+    are reported together; the HBM-side stages carry their algorithmic bytes
+    (64 x 64, batch 1024, M = 410: conv1 130 B and conv3 68 B per pixel)."""
+    monkeypatch.setattr(bench, "traffic_record", lambda: None)
+    pk = dict(hbm=7000.0, bf16=2000.0, bf16_sust=1700.0, src="measured", sust_mhz=1447.0)
+    st = {"measure": 0.05, "fc": 0.02, "conv1": 0.16, "conv2": 1.2, "conv3": 0.16, "hidden": 0.0}
+    r = bench.roofline(st, 1024, 64, 410, pk, {"sm_mhz": 2070.0})
+    px = 1024 * 4096
+    conv2 = 2 * 64 * 32 * 121 * px / 1.2e-3 / 1e12
+    assert abs(r["achieved"] - conv2) < 1e-9 and r["peak"] == 2000.0
+    assert abs(r["frac"] - conv2 / 2000.0) < 1e-12
+    assert abs(r["frac_of_sustained"] - conv2 / 1700.0) < 1e-12
+    c = r["conv_layers"]
+    assert c["flop_per_px"] == 518848 and abs(c["ms"] - 1.52) < 1e-12
+    assert abs(c["frac"] - 518848 * px / 1.52e-3 / 1e12 / 2000.0) < 1e-12
+    h = r["hbm_stages"]["stages"]
+    assert h["conv1"]["algorithmic_bytes"] == 130 * px and h["conv3"]["algorithmic_bytes"] == 68 * px
+    assert h["measure"]["algorithmic_bytes"] == 4 * px + 2 * 410 * 4096 + 4 * 1024 * 410
+    assert abs(h["conv3"]["frac"] - 68 * px / 0.16e-3 / 1e9 / 7000.0) < 1e-12
 
 
 def test_traffic_only_for_the_measured_conv2_source(tmp_path, monkeypatch):

@@ -235,6 +235,39 @@ def test_forward_bf16_full_batch_sampled(di):
     net.close()
 
 
+def test_f32_gemm_rows_above_grid_limit(di):
+    """The float32 GEMM runs problems taller than 65535 row tiles of 64 (the gridDim.y
+    limit) as several launches: y = Phi x for 65535 * 64 + 100 signals (two launches),
+    rows on both sides of the launch boundary against the oracle."""
+    M, N = 8, 16
+    B = 65535 * 64 + 100
+    phi = synth.gaussian_phi(M, N, seed=11)
+    x = np.random.default_rng(12).uniform(0, 1, (B, N)).astype(np.float32)
+    y = di.measure(_cuda(phi), _cuda(x), prec="f32").cpu().numpy()
+    idx = np.r_[0, 1, 65535 * 64 - 1, 65535 * 64, 65535 * 64 + 1, B - 1,
+                np.random.default_rng(13).integers(0, B, 50)]
+    assert _maxrel(y[idx], oracle.measure(phi, x[idx])) <= TOL["f32"]
+
+
+def test_f32_conv_batch_above_grid_limit(di):
+    """The float32 convolutions run batches above 65535 images (the gridDim.z limit)
+    as several launches: a 4 x 4 network over 65535 + 70 images, images on both
+    sides of the launch boundary against the oracle."""
+    n1 = n2 = 4
+    B = 65535 + 70
+    phi = synth.gaussian_phi(8, 16, seed=14)
+    params = synth.he_params(seed=15, bias_std=0.05)
+    x = np.random.default_rng(16).uniform(0, 1, (B, 16)).astype(np.float32)
+    net = di.Net(phi, params, n1, n2, prec="f32")
+    y = net.measure(_cuda(x))
+    xhat = net.forward(y).cpu().numpy()
+    idx = np.r_[0, 65534, 65535, 65536, B - 1, np.random.default_rng(17).integers(0, B, 20)]
+    ref = oracle.forward(oracle.measure(phi, x[idx]), params, n1, n2, phi=phi)
+    assert np.all(np.isfinite(xhat))
+    assert _maxrel(xhat[idx], ref) <= TOL["f32"]
+    net.close()
+
+
 def test_forward_batch_sizes_reuse_workspace(di):
     """Growing and shrinking the batch on one network keeps results exact (zero borders preserved)."""
     phi, params, x = _case(32, 32, 0.1, 40)
