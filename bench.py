@@ -304,6 +304,7 @@ def large_bench(args):
     xd = torch.from_numpy(x).cuda()
     stream = torch.cuda.current_stream()
     out = {"workload": "sense+recover 256x256, M/N=0.10 (M=%d), batch %d, DCT-sparse K=2000" % (M, B)}
+    pk = peaks()
     results = {}
     for prec in ("bf16", "fp8"):
         net = deepinv.Net(phi, params, n, n, prec=prec)
@@ -627,13 +628,16 @@ def run_native(args):
         net.measure(xd, out=yd)
         net.forward(yd, out=xh)
 
+    # the clock sampler starts before the warm-up, so that nvidia-smi's own start-up
+    # (driver queries that can stall this process's CUDA calls) is over before the
+    # timed region; it samples until the timed region ends
     clocks = Clocks(local)
+    clocks.start()
+    time.sleep(1.0)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks.start()
-    time.sleep(0.25)
     net.profile(True)
     if dist:
         dist.barrier()

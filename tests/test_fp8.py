@@ -3,22 +3,26 @@
 Weights are scaled per filter (max |w| -> 448) and the conv1 output by one
 static factor calibrated on a batch; accumulation is float32.
 
-Tolerance, from the arithmetic: e4m3 keeps 4 significant bits, so rounding an
-operand costs up to 2^-4 relative (about 3.6 % rms for values spread over a
-binade) and a product of two rounded operands about 5 % rms.  conv2's sums over
-7744 products of mixed sign pass that on to z2 (the cancellation of the seeded
-random network keeps ||terms|| / |sum| near 1), and conv3 passes it on to x^.
-Measured: 5.2-5.4 % per image at every size; the tests allow 8e-2.  (3e-2 is
-below what e4m3 operands on both sides of the product permit here.)
+Tolerance, from the rounding floor (tests/_precision.py): the rounded-operand
+oracle (oracle/rounded.py) evaluates the network with a1 and conv2's weights
+rounded to e4m3 exactly as this path scales and stores them, every other
+operand as the bfloat16 path stores it, and every sum exact.  Its distance to
+the exact oracle is what e4m3 operands allow: 3.3-4.1 % per image on these
+seeded networks (4 significant bits on both operands of every conv2 product),
+above the 3e-2 the target states -- tests/test_rounding_pins.py shows that
+floor on the CPU, with one activation scale per layer and with one per
+channel.  The kernel is held to 0.75 floors of the rounded oracle and 1.25
+floors of the exact one, every pixel checked.
 """
 import numpy as np
 import pytest
 
 import oracle
+from oracle import rounded
 from paper_1701_03891_gb300 import synth
+from _precision import check_images
 
 pytestmark = pytest.mark.gpu
-TOL_FP8 = 8e-2
 
 
 @pytest.fixture(scope="module")
@@ -57,9 +61,10 @@ def test_forward_fp8(di, n1, n2, ratio, B, images):
     net.calibrate(y)
     xhat = net.forward(y).cpu().numpy()
     ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
-    err = float(np.max(oracle.rel_l2(xhat, ref)))
-    assert np.all(np.isfinite(xhat))
-    assert err <= TOL_FP8, err
+    yb = rounded.measure_bf16(phi, x)
+    rnd = rounded.forward_e4m3(yb, params, n1, n2, phi=phi, amax_a1=rounded.amax_a1(yb, params, n1, n2, phi=phi))
+    floor, _ = check_images(xhat, ref, rnd, what=(n1, n2, "e4m3"))
+    assert floor > 3e-2          # the format's floor, not the kernel, misses the stated 3e-2
 
 
 def test_fp8_calibration_on_other_batch_and_inference_only(di):
@@ -75,6 +80,8 @@ def test_fp8_calibration_on_other_batch_and_inference_only(di):
     y = net.measure(_cuda(x))
     xhat = net.forward(y).cpu().numpy()
     ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
-    assert float(np.max(oracle.rel_l2(xhat, ref))) <= TOL_FP8
+    amax = rounded.amax_a1(rounded.measure_bf16(phi, calib), params, n1, n2, phi=phi)
+    rnd = rounded.forward_e4m3(rounded.measure_bf16(phi, x), params, n1, n2, phi=phi, amax_a1=amax)
+    check_images(xhat, ref, rnd, what="calibrated on another batch")
     with pytest.raises(di.DeepInvError):
         net.forward(y, saved=net.new_saved(8))   # e4m3 networks do not train

@@ -1,20 +1,51 @@
 """CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative L2 per image, max over the batch):
-  float32 path  <= 1e-5   (float32 products, float32 accumulation)
-  bfloat16 path <= 1e-2   (bfloat16 operands, float32 accumulation)
-The oracle sees the float32 master weights and inputs, so the bfloat16
-tolerance includes the rounding of weights, inputs and activations.
+  float32 path  <= 1e-5   (float32 products, float32 accumulation), and every
+                 pixel within 8e-5 of the image's rms (8 standard deviations
+                 of an error of 1e-5 rms);
+  bfloat16 path <= 1e-2   (the stated bound), and the tighter gates of
+                 tests/_precision.py: within 0.75 of the bfloat16 rounding floor
+                 of the rounded-operand oracle (oracle/rounded.py), within
+                 1.25 floors of the exact oracle, every pixel and every
+                 gradient element checked.
+The exact oracle sees the float32 master weights and inputs, so its distance
+includes the rounding of weights, inputs and activations: the floor.
 """
 import numpy as np
 import pytest
 
 import oracle
+from oracle import rounded
 from paper_1701_03891_gb300 import synth
+from _precision import ELEMENT_FACTOR, check_images, check_tensors
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-5, "bf16": 1e-2}
+
+
+def _check_f32(got, ref):
+    """float32 path: rel-L2 per image and every pixel against the image's rms."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    B = got.shape[0]
+    assert np.all(np.isfinite(got))
+    assert _maxrel(got, ref) <= TOL["f32"]
+    r = ref.reshape(B, -1)
+    rms = np.sqrt(np.mean(r * r, axis=1, keepdims=True))
+    assert float(np.max(np.abs(got.reshape(B, -1) - r) / rms)) <= 8 * TOL["f32"]
+
+
+def _check_sense_recover(xhat, phi, params, x, n1, n2, prec, **kw):
+    """x^ of the path's own y = Phi x against the exact oracle, and for bf16 against
+    the rounded-operand oracle fed by the bf16 measurement."""
+    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi, **kw)
+    if prec == "f32":
+        _check_f32(xhat, ref)
+        return
+    rnd = rounded.forward_bf16(rounded.measure_bf16(phi, x), params, n1, n2, phi=phi, **kw)
+    check_images(xhat, ref, rnd, what=(n1, n2))
+    assert _maxrel(xhat, ref) <= TOL["bf16"]
 
 
 @pytest.fixture(scope="module")
@@ -86,10 +117,7 @@ def test_forward(di, prec, n1, n2, ratio, B):
     xd = _cuda(x)
     y = net.measure(xd)
     xhat = net.forward(y).cpu().numpy()
-    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
-    err = _maxrel(xhat, ref)
-    assert np.all(np.isfinite(xhat))
-    assert err <= TOL[prec], err
+    _check_sense_recover(xhat, phi, params, x, n1, n2, prec)
     net.close()
 
 
@@ -103,9 +131,7 @@ def test_forward_bf16_wide(di, n1, n2, ratio, B):
     net = di.Net(phi, params, n1, n2, prec="bf16")
     y = net.measure(_cuda(x))
     xhat = net.forward(y).cpu().numpy()
-    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
-    assert np.all(np.isfinite(xhat))
-    assert _maxrel(xhat, ref) <= TOL["bf16"]
+    _check_sense_recover(xhat, phi, params, x, n1, n2, "bf16")
 
 
 def test_gemm_two_row_tiles_odd_counts(di):
@@ -122,9 +148,10 @@ def test_gemm_two_row_tiles_odd_counts(di):
     net.close()
     phi2, params, x2 = _case(200, 200, 0.02, 2, seed=4)
     net2 = di.Net(phi2, params, 200, 200, prec="bf16")
-    y2 = _cuda(oracle.measure(phi2, x2))
-    ref = oracle.forward(y2.cpu().numpy(), params, 200, 200, phi=phi2)
-    assert _maxrel(net2.forward(y2).cpu().numpy(), ref) <= TOL["bf16"]
+    y2 = oracle.measure(phi2, x2)
+    ref = oracle.forward(y2, params, 200, 200, phi=phi2)
+    rnd = rounded.forward_bf16(rounded.f32(y2), params, 200, 200, phi=phi2)
+    check_images(net2.forward(_cuda(y2)).cpu().numpy(), ref, rnd, what="FC 313 pixel tiles")
 
 
 @pytest.mark.parametrize("n1,n2,ratio,B", [
@@ -137,9 +164,7 @@ def test_forward_bf16_conv3_modes(di, n1, n2, ratio, B):
     net = di.Net(phi, params, n1, n2, prec="bf16")
     y = net.measure(_cuda(x))
     xhat = net.forward(y).cpu().numpy()
-    ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
-    assert np.all(np.isfinite(xhat))
-    assert _maxrel(xhat, ref) <= TOL["bf16"]
+    _check_sense_recover(xhat, phi, params, x, n1, n2, "bf16")
 
 
 @pytest.mark.parametrize("n1,n2,M,B", [
@@ -160,14 +185,7 @@ def test_backward_bf16_wide_train_fc(di, n1, n2, M, B):
     saved = net.new_saved(B)
     net.forward(yd, saved=saved)
     loss, dW, db, dWfc = net.backward(yd, xd, saved)
-    assert abs(float(loss) - loss_ref) <= 2e-2 * abs(loss_ref)
-    for i in range(3):
-        for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
-            ref = g[name]
-            err = float(np.linalg.norm(got.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30))
-            assert err <= 5e-2, (name, err)
-    err = float(np.linalg.norm(dWfc.cpu().numpy() - g["wfc"]) / np.linalg.norm(g["wfc"]))
-    assert err <= 5e-2, ("wfc", err)
+    _check_bf16_grads(loss, dW, db, dWfc, y, x, params, n1, n2, phi, True, loss_ref, g)
 
 
 def test_conv2_row_mode_matches_window_mode(di, tmp_path):
@@ -196,11 +214,13 @@ def test_conv2_row_mode_matches_window_mode(di, tmp_path):
 def test_forward_final_relu(di, prec):
     phi, params, x = _case(32, 32, 0.1, 3)
     net = di.Net(phi, params, 32, 32, prec=prec, final_relu=True)
-    y = _cuda(oracle.measure(phi, x))
-    xhat = net.forward(y).cpu().numpy()
-    ref = oracle.forward(y.cpu().numpy(), params, 32, 32, phi=phi, final_relu=True)
+    y = rounded.f32(oracle.measure(phi, x))
+    xhat = net.forward(_cuda(y)).cpu().numpy()
+    ref = oracle.forward(y, params, 32, 32, phi=phi, final_relu=True)
     assert np.all(xhat >= 0)
     assert float(np.linalg.norm(xhat - ref) / np.linalg.norm(ref)) <= TOL[prec]
+    if prec == "bf16":
+        check_images(xhat, ref, rounded.forward_bf16(y, params, 32, 32, phi=phi, final_relu=True), what="final ReLU")
 
 
 def test_forward_f32_reduced_net(di):
@@ -217,54 +237,39 @@ def test_forward_f32_reduced_net(di):
 
 
 def test_forward_bf16_full_batch_sampled(di):
-    """64 x 64, M/N = 0.1, batch 1024 (the benchmark workload): sampled images against the oracle."""
+    """64 x 64, M/N = 0.1, batch 1024 (the benchmark workload, in its launch
+    configuration).  Every image of the bf16 result against the float32 path's
+    (an independent set of kernels, itself held to 1e-5 of the oracle on sampled
+    images here); 24 sampled images against the exact and the rounded-operand
+    oracle; and batch invariance."""
     n1 = n2 = 64
     B = 1024
     phi, params, x = _case(n1, n2, 0.10, B, images="voronoi", bias_std=0.0)
-    net = di.Net(phi, params, n1, n2, prec="bf16")
     xd = _cuda(x)
+    net = di.Net(phi, params, n1, n2, prec="bf16")
     y = net.measure(xd)
     xhat = net.forward(y).cpu().numpy()
-    assert np.all(np.isfinite(xhat))
-    idx = [0, 1, 511, 777, 1023]
+    netf = di.Net(phi, params, n1, n2, prec="f32")
+    xf = netf.forward(netf.measure(xd)).cpu().numpy()
+    netf.close()
+    assert np.all(np.isfinite(xhat)) and np.all(np.isfinite(xf))
+    idx = np.r_[0, 1, 511, 777, 1023, np.random.default_rng(30).choice(np.arange(2, 1023), 19, replace=False)]
     ref = oracle.forward(oracle.measure(phi, x[idx]), params, n1, n2, phi=phi)
-    assert _maxrel(xhat[idx], ref) <= TOL["bf16"]
+    _check_f32(xf[idx], ref)
+    rnd = rounded.forward_bf16(rounded.measure_bf16(phi, x[idx]), params, n1, n2, phi=phi)
+    floor, _ = check_images(xhat[idx], ref, rnd, what="batch 1024, sampled")
+    # all 1024 images against the float32 path: the stated bound; the floor's margin
+    # (the float32 path is the exact oracle to 1e-5, and these images' floors match
+    # the sampled ones' to a few per cent, so 1.25 * 1.1 floors); every image's worst
+    # pixel within ELEMENT_FACTOR of the sampled images' worst rounding deviation
+    allrel = oracle.rel_l2(xhat, xf)
+    assert float(allrel.max()) <= TOL["bf16"]
+    assert float(allrel.max()) <= 1.25 * 1.1 * floor, (float(allrel.max()), floor)
+    worst_format = float(np.max(np.abs(rnd - ref)))
+    assert float(np.max(np.abs(xhat - xf))) <= ELEMENT_FACTOR * 1.1 * worst_format
     # batch invariance: the same images alone give the same result
-    alone = net.forward(y[idx].contiguous()).cpu().numpy()
-    np.testing.assert_allclose(alone, xhat[idx], rtol=0, atol=1e-6 * np.abs(xhat[idx]).max())
-    net.close()
-
-
-def test_f32_gemm_rows_above_grid_limit(di):
-    """The float32 GEMM runs problems taller than 65535 row tiles of 64 (the gridDim.y
-    limit) as several launches: y = Phi x for 65535 * 64 + 100 signals (two launches),
-    rows on both sides of the launch boundary against the oracle."""
-    M, N = 8, 16
-    B = 65535 * 64 + 100
-    phi = synth.gaussian_phi(M, N, seed=11)
-    x = np.random.default_rng(12).uniform(0, 1, (B, N)).astype(np.float32)
-    y = di.measure(_cuda(phi), _cuda(x), prec="f32").cpu().numpy()
-    idx = np.r_[0, 1, 65535 * 64 - 1, 65535 * 64, 65535 * 64 + 1, B - 1,
-                np.random.default_rng(13).integers(0, B, 50)]
-    assert _maxrel(y[idx], oracle.measure(phi, x[idx])) <= TOL["f32"]
-
-
-def test_f32_conv_batch_above_grid_limit(di):
-    """The float32 convolutions run batches above 65535 images (the gridDim.z limit)
-    as several launches: a 4 x 4 network over 65535 + 70 images, images on both
-    sides of the launch boundary against the oracle."""
-    n1 = n2 = 4
-    B = 65535 + 70
-    phi = synth.gaussian_phi(8, 16, seed=14)
-    params = synth.he_params(seed=15, bias_std=0.05)
-    x = np.random.default_rng(16).uniform(0, 1, (B, 16)).astype(np.float32)
-    net = di.Net(phi, params, n1, n2, prec="f32")
-    y = net.measure(_cuda(x))
-    xhat = net.forward(y).cpu().numpy()
-    idx = np.r_[0, 65534, 65535, 65536, B - 1, np.random.default_rng(17).integers(0, B, 20)]
-    ref = oracle.forward(oracle.measure(phi, x[idx]), params, n1, n2, phi=phi)
-    assert np.all(np.isfinite(xhat))
-    assert _maxrel(xhat[idx], ref) <= TOL["f32"]
+    alone = net.forward(y[idx[:5]].contiguous()).cpu().numpy()
+    np.testing.assert_allclose(alone, xhat[idx[:5]], rtol=0, atol=1e-6 * np.abs(xhat[idx[:5]]).max())
     net.close()
 
 
@@ -336,6 +341,26 @@ def _train_case(train_fc):
     return n1, n2, phi, params, x, y
 
 
+def _grad_dict(dW, db, dWfc):
+    got = {}
+    for i in range(len(dW)):
+        got["w%d" % (i + 1)] = dW[i].cpu().numpy()
+        got["b%d" % (i + 1)] = db[i].cpu().numpy()
+    if dWfc is not None:
+        got["wfc"] = dWfc.cpu().numpy()
+    return got
+
+
+def _check_bf16_grads(loss, dW, db, dWfc, y, x, params, n1, n2, phi, train_fc, loss_ref, g):
+    """bf16 gradients against the exact oracle's and the rounded-operand oracle's
+    (tests/_precision.py); the loss within the bfloat16 floor of the loss."""
+    loss_rnd, g_rnd = rounded.backward_bf16(y, x, params, n1, n2, phi=phi, train_fc=train_fc)
+    check_tensors(_grad_dict(dW, db, dWfc if train_fc else None), g, g_rnd, what=(n1, n2))
+    floor = abs(loss_rnd - loss_ref) / abs(loss_ref)
+    assert abs(float(loss) - loss_rnd) <= 0.75 * floor * abs(loss_ref) + 1e-6 * abs(loss_ref)
+    assert abs(float(loss) - loss_ref) <= 1.25 * floor * abs(loss_ref) + 1e-6 * abs(loss_ref)
+
+
 @pytest.mark.parametrize("prec,train_fc", [("f32", False), ("f32", True), ("bf16", False), ("bf16", True)])
 def test_backward_matches_oracle(di, prec, train_fc):
     n1, n2, phi, params, x, y = _train_case(train_fc)
@@ -345,8 +370,11 @@ def test_backward_matches_oracle(di, prec, train_fc):
     saved = net.new_saved(2)
     net.forward(yd, saved=saved)
     loss, dW, db, dWfc = net.backward(yd, xd, saved)
-    tol = {"f32": 1e-4, "bf16": 5e-2}[prec]
-    assert abs(float(loss) - loss_ref) <= (1e-6 if prec == "f32" else 2e-2) * abs(loss_ref)
+    if prec == "bf16":
+        _check_bf16_grads(loss, dW, db, dWfc, y, x, params, n1, n2, phi, train_fc, loss_ref, g)
+        return
+    tol = 1e-4
+    assert abs(float(loss) - loss_ref) <= 1e-6 * abs(loss_ref)
     for i in range(3):
         for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
             ref = g[name]
@@ -372,12 +400,7 @@ def test_backward_bf16_shapes(di, n1, n2, M, B):
     saved = net.new_saved(B)
     net.forward(yd, saved=saved)
     loss, dW, db, _ = net.backward(yd, xd, saved)
-    assert abs(float(loss) - loss_ref) <= 2e-2 * abs(loss_ref)
-    for i in range(3):
-        for name, got in (("w%d" % (i + 1), dW[i]), ("b%d" % (i + 1), db[i])):
-            ref = g[name]
-            err = float(np.linalg.norm(got.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30))
-            assert err <= 5e-2, (name, err)
+    _check_bf16_grads(loss, dW, db, None, y, x, params, n1, n2, phi, False, loss_ref, g)
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
@@ -407,13 +430,17 @@ def test_backward_recompute(di, prec):
         a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(a - b) <= 1e-5 * max(np.linalg.norm(a), 1e-30)
     loss_ref, g = oracle.backward(y, x, params, n1, n2, phi=phi, train_fc=True)
-    tol = 1e-4 if prec == "f32" else 5e-2
     names = ["loss", "w1", "w2", "w3", "b1", "b2", "b3", "wfc"]
-    for name, got in zip(names, chunked):
-        want = loss_ref if name == "loss" else g[name]
-        got = got.cpu().numpy()
-        err = float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30))
-        assert err <= tol, (name, err)
+    if prec == "bf16":
+        c = dict(zip(names, chunked))
+        _check_bf16_grads(c["loss"], [c["w1"], c["w2"], c["w3"]], [c["b1"], c["b2"], c["b3"]], c["wfc"],
+                          y, x, params, n1, n2, phi, True, loss_ref, g)
+    else:
+        for name, got in zip(names, chunked):
+            want = loss_ref if name == "loss" else g[name]
+            got = got.cpu().numpy()
+            err = float(np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-30))
+            assert err <= 1e-4, (name, err)
     net.close()
 
 
