@@ -698,6 +698,13 @@ int net_measure_impl(deepinv_net* n, const float* x, int B, float* y, cudaStream
         const FwdWs w = carve_fwd(n, n->ws_B, n->ws);
         int* status = device_status_word();
         DI_REQUIRE(status, "no device status word");
+        if ((size_t)n->Kms * cdiv(M, n->NBms) * n->NBms * sizeof(bf16) <= ((size_t)64 << 20) &&
+            measure_f32in_supported(x, N, n->NBms)) {
+            // x read by TMA and rounded to bf16 inside the GEMM, K split over a
+            // cluster (Phi stays in L2)
+            return gemm_measure_f32in(x, N, N, n->msB, n->Kms, B, M, n->NBms, y, M, n->num_sms, status, st);
+        }
+        // Phi too large for L2: x packed once, two row tiles per CTA read Phi once per 256 signals
         DI_TRY(pack_kmajor(x, N, 1, B, N, 128, n->Kms, w.xpk, st));
         const int ks = gemm_ksplit(B, M, n->NBms, n->Kms, n->num_sms);
         return tc_gemm_splitk(w.xpk, n->msB, n->Kms, B, M, n->NBms, y, w.mpart, ks, status, st);

@@ -75,6 +75,16 @@ int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mo
 // tile; part holds ksplit * Mr * Nc floats of partial sums (summed in order).
 int tc_gemm_splitk(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, float* out, float* part, int ksplit,
                    int* status, cudaStream_t st);
+// The measurement fed straight from the float32 signals (gemm_f32in.cu):
+// out [Mr][Nc] float32 = X B^T, X float32 [Mr][K] (row stride ldx) read by TMA
+// and rounded to bfloat16 inside the kernel, B packed (TR = NB, Kp); K split
+// over a thread-block cluster, summed through distributed shared memory in a
+// fixed order.  Supported when X is 16-byte aligned with a row stride of a
+// multiple of 4 floats (the tensor map's rules) and NB <= 256; otherwise the
+// call returns DEEPINV_EUNSUPPORTED.
+bool measure_f32in_supported(const float* X, long long ldx, int NB);
+int gemm_measure_f32in(const float* X, long long ldx, int K, const bf16* Bpk, int Kp, int Mr, int Nc, int NB,
+                       float* out, long long ldo, int num_sms, int* status, cudaStream_t st);
 // Split that keeps about one wave of CTAs busy for a GEMM with the given tiles.
 inline int gemm_ksplit(int Mr, int Nc, int NB, int Kp, int num_sms)
 {
