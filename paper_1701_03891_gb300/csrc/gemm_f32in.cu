@@ -20,13 +20,11 @@
 // one of its threads issues the MMAs; warps 2..5 convert the staged float32
 // boxes (one of their threads keeps kFiRawNS stages of x loads in flight), then
 // drain the accumulator.  Every wait is bounded.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <mutex>
 
 #include "kernels.cuh"
 #include "tc.cuh"
+#include "tma.cuh"
 
 namespace di {
 namespace {
@@ -114,17 +112,6 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// ---------------------------------------------------------------- TMA
-// 2-D tiled load of the box at (c0 = column, c1 = row) of the tensor map into
-// shared memory, completing its bytes on `bar`.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
 }
 
 // ---------------------------------------------------------------- conversion
@@ -387,7 +374,14 @@ __global__ void __launch_bounds__(192, 1) measure_f32in_kernel(const __grid_cons
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+size_t fi_smem(int NB)
+{
+    return 1024 + (size_t)kFiRawNS * kFiRaw + (size_t)kFiNS * (kFiA + (size_t)kFiKS * NB * 32) + sizeof(FiSmem);
+}
+
+}  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -403,17 +397,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
     return fn;
 }
 
-size_t fi_smem(int NB)
-{
-    return 1024 + (size_t)kFiRawNS * kFiRaw + (size_t)kFiNS * (kFiA + (size_t)kFiKS * NB * 32) + sizeof(FiSmem);
-}
-
-}  // namespace
-
 // ================================================================ launcher
 bool measure_f32in_supported(const float* X, long long ldx, int NB)
 {
-    return encode_tiled() != nullptr && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ldx * 4) % 16 == 0 &&
+    return tensor_map_encoder() != nullptr && (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ldx * 4) % 16 == 0 &&
            NB >= 16 && NB <= 256 && NB % 16 == 0 && fi_smem(NB) <= 227 * 1024;
 }
 
@@ -432,7 +419,7 @@ int gemm_measure_f32in(const float* X, long long ldx, int K, const bf16* Bpk, in
     const cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
     const cuuint32_t box[2] = {32, 128};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult cr = encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box,
+    const CUresult cr = tensor_map_encoder()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box,
                                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
