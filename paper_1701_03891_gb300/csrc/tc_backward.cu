@@ -557,11 +557,180 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
     return DEEPINV_OK;
 }
 
+// ---------------------------------------------------------------- conv2 weight gradient, swizzled windows
+// The same contraction as wgrad2_kernel<64>, dW2[co][ci][dy][4 s + g] =
+// sum_u G[u - g][co] A1[u + (dy - 5) P + 4 s - 5][ci], with each shifted
+// window read straight out of ONE window per plane instead of one copy per
+// shift.  The windows are stored channel-contiguous per position, with the
+// tensor core's swizzles: the a1 window as 128-byte rows (64 channels, 16-byte
+// chunk c of row r at chunk c ^ (r % 8)), the g2 window as 64-byte rows (32
+// channels, chunk c at c ^ ((r / 2) % 4)).  Both are MN-major operands whose
+// swizzle follows the shared-memory address, so an operand may start at any
+// row: the A operand (M = 128: slots j = 0..3 x 32 filters, slot j = tap phase
+// g = 3 - j, i.e. the g2 rows one position apart) is the g2 window from row
+// 16 k + 5 with LBO = 64 bytes (next slot) and SBO = 512 (next 8 positions);
+// the B operand (N = 192: column groups s = 0..2 x 64 channels, 4 positions
+// apart) is the a1 window from row 16 k with LBO = 512 and SBO = 1024.  One
+// MMA then covers the 12 taps (dy, 4 s + g) of a kernel row (tap 11 unused)
+// for 16 positions.
+//
+// Each CTA takes one kernel row dy (its column) and a contiguous run of
+// 128-position blocks (its split); per block it loads the two windows (136
+// rows each) with 16-byte cp.async from the four epilogue warps, which place
+// every chunk at its swizzled address: 26 KB per block instead of the 72 KB of
+// shifted copies, for 8 MMAs M128 N192 K16.
+constexpr int kWsKB = 128;                         // positions per block
+constexpr int kWsRows = kWsKB + 8;                 // window rows (taps reach 8 + 15 past a step's start)
+constexpr int kWsStages = 6;
+constexpr uint32_t kWsABytes = 17 * 1024;          // a1 window: 136 x 128 B, a whole number of 1024-byte patterns
+constexpr uint32_t kWsGBytes = 9 * 1024;           // g2 window: 136 x 64 B, rounded up to 1024
+constexpr uint32_t kWsStage = kWsABytes + kWsGBytes;
+constexpr int kWsSplit = 13;                       // 11 kernel rows x 13 = 143 CTAs
+constexpr int kWsN = 192;
+
+struct WsSmem {
+    uint64_t full[kWsStages], empty[kWsStages], acc_full, drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// MN-major shared-memory descriptor with a swizzle mode (2 = 128-byte, 4 = 64-byte).
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz)
+{
+    return sdesc(saddr, lbo, sbo) | ((uint64_t)swz << 61);
+}
+
+__global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
+                                                          int B, int P, int HP16, int plane_len,
+                                                          float* __restrict__ part, int* status)
+{
+    extern __shared__ uint8_t smem_dyn[];
+    uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    WsSmem* ss = reinterpret_cast<WsSmem*>(smem + kWsStages * kWsStage);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int dy = blockIdx.x % 11, split = blockIdx.x / 11;
+    const int nb_img = (HP16 + kWsKB - 1) / kWsKB;
+    const long long total = (long long)B * nb_img;
+    const long long blk0 = total * split / kWsSplit, blk1 = total * (split + 1) / kWsSplit;
+    const int u_begin = kPad * P + kPad;
+    const int off0 = (dy - 5) * P - 5;                 // a1 offset of column group s = 0
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            mbar_init(smem_u32(&ss->full[s]), 128);    // one cp.async arrival per loader thread
+            mbar_init(smem_u32(&ss->empty[s]), 1);
+        }
+        mbar_init(smem_u32(&ss->acc_full), 1);
+        mbar_init(smem_u32(&ss->drain), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&ss->tmem_base), 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+
+    if (warp >= 2) {
+        // ------------------------------------------------ loaders (then the epilogue)
+        const int t = threadIdx.x - 64;
+        for (long long k = blk0; k < blk1; ++k) {
+            const int st = (int)((k - blk0) % kWsStages), n = (int)((k - blk0) / kWsStages);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+            const int b = (int)(k / nb_img);
+            const int u0 = u_begin + (int)(k % nb_img) * kWsKB;
+            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + ((size_t)b * 8 * plane_len + (size_t)(u0 + off0)) * 16;
+            const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + ((size_t)b * 4 * plane_len + (size_t)(u0 - 8)) * 16;
+            const uint32_t dA = smem_u32(smem + st * kWsStage), dG = dA + kWsABytes;
+            // a1: row r = position u0 + off0 + r, chunk c (8 per row); g2: row r = position u0 - 8 + r, chunk c (4 per row)
+            for (int i = t; i < kWsRows * 8; i += 128) {
+                const int r = i >> 3, c = i & 7;
+                cp_async16(dA + r * 128 + ((c ^ (r & 7)) << 4), a1b + ((size_t)c * plane_len + r) * 16);
+            }
+            for (int i = t; i < kWsRows * 4; i += 128) {
+                const int r = i >> 2, c = i & 3;
+                cp_async16(dG + r * 64 + ((c ^ ((r >> 1) & 3)) << 4), g2b + ((size_t)c * plane_len + r) * 16);
+            }
+            cp_async_arrive(smem_u32(&ss->full[st]));
+        }
+        cp_async_wait_all();
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16_mn(128, kWsN);
+        bool first = true;
+        for (long long k = blk0; k < blk1; ++k) {
+            const int st = (int)((k - blk0) % kWsStages), n = (int)((k - blk0) / kWsStages);
+            if (!mbar_wait(smem_u32(&ss->full[st]), n & 1, status, &ss->abort_flag)) break;
+            fence_proxy_async();   // the windows were written by cp.async (generic proxy)
+            tc_fence_after();
+            const int u0 = u_begin + (int)(k % nb_img) * kWsKB;
+            const int nsteps = min(kWsKB, u_begin + HP16 - u0) / 16;
+            const uint32_t a0 = smem_u32(smem + st * kWsStage), g0 = a0 + kWsABytes;
+            for (int j = 0; j < nsteps; ++j) {
+                const uint64_t ad = sdesc_sw(g0 + (16 * j + 5) * 64, 64, 512, 4);
+                const uint64_t bd = sdesc_sw(a0 + (16 * j) * 128, 512, 1024, 2);
+                mma_bf16(tbase, ad, bd, idesc, first ? 0u : 1u);
+                first = false;
+            }
+            mma_commit(smem_u32(&ss->empty[st]));
+        }
+        // an empty range still produces a (zero) partial
+        mma_commit(smem_u32(&ss->acc_full));
+        mma_commit(smem_u32(&ss->drain));
+        mbar_wait_drain(smem_u32(&ss->drain), 0);
+    }
+    if (warp >= 2) {
+        const int q = warp % 4;
+        bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        tc_fence_after();
+        float* dst = part + ((size_t)blockIdx.x * 128 + q * 32 + lane) * kWsN;
+        const bool empty = blk1 <= blk0;
+        for (int c0 = 0; c0 < kWsN; c0 += 16) {
+            float v[16];
+            if (ok && !empty) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + c0, v);
+            else
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 256);
+    }
+}
+
+// dW[co][ci][dy][dx] = sum over splits of part[dy + 11 split][32 (3 - g) + co][64 s + ci], dx = 4 s + g,
+// in float64 in split order.  Consecutive threads take consecutive ci (contiguous partials).
+__global__ void wgrad2sw_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
+{
+    const int n = 32 * 64 * 121;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % 64, dx = (i / 64) % 11, dy = (i / (64 * 11)) % 11, co = i / (64 * 121);
+        const int s = dx / 4, g = dx % 4;
+        double acc = 0.0;
+        for (int k = 0; k < kWsSplit; ++k)
+            acc += (double)part[((size_t)(dy + 11 * k) * 128 + 32 * (3 - g) + co) * kWsN + 64 * s + ci];
+        dw[((co * 64 + ci) * 11 + dy) * 11 + dx] = (float)acc;
+    }
+}
+
 // Positions u that can carry a nonzero gradient: the data rows [5P+5, 5P+5+HP).
 size_t wgrad2_scratch_floats()
 {
     const size_t c64 = (size_t)WgCfg<64>::COLS * WgCfg<64>::SPLIT, c32 = (size_t)WgCfg<32>::COLS * WgCfg<32>::SPLIT;
-    return (c64 > c32 ? c64 : c32) * 128 * 256;
+    const size_t sw = (size_t)11 * kWsSplit * 128 * kWsN;
+    const size_t old = (c64 > c32 ? c64 : c32) * 128 * 256;
+    return old > sw ? old : sw;
 }
 
 template <int CIN>
@@ -582,7 +751,14 @@ static int wgrad_launch(const bf16* G, const bf16* A, int B, const Geo& g, float
 int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
               cudaStream_t st)
 {
-    return wgrad_launch<64>(G2, A1, B, g, part, dw, status, st);
+    const int HP16 = (g.HP + 15) / 16 * 16;
+    const size_t smem = 1024 + (size_t)kWsStages * kWsStage + sizeof(WsSmem);
+    DI_CUDA(cudaFuncSetAttribute(wgrad2sw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad2sw_kernel<<<11 * kWsSplit, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, part, status);
+    DI_LAUNCH_CHECK();
+    wgrad2sw_reduce_kernel<<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
 }
 
 int wgrad_hidden_tc(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
