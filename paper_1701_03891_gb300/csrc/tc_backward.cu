@@ -570,26 +570,37 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 // g = 3 - j, i.e. the g2 rows one position apart) is the g2 window from row
 // 16 k + 5 with LBO = 64 bytes (next slot) and SBO = 512 (next 8 positions);
 // the B operand (N = 192: column groups s = 0..2 x 64 channels, 4 positions
-// apart) is the a1 window from row 16 k with LBO = 512 and SBO = 1024.  One
-// MMA then covers the 12 taps (dy, 4 s + g) of a kernel row (tap 11 unused)
-// for 16 positions.
+// apart) is the a1 window from row 16 k + r P (kernel row dy0 + r) with
+// LBO = 512 and SBO = 1024.  One MMA covers the 12 taps (dy, 4 s + g) of a
+// kernel row (tap 11 unused) for 16 positions.
 //
-// Each CTA takes one kernel row dy (its column) and a contiguous run of
-// 128-position blocks (its split); per block it loads the two windows (136
-// rows each) with 16-byte cp.async from the four epilogue warps, which place
-// every chunk at its swizzled address: 26 KB per block instead of the 72 KB of
-// shifted copies, for 8 MMAs M128 N192 K16.
+// Each CTA takes ROWS consecutive kernel rows (its column; ROWS = 2 when two
+// windows' worth of a1 rows fit, one TMEM accumulator per row) and a run of
+// 128-position blocks (its split).  Per block the four epilogue warps load the
+// two windows with 16-byte cp.async, each chunk placed at its swizzled address
+// (the g2 window serves every row of the CTA): with ROWS = 2 at 64 x 64, 35 KB
+// per block for 16 MMAs M128 N192 K16, where the shifted copies took 72 KB for
+// 6 MMAs M128 N256 K16.
 constexpr int kWsKB = 128;                         // positions per block
-constexpr int kWsRows = kWsKB + 8;                 // window rows (taps reach 8 + 15 past a step's start)
-constexpr int kWsStages = 6;
-constexpr uint32_t kWsABytes = 17 * 1024;          // a1 window: 136 x 128 B, a whole number of 1024-byte patterns
+constexpr int kWsRows = kWsKB + 8;                 // g2 window rows; the a1 window adds (ROWS - 1) P
+constexpr int kWsMaxStages = 6;
 constexpr uint32_t kWsGBytes = 9 * 1024;           // g2 window: 136 x 64 B, rounded up to 1024
-constexpr uint32_t kWsStage = kWsABytes + kWsGBytes;
-constexpr int kWsSplit = 13;                       // 11 kernel rows x 13 = 143 CTAs
 constexpr int kWsN = 192;
 
+template <int ROWS>
+struct WsCfg {
+    static constexpr int COLS = (11 + ROWS - 1) / ROWS;
+    static constexpr int SPLIT = ROWS == 2 ? 24 : 13;   // 144 or 143 CTAs
+};
+
+// a1 window bytes (rows of 128 B, a whole number of 1024-byte swizzle patterns)
+__host__ __device__ inline uint32_t ws_abytes(int rows, int P)
+{
+    return ((uint32_t)(kWsRows + (rows - 1) * P) * 128u + 1023u) / 1024u * 1024u;
+}
+
 struct WsSmem {
-    uint64_t full[kWsStages], empty[kWsStages], acc_full, drain;
+    uint64_t full[kWsMaxStages], empty[kWsMaxStages], acc_full, drain;
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -600,23 +611,28 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, uint32_t lbo, uint3
     return sdesc(saddr, lbo, sbo) | ((uint64_t)swz << 61);
 }
 
+template <int ROWS>
 __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
-                                                          int B, int P, int HP16, int plane_len,
+                                                          int B, int P, int HP16, int plane_len, int nst,
                                                           float* __restrict__ part, int* status)
 {
+    using C = WsCfg<ROWS>;
     extern __shared__ uint8_t smem_dyn[];
     uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
-    WsSmem* ss = reinterpret_cast<WsSmem*>(smem + kWsStages * kWsStage);
+    const uint32_t abytes = ws_abytes(ROWS, P), stage = abytes + kWsGBytes;
+    WsSmem* ss = reinterpret_cast<WsSmem*>(smem + nst * stage);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int dy = blockIdx.x % 11, split = blockIdx.x / 11;
+    const int col = blockIdx.x % C::COLS, split = blockIdx.x / C::COLS;
+    const int dy0 = col * ROWS, nrows = min(ROWS, 11 - dy0);
+    const int arows = kWsRows + (nrows - 1) * P;       // a1 window rows of this CTA
     const int nb_img = (HP16 + kWsKB - 1) / kWsKB;
     const long long total = (long long)B * nb_img;
-    const long long blk0 = total * split / kWsSplit, blk1 = total * (split + 1) / kWsSplit;
+    const long long blk0 = total * split / C::SPLIT, blk1 = total * (split + 1) / C::SPLIT;
     const int u_begin = kPad * P + kPad;
-    const int off0 = (dy - 5) * P - 5;                 // a1 offset of column group s = 0
+    const int off0 = (dy0 - 5) * P - 5;                // a1 offset of kernel row dy0, column group s = 0
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kWsStages; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(smem_u32(&ss->full[s]), 128);    // one cp.async arrival per loader thread
             mbar_init(smem_u32(&ss->empty[s]), 1);
         }
@@ -626,7 +642,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(&ss->tmem_base), 256);
+        tmem_alloc(smem_u32(&ss->tmem_base), ROWS * 256);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -638,7 +654,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         // ------------------------------------------------ loaders (then the epilogue)
         const int t = threadIdx.x - 64;
         for (long long k = blk0; k < blk1; ++k) {
-            const int st = (int)((k - blk0) % kWsStages), n = (int)((k - blk0) / kWsStages);
+            const int st = (int)((k - blk0) % nst), n = (int)((k - blk0) / nst);
             bool ok = true;
             if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
@@ -646,9 +662,9 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
             const int u0 = u_begin + (int)(k % nb_img) * kWsKB;
             const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + ((size_t)b * 8 * plane_len + (size_t)(u0 + off0)) * 16;
             const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + ((size_t)b * 4 * plane_len + (size_t)(u0 - 8)) * 16;
-            const uint32_t dA = smem_u32(smem + st * kWsStage), dG = dA + kWsABytes;
+            const uint32_t dA = smem_u32(smem + st * stage), dG = dA + abytes;
             // a1: row r = position u0 + off0 + r, chunk c (8 per row); g2: row r = position u0 - 8 + r, chunk c (4 per row)
-            for (int i = t; i < kWsRows * 8; i += 128) {
+            for (int i = t; i < arows * 8; i += 128) {
                 const int r = i >> 3, c = i & 7;
                 cp_async16(dA + r * 128 + ((c ^ (r & 7)) << 4), a1b + ((size_t)c * plane_len + r) * 16);
             }
@@ -664,17 +680,22 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         const uint32_t idesc = idesc_bf16_mn(128, kWsN);
         bool first = true;
         for (long long k = blk0; k < blk1; ++k) {
-            const int st = (int)((k - blk0) % kWsStages), n = (int)((k - blk0) / kWsStages);
+            const int st = (int)((k - blk0) % nst), n = (int)((k - blk0) / nst);
             if (!mbar_wait(smem_u32(&ss->full[st]), n & 1, status, &ss->abort_flag)) break;
             fence_proxy_async();   // the windows were written by cp.async (generic proxy)
             tc_fence_after();
             const int u0 = u_begin + (int)(k % nb_img) * kWsKB;
             const int nsteps = min(kWsKB, u_begin + HP16 - u0) / 16;
-            const uint32_t a0 = smem_u32(smem + st * kWsStage), g0 = a0 + kWsABytes;
+            const uint32_t a0 = smem_u32(smem + st * stage), g0 = a0 + abytes;
             for (int j = 0; j < nsteps; ++j) {
                 const uint64_t ad = sdesc_sw(g0 + (16 * j + 5) * 64, 64, 512, 4);
-                const uint64_t bd = sdesc_sw(a0 + (16 * j) * 128, 512, 1024, 2);
-                mma_bf16(tbase, ad, bd, idesc, first ? 0u : 1u);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    if (r < nrows) {
+                        const uint64_t bd = sdesc_sw(a0 + (16 * j + r * P) * 128, 512, 1024, 2);
+                        mma_bf16(tbase + (uint32_t)(r * 256), ad, bd, idesc, first ? 0u : 1u);
+                    }
+                }
                 first = false;
             }
             mma_commit(smem_u32(&ss->empty[st]));
@@ -689,37 +710,42 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
         ok = __all_sync(0xffffffffu, ok);
         tc_fence_after();
-        float* dst = part + ((size_t)blockIdx.x * 128 + q * 32 + lane) * kWsN;
         const bool empty = blk1 <= blk0;
-        for (int c0 = 0; c0 < kWsN; c0 += 16) {
-            float v[16];
-            if (ok && !empty) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + c0, v);
-            else
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        for (int r = 0; r < nrows; ++r) {
+            float* dst = part + (((size_t)blockIdx.x * ROWS + r) * 128 + q * 32 + lane) * kWsN;
+            for (int c0 = 0; c0 < kWsN; c0 += 16) {
+                float v[16];
+                if (ok && !empty) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 256 + c0), v);
+                else
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
 #pragma unroll
-            for (int i = 0; i < 16; i += 4)
-                *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 256);
+        tmem_dealloc(tbase, ROWS * 256);
     }
 }
 
-// dW[co][ci][dy][dx] = sum over splits of part[dy + 11 split][32 (3 - g) + co][64 s + ci], dx = 4 s + g,
-// in float64 in split order.  Consecutive threads take consecutive ci (contiguous partials).
+// dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][row][32 (3 - g) + co][64 s + ci],
+// col = dy / ROWS, row = dy % ROWS, dx = 4 s + g, in float64 in split order.
+// Consecutive threads take consecutive ci (contiguous partials).
+template <int ROWS>
 __global__ void wgrad2sw_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
 {
+    using C = WsCfg<ROWS>;
     const int n = 32 * 64 * 121;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int ci = i % 64, dx = (i / 64) % 11, dy = (i / (64 * 11)) % 11, co = i / (64 * 121);
-        const int s = dx / 4, g = dx % 4;
+        const int s = dx / 4, g = dx % 4, col = dy / ROWS, row = dy % ROWS;
         double acc = 0.0;
-        for (int k = 0; k < kWsSplit; ++k)
-            acc += (double)part[((size_t)(dy + 11 * k) * 128 + 32 * (3 - g) + co) * kWsN + 64 * s + ci];
+        for (int k = 0; k < C::SPLIT; ++k)
+            acc += (double)part[((((size_t)(col + C::COLS * k) * ROWS + row) * 128) + 32 * (3 - g) + co) * kWsN + 64 * s + ci];
         dw[((co * 64 + ci) * 11 + dy) * 11 + dx] = (float)acc;
     }
 }
@@ -728,7 +754,9 @@ __global__ void wgrad2sw_reduce_kernel(const float* __restrict__ part, float* __
 size_t wgrad2_scratch_floats()
 {
     const size_t c64 = (size_t)WgCfg<64>::COLS * WgCfg<64>::SPLIT, c32 = (size_t)WgCfg<32>::COLS * WgCfg<32>::SPLIT;
-    const size_t sw = (size_t)11 * kWsSplit * 128 * kWsN;
+    const size_t sw1 = (size_t)WsCfg<1>::COLS * WsCfg<1>::SPLIT * 128 * kWsN;
+    const size_t sw2 = (size_t)WsCfg<2>::COLS * WsCfg<2>::SPLIT * 2 * 128 * kWsN;
+    const size_t sw = sw1 > sw2 ? sw1 : sw2;
     const size_t old = (c64 > c32 ? c64 : c32) * 128 * 256;
     return old > sw ? old : sw;
 }
@@ -748,17 +776,38 @@ static int wgrad_launch(const bf16* G, const bf16* A, int B, const Geo& g, float
     return DEEPINV_OK;
 }
 
+template <int ROWS>
+static int wgrad2sw_launch(const bf16* G2, const bf16* A1, int B, const Geo& g, int nst, float* part, float* dw,
+                           int* status, cudaStream_t st)
+{
+    using C = WsCfg<ROWS>;
+    const int HP16 = (g.HP + 15) / 16 * 16;
+    const size_t smem = 1024 + (size_t)nst * (ws_abytes(ROWS, g.P) + kWsGBytes) + sizeof(WsSmem);
+    DI_CUDA(cudaFuncSetAttribute(wgrad2sw_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad2sw_kernel<ROWS><<<C::COLS * C::SPLIT, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, nst, part, status);
+    DI_LAUNCH_CHECK();
+    wgrad2sw_reduce_kernel<ROWS><<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+// Stages of the swizzled-window kernel that fit in shared memory (0: none).
+static int ws_stages(int rows, int P)
+{
+    const size_t per = (size_t)ws_abytes(rows, P) + kWsGBytes;
+    const size_t avail = 227 * 1024 - 1024 - sizeof(WsSmem);
+    const size_t n = avail / per;
+    return (int)(n > (size_t)kWsMaxStages ? kWsMaxStages : n);
+}
+
 int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, float* dw, int* status,
               cudaStream_t st)
 {
-    const int HP16 = (g.HP + 15) / 16 * 16;
-    const size_t smem = 1024 + (size_t)kWsStages * kWsStage + sizeof(WsSmem);
-    DI_CUDA(cudaFuncSetAttribute(wgrad2sw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad2sw_kernel<<<11 * kWsSplit, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, part, status);
-    DI_LAUNCH_CHECK();
-    wgrad2sw_reduce_kernel<<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
+    // two kernel rows per CTA while three stages of their window fit, else one
+    // row per CTA (its window does not depend on the image width)
+    const int n2 = ws_stages(2, g.P);
+    if (n2 >= 3) return wgrad2sw_launch<2>(G2, A1, B, g, n2, part, dw, status, st);
+    return wgrad2sw_launch<1>(G2, A1, B, g, ws_stages(1, g.P), part, dw, status, st);
 }
 
 int wgrad_hidden_tc(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
