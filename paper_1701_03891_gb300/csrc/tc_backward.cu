@@ -143,232 +143,13 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// ---------------------------------------------------------------- conv2 weight gradient
-// dW2[co][ci][dy][4 s + g] = sum_u' G[u' - g][co] A1[u' + (dy - 5) P + 4 s - 5][ci]
-// as MMAs with K = 16 plane positions u', both operands MN-major (channels
-// contiguous in 16-byte chunks, positions 16 bytes apart -- the planes' own
-// layout): A = 128 rows (tap slot g, filter co) read from four windows of the
-// g2 plane shifted by g; B = up to 256 rows (kernel-row group p = (dy, s),
-// channel ci) read from 256 / CIN windows of the input plane (a1: CIN = 64,
-// four groups; a hidden layer's input: CIN = 32, eight groups).  The 33
-// groups p make WgCfg::COLS CTA columns; positions are split over
-// WgCfg::SPLIT CTAs each; every CTA leaves a 128 x 256 float32 partial,
-// summed in float64 in a fixed order.
-//
-// Loading is the limit (every stage pulls 48 small shifted windows from L2):
-// the first half of a stage's windows go by 1-D bulk copy from warp 0, the
-// other half by 16-byte cp.async from the four epilogue warps (idle until
-// the end), both completing the stage's barrier.  Measured at 64 x 64, batch
-// 256: this split with 3 stages of 96 positions beats bulk copies alone
-// (2 x 128: backward 1.95 ms; 3 x 96: 2.28 ms) at 1.87 ms, and 1/3 or 2/3 bulk.
-constexpr int kWgKB = 96;           // positions per stage
-constexpr int kWgStages = 3;
-constexpr uint32_t kWgABytes = 16 * kWgKB * 16;     // 16 M-groups
-constexpr uint32_t kWgBBytes = 32 * kWgKB * 16;     // 32 N-groups
-
-template <int CIN>
-struct WgCfg {
-    static constexpr int CPG = CIN / 8;                      // 16-byte chunks per kernel-row group
-    static constexpr int GPC = 256 / CIN;                    // kernel-row groups per CTA column
-    static constexpr int COLS = (33 + GPC - 1) / GPC;        // 9 (CIN = 64) or 5 (CIN = 32)
-    static constexpr int SPLIT = CIN == 64 ? 16 : 30;        // 144 or 150 CTAs
-};
-
-struct WgSmem {
-    uint64_t full[kWgStages], empty[kWgStages], acc_full, drain;
-    uint32_t tmem_base;
-    int abort_flag;
-};
-
+// Instruction descriptor of tcgen05.mma.kind::f16 with both operands MN-major
+// (bits 15 and 16), bf16 in, float32 out.
 __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
-
-template <int CIN>
-__global__ void __launch_bounds__(192, 1) wgrad2_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
-                                                        int B, int P, int HP16, int plane_len,
-                                                        float* __restrict__ part, int* status)
-{
-    using C = WgCfg<CIN>;
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* sA = smem_raw;                                        // [stage][16 groups][KB][16 B]
-    uint8_t* sB = smem_raw + kWgStages * kWgABytes;                // [stage][32 groups][KB][16 B]
-    WgSmem* ss = reinterpret_cast<WgSmem*>(sB + kWgStages * kWgBBytes);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int col = blockIdx.x % C::COLS, split = blockIdx.x / C::COLS;
-    const int ngroups = min(C::GPC, 33 - col * C::GPC);
-    const int NB = ngroups * CIN;
-    const int ncopy = 16 + C::CPG * ngroups;
-    const int nbulk = ncopy / 2;                 // windows [0, nbulk) by bulk copy, the rest by cp.async
-    const int nb_img = (HP16 + kWgKB - 1) / kWgKB;
-    const long long total = (long long)B * nb_img;
-    const long long blk0 = total * split / C::SPLIT, blk1 = total * (split + 1) / C::SPLIT;
-    const int u_begin = kPad * P + kPad;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kWgStages; ++s) {
-            mbar_init(smem_u32(&ss->full[s]), 1 + 128);    // producer (bulk bytes) + 128 cp.async threads
-            mbar_init(smem_u32(&ss->empty[s]), 1);
-        }
-        mbar_init(smem_u32(&ss->acc_full), 1);
-        mbar_init(smem_u32(&ss->drain), 1);
-        ss->abort_flag = 0;
-        fence_mbar_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(smem_u32(&ss->tmem_base), 256);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = ss->tmem_base;
-
-    if (warp == 0) {
-        // producer warp: lane 0 waits and arms the stage barrier, then the 16 + CPG ngroups
-        // window copies of the stage are issued by all 32 lanes (small bulk copies are
-        // limited by their issue rate per thread)
-        int parity[kWgStages];
-        for (int s = 0; s < kWgStages; ++s) parity[s] = -1;
-        for (long long k = blk0; k < blk1; ++k) {
-            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
-            const int b = (int)(k / nb_img);
-            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
-            const int npos = min(kWgKB, u_begin + HP16 - u0);
-            const uint32_t bytes = (uint32_t)npos * 16;
-            if (lane == 0 && ok) mbar_arrive_expect_tx(smem_u32(&ss->full[st]), (uint32_t)nbulk * bytes);
-            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-            parity[st] = n & 1;
-            const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
-            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * C::CPG * plane_len * 16;
-            uint8_t* dA = sA + st * kWgABytes;
-            uint8_t* dB = sB + st * kWgBBytes;
-            for (int c = lane; c < nbulk; c += 32) {
-                if (c < 16) {
-                    const int g = c / 4, c4 = c % 4;
-                    bulk_g2s(smem_u32(dA + (g * 4 + c4) * kWgKB * 16),
-                             g2b + ((size_t)c4 * plane_len + u0 - g) * 16, bytes, smem_u32(&ss->full[st]));
-                } else {
-                    const int pl = (c - 16) / C::CPG, c8 = (c - 16) % C::CPG;
-                    const int p = col * C::GPC + pl, dy = p / 3, s = p % 3;
-                    const int off = (dy - 5) * P + 4 * s - 5;
-                    bulk_g2s(smem_u32(dB + (pl * C::CPG + c8) * kWgKB * 16),
-                             a1b + ((size_t)c8 * plane_len + u0 + off) * 16, bytes, smem_u32(&ss->full[st]));
-                }
-            }
-        }
-        if (lane == 0)
-            for (int s = 0; s < kWgStages; ++s)
-                if (parity[s] >= 0) {
-                    const unsigned long long t0 = globaltimer();
-                    while (!mbar_try_wait(smem_u32(&ss->full[s]), parity[s]) && globaltimer() - t0 < 1000000000ull) {}
-                }
-    } else if (warp >= 2) {
-        // loaders of windows [nbulk, ncopy): one warp per window, 16 bytes per lane per copy
-        const int lw = warp - 2;
-        for (long long k = blk0; k < blk1; ++k) {
-            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(smem_u32(&ss->empty[st]), (n & 1) ^ 1, status, &ss->abort_flag);
-            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-            const int b = (int)(k / nb_img);
-            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
-            const int npos = min(kWgKB, u_begin + HP16 - u0);
-            const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + (size_t)b * 4 * plane_len * 16;
-            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + (size_t)b * C::CPG * plane_len * 16;
-            const uint32_t dA = smem_u32(sA + st * kWgABytes), dB = smem_u32(sB + st * kWgBBytes);
-            for (int c = nbulk + lw; c < ncopy; c += 4) {
-                uint32_t dst;
-                const uint8_t* src;
-                if (c < 16) {
-                    const int g = c / 4, c4 = c % 4;
-                    dst = dA + (g * 4 + c4) * kWgKB * 16;
-                    src = g2b + ((size_t)c4 * plane_len + u0 - g) * 16;
-                } else {
-                    const int pl = (c - 16) / C::CPG, c8 = (c - 16) % C::CPG;
-                    const int p = col * C::GPC + pl, dy = p / 3, s = p % 3;
-                    dst = dB + (pl * C::CPG + c8) * kWgKB * 16;
-                    src = a1b + ((size_t)c8 * plane_len + u0 + (dy - 5) * P + 4 * s - 5) * 16;
-                }
-                for (int i = lane; i < npos; i += 32) cp_async16(dst + i * 16, src + (size_t)i * 16);
-            }
-            cp_async_arrive(smem_u32(&ss->full[st]));
-        }
-        cp_async_wait_all();
-    }
-    if (warp == 1 && lane == 0) {
-        const uint32_t idesc = idesc_bf16_mn(128, NB);
-        bool first = true;
-        for (long long k = blk0; k < blk1; ++k) {
-            const int st = (int)((k - blk0) % kWgStages), n = (int)((k - blk0) / kWgStages);
-            if (!mbar_wait(smem_u32(&ss->full[st]), n & 1, status, &ss->abort_flag)) break;
-            fence_proxy_async();   // part of the stage was written by cp.async (generic proxy)
-            tc_fence_after();
-            const int u0 = u_begin + (int)(k % nb_img) * kWgKB;
-            const int nsteps = min(kWgKB, u_begin + HP16 - u0) / 16;
-            const uint32_t a0 = smem_u32(sA + st * kWgABytes), b0 = smem_u32(sB + st * kWgBBytes);
-            for (int ks = 0; ks < nsteps; ++ks) {
-                const uint64_t ad = sdesc(a0 + ks * 256, 128, kWgKB * 16);
-                const uint64_t bd = sdesc(b0 + ks * 256, 128, kWgKB * 16);
-                mma_bf16(tbase, ad, bd, idesc, first ? 0u : 1u);
-                first = false;
-            }
-            mma_commit(smem_u32(&ss->empty[st]));
-        }
-        // an empty range still produces a (zero) partial
-        mma_commit(smem_u32(&ss->acc_full));
-        mma_commit(smem_u32(&ss->drain));
-        const unsigned long long t0 = globaltimer();
-        while (!mbar_try_wait(smem_u32(&ss->drain), 0) && globaltimer() - t0 < 1000000000ull) {}
-    }
-    if (warp >= 2) {
-        const int q = warp % 4;
-        bool ok = mbar_wait(smem_u32(&ss->acc_full), 0, status, &ss->abort_flag);
-        ok = __all_sync(0xffffffffu, ok);
-        tc_fence_after();
-        float* dst = part + ((size_t)blockIdx.x * 128 + q * 32 + lane) * 256;
-        const bool empty = blk1 <= blk0;
-        for (int c0 = 0; c0 < 256; c0 += 16) {
-            float v[16];
-            if (ok && !empty && c0 < NB) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + c0, v);
-            else
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; i += 4)
-                *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tbase, 256);
-    }
-}
-
-// dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][32 g + co][CIN pl + ci],
-// with p = GPC col + pl = 3 dy + s and dx = 4 s + g (< 11).
-// Consecutive threads take consecutive input channels ci, so that the partials
-// they read are contiguous.
-template <int CIN>
-__global__ void wgrad2_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
-{
-    using C = WgCfg<CIN>;
-    const int n = 32 * CIN * 121;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int ci = i % CIN, dx = (i / CIN) % 11, dy = (i / (CIN * 11)) % 11, co = i / (CIN * 121);
-        const int s = dx / 4, g = dx % 4, p = dy * 3 + s, col = p / C::GPC, pl = p % C::GPC;
-        double acc = 0.0;
-        for (int k = 0; k < C::SPLIT; ++k)
-            acc += (double)part[((size_t)(col + C::COLS * k) * 128 + g * 32 + co) * 256 + pl * CIN + ci];
-        dw[((co * CIN + ci) * 11 + dy) * 11 + dx] = (float)acc;
-    }
-}
-
 
 // ---------------------------------------------------------------- conv1 / conv3 weight gradients
 // D[t][j] = sum_u S[u + sgn off(t)] C[u][j], off(t) = (dy - 5) P + (dx - 5) for
@@ -557,11 +338,13 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
     return DEEPINV_OK;
 }
 
-// ---------------------------------------------------------------- conv2 weight gradient, swizzled windows
-// The same contraction as wgrad2_kernel<64>, dW2[co][ci][dy][4 s + g] =
-// sum_u G[u - g][co] A1[u + (dy - 5) P + 4 s - 5][ci], with each shifted
-// window read straight out of ONE window per plane instead of one copy per
-// shift.  The windows are stored channel-contiguous per position, with the
+// ---------------------------------------------------------------- conv2 / hidden-layer weight gradients
+// dW2[co][ci][dy][4 s + g] = sum_u G[u - g][co] A1[u + (dy - 5) P + 4 s - 5][ci]
+// over plane positions u (G is zero off the data positions), as MMAs with
+// K = 16 positions whose operands are shifted windows of the two planes: the
+// tap phase g shifts G, the kernel row and column group (dy, s) shift A1.
+// Every shifted window is read straight out of ONE window per plane instead of
+// one copy per shift.  The windows are stored channel-contiguous per position, with the
 // tensor core's swizzles: the a1 window as 128-byte rows (64 channels, 16-byte
 // chunk c of row r at chunk c ^ (r % 8)), the g2 window as 64-byte rows (32
 // channels, chunk c at c ^ ((r / 2) % 4)).  Both are MN-major operands whose
@@ -574,29 +357,37 @@ int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* pa
 // LBO = 512 and SBO = 1024.  One MMA covers the 12 taps (dy, 4 s + g) of a
 // kernel row (tap 11 unused) for 16 positions.
 //
-// Each CTA takes ROWS consecutive kernel rows (its column; ROWS = 2 when two
-// windows' worth of a1 rows fit, one TMEM accumulator per row) and a run of
-// 128-position blocks (its split).  Per block the four epilogue warps load the
-// two windows with 16-byte cp.async, each chunk placed at its swizzled address
-// (the g2 window serves every row of the CTA): with ROWS = 2 at 64 x 64, 35 KB
-// per block for 16 MMAs M128 N192 K16, where the shifted copies took 72 KB for
-// 6 MMAs M128 N256 K16.
+// Each CTA takes ROWS consecutive kernel rows (its column; ROWS = 2 for conv2
+// and 4 for a hidden layer when three stages of the window fit, one TMEM
+// accumulator per row) and a run of 128-position blocks (its split).  Per block
+// the four epilogue warps load the two windows with 16-byte cp.async, each
+// chunk placed at its swizzled address (the g2 window serves every row of the
+// CTA): for conv2 at 64 x 64, 35 KB per block for 16 MMAs M128 N192 K16.  A
+// copy of every shifted window (one 1-D bulk copy or cp.async run per window)
+// had taken 72 KB for 6 MMAs M128 N256 K16, paced by the copies.
 constexpr int kWsKB = 128;                         // positions per block
 constexpr int kWsRows = kWsKB + 8;                 // g2 window rows; the a1 window adds (ROWS - 1) P
 constexpr int kWsMaxStages = 6;
 constexpr uint32_t kWsGBytes = 9 * 1024;           // g2 window: 136 x 64 B, rounded up to 1024
-constexpr int kWsN = 192;
 
-template <int ROWS>
+// CIN = 64: conv2 (a1 window rows of 128 bytes, 128-byte swizzle, N = 192).
+// CIN = 32: a hidden layer (its input plane as 64-byte rows, 64-byte swizzle,
+// N = 96; up to four kernel rows per CTA).
+template <int CIN, int ROWS>
 struct WsCfg {
+    static constexpr int N = 3 * CIN;                    // column groups s = 0..2 x CIN channels
+    static constexpr int RB = 2 * CIN;                   // bytes per window row of the input plane
+    static constexpr int CPG = CIN / 8;                  // 16-byte chunks per row
+    static constexpr uint32_t SWZ = CIN == 64 ? 2 : 4;   // 128- or 64-byte swizzle
+    static constexpr int TCOLS = N <= 128 ? 128 : 256;   // TMEM columns per kernel row
     static constexpr int COLS = (11 + ROWS - 1) / ROWS;
-    static constexpr int SPLIT = ROWS == 2 ? 24 : 13;   // 144 or 143 CTAs
+    static constexpr int SPLIT = 144 / COLS;             // 143 or 144 CTAs
 };
 
-// a1 window bytes (rows of 128 B, a whole number of 1024-byte swizzle patterns)
-__host__ __device__ inline uint32_t ws_abytes(int rows, int P)
+// input-window bytes (a whole number of 1024-byte swizzle patterns)
+__host__ __device__ inline uint32_t ws_abytes(int rows, int P, int rb)
 {
-    return ((uint32_t)(kWsRows + (rows - 1) * P) * 128u + 1023u) / 1024u * 1024u;
+    return ((uint32_t)(kWsRows + (rows - 1) * P) * (uint32_t)rb + 1023u) / 1024u * 1024u;
 }
 
 struct WsSmem {
@@ -611,15 +402,15 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr, uint32_t lbo, uint3
     return sdesc(saddr, lbo, sbo) | ((uint64_t)swz << 61);
 }
 
-template <int ROWS>
+template <int CIN, int ROWS>
 __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict__ G2, const bf16* __restrict__ A1,
                                                           int B, int P, int HP16, int plane_len, int nst,
                                                           float* __restrict__ part, int* status)
 {
-    using C = WsCfg<ROWS>;
+    using C = WsCfg<CIN, ROWS>;
     extern __shared__ uint8_t smem_dyn[];
     uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
-    const uint32_t abytes = ws_abytes(ROWS, P), stage = abytes + kWsGBytes;
+    const uint32_t abytes = ws_abytes(ROWS, P, C::RB), stage = abytes + kWsGBytes;
     WsSmem* ss = reinterpret_cast<WsSmem*>(smem + nst * stage);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int col = blockIdx.x % C::COLS, split = blockIdx.x / C::COLS;
@@ -642,7 +433,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(&ss->tmem_base), ROWS * 256);
+        tmem_alloc(smem_u32(&ss->tmem_base), ROWS * C::TCOLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -660,13 +451,16 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
             if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
             const int b = (int)(k / nb_img);
             const int u0 = u_begin + (int)(k % nb_img) * kWsKB;
-            const uint8_t* a1b = reinterpret_cast<const uint8_t*>(A1) + ((size_t)b * 8 * plane_len + (size_t)(u0 + off0)) * 16;
+            const uint8_t* a1b =
+                reinterpret_cast<const uint8_t*>(A1) + ((size_t)b * C::CPG * plane_len + (size_t)(u0 + off0)) * 16;
             const uint8_t* g2b = reinterpret_cast<const uint8_t*>(G2) + ((size_t)b * 4 * plane_len + (size_t)(u0 - 8)) * 16;
             const uint32_t dA = smem_u32(smem + st * stage), dG = dA + abytes;
-            // a1: row r = position u0 + off0 + r, chunk c (8 per row); g2: row r = position u0 - 8 + r, chunk c (4 per row)
-            for (int i = t; i < arows * 8; i += 128) {
-                const int r = i >> 3, c = i & 7;
-                cp_async16(dA + r * 128 + ((c ^ (r & 7)) << 4), a1b + ((size_t)c * plane_len + r) * 16);
+            // input: row r = position u0 + off0 + r, chunk c (CPG per row); g2: row r = position
+            // u0 - 8 + r, chunk c (4 per row)
+            for (int i = t; i < arows * C::CPG; i += 128) {
+                const int r = i / C::CPG, c = i % C::CPG;
+                const int pc = CIN == 64 ? (c ^ (r & 7)) : (c ^ ((r >> 1) & 3));
+                cp_async16(dA + r * C::RB + (pc << 4), a1b + ((size_t)c * plane_len + r) * 16);
             }
             for (int i = t; i < kWsRows * 4; i += 128) {
                 const int r = i >> 2, c = i & 3;
@@ -677,7 +471,7 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         cp_async_wait_all();
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_bf16_mn(128, kWsN);
+        const uint32_t idesc = idesc_bf16_mn(128, C::N);
         bool first = true;
         for (long long k = blk0; k < blk1; ++k) {
             const int st = (int)((k - blk0) % nst), n = (int)((k - blk0) / nst);
@@ -692,8 +486,8 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     if (r < nrows) {
-                        const uint64_t bd = sdesc_sw(a0 + (16 * j + r * P) * 128, 512, 1024, 2);
-                        mma_bf16(tbase + (uint32_t)(r * 256), ad, bd, idesc, first ? 0u : 1u);
+                        const uint64_t bd = sdesc_sw(a0 + (16 * j + r * P) * C::RB, 4 * C::RB, 8 * C::RB, C::SWZ);
+                        mma_bf16(tbase + (uint32_t)(r * C::TCOLS), ad, bd, idesc, first ? 0u : 1u);
                     }
                 }
                 first = false;
@@ -712,10 +506,10 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
         tc_fence_after();
         const bool empty = blk1 <= blk0;
         for (int r = 0; r < nrows; ++r) {
-            float* dst = part + (((size_t)blockIdx.x * ROWS + r) * 128 + q * 32 + lane) * kWsN;
-            for (int c0 = 0; c0 < kWsN; c0 += 16) {
+            float* dst = part + (((size_t)blockIdx.x * ROWS + r) * 128 + q * 32 + lane) * C::N;
+            for (int c0 = 0; c0 < C::N; c0 += 16) {
                 float v[16];
-                if (ok && !empty) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 256 + c0), v);
+                if (ok && !empty) tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * C::TCOLS + c0), v);
                 else
                     for (int i = 0; i < 16; ++i) v[i] = 0.f;
 #pragma unroll
@@ -728,73 +522,62 @@ __global__ void __launch_bounds__(192, 1) wgrad2sw_kernel(const bf16* __restrict
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, ROWS * 256);
+        tmem_dealloc(tbase, ROWS * C::TCOLS);
     }
 }
 
-// dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][row][32 (3 - g) + co][64 s + ci],
+// dW[co][ci][dy][dx] = sum over splits of part[col + COLS split][row][32 (3 - g) + co][CIN s + ci],
 // col = dy / ROWS, row = dy % ROWS, dx = 4 s + g, in float64 in split order.
 // Consecutive threads take consecutive ci (contiguous partials).
-template <int ROWS>
+template <int CIN, int ROWS>
 __global__ void wgrad2sw_reduce_kernel(const float* __restrict__ part, float* __restrict__ dw)
 {
-    using C = WsCfg<ROWS>;
-    const int n = 32 * 64 * 121;
+    using C = WsCfg<CIN, ROWS>;
+    const int n = 32 * CIN * 121;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int ci = i % 64, dx = (i / 64) % 11, dy = (i / (64 * 11)) % 11, co = i / (64 * 121);
+        const int ci = i % CIN, dx = (i / CIN) % 11, dy = (i / (CIN * 11)) % 11, co = i / (CIN * 121);
         const int s = dx / 4, g = dx % 4, col = dy / ROWS, row = dy % ROWS;
         double acc = 0.0;
         for (int k = 0; k < C::SPLIT; ++k)
-            acc += (double)part[((((size_t)(col + C::COLS * k) * ROWS + row) * 128) + 32 * (3 - g) + co) * kWsN + 64 * s + ci];
-        dw[((co * 64 + ci) * 11 + dy) * 11 + dx] = (float)acc;
+            acc += (double)part[((((size_t)(col + C::COLS * k) * ROWS + row) * 128) + 32 * (3 - g) + co) * C::N +
+                                CIN * s + ci];
+        dw[((co * CIN + ci) * 11 + dy) * 11 + dx] = (float)acc;
     }
 }
 
 // Positions u that can carry a nonzero gradient: the data rows [5P+5, 5P+5+HP).
 size_t wgrad2_scratch_floats()
 {
-    const size_t c64 = (size_t)WgCfg<64>::COLS * WgCfg<64>::SPLIT, c32 = (size_t)WgCfg<32>::COLS * WgCfg<32>::SPLIT;
-    const size_t sw1 = (size_t)WsCfg<1>::COLS * WsCfg<1>::SPLIT * 128 * kWsN;
-    const size_t sw2 = (size_t)WsCfg<2>::COLS * WsCfg<2>::SPLIT * 2 * 128 * kWsN;
-    const size_t sw = sw1 > sw2 ? sw1 : sw2;
-    const size_t old = (c64 > c32 ? c64 : c32) * 128 * 256;
-    return old > sw ? old : sw;
+    size_t sw = 0;
+    auto upd = [&](size_t v) { if (v > sw) sw = v; };
+    upd((size_t)WsCfg<64, 1>::COLS * WsCfg<64, 1>::SPLIT * 1 * 128 * WsCfg<64, 1>::N);
+    upd((size_t)WsCfg<64, 2>::COLS * WsCfg<64, 2>::SPLIT * 2 * 128 * WsCfg<64, 2>::N);
+    upd((size_t)WsCfg<32, 1>::COLS * WsCfg<32, 1>::SPLIT * 1 * 128 * WsCfg<32, 1>::N);
+    upd((size_t)WsCfg<32, 4>::COLS * WsCfg<32, 4>::SPLIT * 4 * 128 * WsCfg<32, 4>::N);
+    return sw;
 }
 
-template <int CIN>
-static int wgrad_launch(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
-                        cudaStream_t st)
-{
-    using C = WgCfg<CIN>;
-    const int HP16 = (g.HP + 15) / 16 * 16;
-    const size_t smem = (size_t)kWgStages * (kWgABytes + kWgBBytes) + sizeof(WgSmem) + 16;
-    DI_CUDA(cudaFuncSetAttribute(wgrad2_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad2_kernel<CIN><<<C::COLS * C::SPLIT, 192, smem, st>>>(G, A, B, g.P, HP16, g.plane, part, status);
-    DI_LAUNCH_CHECK();
-    wgrad2_reduce_kernel<CIN><<<grid_for(32 * CIN * 121), 256, 0, st>>>(part, dw);
-    DI_LAUNCH_CHECK();
-    return DEEPINV_OK;
-}
 
-template <int ROWS>
+template <int CIN, int ROWS>
 static int wgrad2sw_launch(const bf16* G2, const bf16* A1, int B, const Geo& g, int nst, float* part, float* dw,
                            int* status, cudaStream_t st)
 {
-    using C = WsCfg<ROWS>;
+    using C = WsCfg<CIN, ROWS>;
     const int HP16 = (g.HP + 15) / 16 * 16;
-    const size_t smem = 1024 + (size_t)nst * (ws_abytes(ROWS, g.P) + kWsGBytes) + sizeof(WsSmem);
-    DI_CUDA(cudaFuncSetAttribute(wgrad2sw_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    wgrad2sw_kernel<ROWS><<<C::COLS * C::SPLIT, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, nst, part, status);
+    const size_t smem = 1024 + (size_t)nst * (ws_abytes(ROWS, g.P, C::RB) + kWsGBytes) + sizeof(WsSmem);
+    DI_CUDA(cudaFuncSetAttribute(wgrad2sw_kernel<CIN, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wgrad2sw_kernel<CIN, ROWS><<<C::COLS * C::SPLIT, 192, smem, st>>>(G2, A1, B, g.P, HP16, g.plane, nst, part,
+                                                                      status);
     DI_LAUNCH_CHECK();
-    wgrad2sw_reduce_kernel<ROWS><<<grid_for(32 * 64 * 121), 256, 0, st>>>(part, dw);
+    wgrad2sw_reduce_kernel<CIN, ROWS><<<grid_for(32 * CIN * 121), 256, 0, st>>>(part, dw);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
 
 // Stages of the swizzled-window kernel that fit in shared memory (0: none).
-static int ws_stages(int rows, int P)
+static int ws_stages(int rows, int P, int rb)
 {
-    const size_t per = (size_t)ws_abytes(rows, P) + kWsGBytes;
+    const size_t per = (size_t)ws_abytes(rows, P, rb) + kWsGBytes;
     const size_t avail = 227 * 1024 - 1024 - sizeof(WsSmem);
     const size_t n = avail / per;
     return (int)(n > (size_t)kWsMaxStages ? kWsMaxStages : n);
@@ -805,15 +588,19 @@ int wgrad2_tc(const bf16* G2, const bf16* A1, int B, const Geo& g, float* part, 
 {
     // two kernel rows per CTA while three stages of their window fit, else one
     // row per CTA (its window does not depend on the image width)
-    const int n2 = ws_stages(2, g.P);
-    if (n2 >= 3) return wgrad2sw_launch<2>(G2, A1, B, g, n2, part, dw, status, st);
-    return wgrad2sw_launch<1>(G2, A1, B, g, ws_stages(1, g.P), part, dw, status, st);
+    const int n2 = ws_stages(2, g.P, 128);
+    if (n2 >= 3) return wgrad2sw_launch<64, 2>(G2, A1, B, g, n2, part, dw, status, st);
+    return wgrad2sw_launch<64, 1>(G2, A1, B, g, ws_stages(1, g.P, 128), part, dw, status, st);
 }
 
 int wgrad_hidden_tc(const bf16* G, const bf16* A, int B, const Geo& g, float* part, float* dw, int* status,
                     cudaStream_t st)
 {
-    return wgrad_launch<32>(G, A, B, g, part, dw, status, st);
+    // four kernel rows per CTA (TMEM: 4 x 128 columns) while three stages fit,
+    // else one
+    const int n4 = ws_stages(4, g.P, 64);
+    if (n4 >= 3) return wgrad2sw_launch<32, 4>(G, A, B, g, n4, part, dw, status, st);
+    return wgrad2sw_launch<32, 1>(G, A, B, g, ws_stages(1, g.P, 64), part, dw, status, st);
 }
 
 size_t tapwgrad_scratch_floats() { return (size_t)kTwCtas * 128 * 64; }
