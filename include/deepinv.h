@@ -276,7 +276,9 @@ int deepinv_get_params(const deepinv_net* net, float* const w[], float* const b[
  * of the network whose oldest request has waited longest, and runs them as one
  * batch on that stream, so batches of different networks (image sizes, M/N)
  * overlap on the device and requests that arrive while others run join the
- * next batch.  Each batch needs a workspace of that network for max_batch
+ * next batch.  The scheduler never holds the lock that submission and
+ * harvest take while it copies data, allocates or enqueues work.  Each batch
+ * needs a workspace of that network for max_batch
  * images; workspaces are kept for reuse and count against the HBM budget,
  * idle ones of other networks are released when a new one does not fit, and
  * a batch waits while its workspace does not fit; requests of a network whose
@@ -309,7 +311,10 @@ int deepinv_serve_open(size_t hbm_budget_bytes, int max_streams, int max_batch, 
 /* Register a network (not owned; it must outlive the server and must not be
  * used by the caller while the server runs).  All networks of a server live
  * on one device.  Add networks before the first request; returns
- * DEEPINV_EBUSY while requests are in flight. */
+ * DEEPINV_EBUSY while requests are in flight.  Synchronously allocates (and
+ * zeroes) up to max_streams workspaces for the network while they fit in the
+ * budget, so that batches do not wait on allocations later; the device's
+ * default stream-ordered memory pool is set to keep released memory. */
 int deepinv_serve_add_net(deepinv_server* s, deepinv_net* net, int* net_id);
 
 /* Submit n_in requests (copied; n_in may be 0), then return up to max_out

@@ -1,4 +1,4 @@
-// Continuous-batching server of libdeepinv (deepinv_serve_*; see deepinv.h).
+// Continuous-batching server of libdeepinv (deepinv_serve_*).
 //
 // The paper motivates DeepInverse by low-latency recovery (Sec. 5).  Here a
 // host scheduler thread turns a stream of single recoveries for several
@@ -119,7 +119,11 @@ Lease* acquire(deepinv_server* s, int net, cudaStream_t st)
             s->cache[other].pop_back();
             cudaFreeAsync(l->ws, st);
             s->held -= l->bytes;
-            s->stats.evictions++;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->stats.evictions++;
+                s->stats.workspace_bytes = s->held;
+            }
             delete l;
         }
     }
@@ -136,15 +140,23 @@ Lease* acquire(deepinv_server* s, int net, cudaStream_t st)
         return nullptr;
     }
     s->held += need;
-    s->stats.workspace_bytes = s->held;
-    s->stats.peak_workspace_bytes = std::max(s->stats.peak_workspace_bytes, s->held);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stats.workspace_bytes = s->held;
+        s->stats.peak_workspace_bytes = std::max(s->stats.peak_workspace_bytes, s->held);
+    }
     Lease* l = new Lease{net, p, need};
     return l;
 }
 
-void finish_slot(deepinv_server* s, Slot& sl, int status)
+// Copies a finished batch's results into the requests' host buffers and builds
+// their result records, without the server lock (the slot and its requests
+// belong to the scheduler thread; a caller does not touch a request's buffer
+// before its result is handed back).
+void collect_slot(deepinv_server* s, Slot& sl, int status, std::vector<deepinv_result>& out)
 {
     const int N = net_N(s->nets[sl.net]);
+    const auto now = Clock::now();
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
         Req& r = sl.reqs[i];
         if (status == DEEPINV_OK) std::memcpy(r.xhat, sl.x_pin + i * (size_t)N, (size_t)N * sizeof(float));
@@ -154,32 +166,38 @@ void finish_slot(deepinv_server* s, Slot& sl, int status)
         res.net_id = r.net;
         res.batch = (int)sl.reqs.size();
         res.queue_us = us_between(r.t_submit, sl.t_launch);
-        res.latency_us = us_between(r.t_submit, Clock::now());
-        s->done.push_back(res);
-        if (status == DEEPINV_OK) s->stats.completed++;
-        else s->stats.failed++;
-        s->outstanding--;
+        res.latency_us = us_between(r.t_submit, status == DEEPINV_OK ? Clock::now() : now);
+        out.push_back(res);
     }
     sl.reqs.clear();
-    s->cache[sl.net].push_back(sl.lease);
+    if (sl.lease) s->cache[sl.net].push_back(sl.lease);
     sl.lease = nullptr;
     sl.busy = false;
     sl.net = -1;
 }
 
-// Launch one batch of `net` on slot `sl` (lock held).
-int launch(deepinv_server* s, Slot& sl, int net, Lease* lease)
+// Hands finished results to the callers (lock held).
+void publish(deepinv_server* s, std::vector<deepinv_result>& res)
+{
+    for (const deepinv_result& r : res) {
+        s->done.push_back(r);
+        if (r.status == DEEPINV_OK) s->stats.completed++;
+        else s->stats.failed++;
+        s->outstanding--;
+    }
+    res.clear();
+}
+
+// Launches the batch already moved into sl.reqs (network `net`, workspace
+// `lease`) on slot `sl`, without the server lock: staging copy, input copy,
+// forward pass, output copy and the slot's completion event.  On failure the
+// batch's failed results are appended to `failed`.
+int launch(deepinv_server* s, Slot& sl, int net, Lease* lease, std::vector<deepinv_result>& failed)
 {
     deepinv_net* n = s->nets[net];
     const int M = net_M(n), N = net_N(n);
-    std::deque<Req>& q = s->pending[net];
-    const int b = (int)std::min<size_t>(q.size(), (size_t)s->max_batch);
-    sl.reqs.clear();
-    for (int i = 0; i < b; ++i) {
-        sl.reqs.push_back(std::move(q.front()));
-        q.pop_front();
-        std::memcpy(sl.y_pin + (size_t)i * M, sl.reqs.back().y.data(), (size_t)M * sizeof(float));
-    }
+    const int b = (int)sl.reqs.size();
+    for (int i = 0; i < b; ++i) std::memcpy(sl.y_pin + (size_t)i * M, sl.reqs[i].y.data(), (size_t)M * sizeof(float));
     sl.net = net;
     sl.lease = lease;
     sl.t_launch = Clock::now();
@@ -195,78 +213,107 @@ int launch(deepinv_server* s, Slot& sl, int net, Lease* lease)
     if (rc == DEEPINV_OK && cudaEventRecord(sl.ev, sl.st) != cudaSuccess) rc = DEEPINV_ECUDA;
     if (rc != DEEPINV_OK) {
         cudaGetLastError();
-        finish_slot(s, sl, rc);
+        collect_slot(s, sl, rc, failed);
         return rc;
     }
     sl.busy = true;
-    s->stats.batches++;
-    int inflight = 0;
-    for (const Slot& o : s->slots) inflight += o.busy ? 1 : 0;
-    s->stats.max_in_flight = std::max(s->stats.max_in_flight, inflight);
     return DEEPINV_OK;
 }
 
+// The scheduler thread.  It owns the slots, the workspace cache and the
+// budget accounting; the server lock guards only what callers share with it
+// (the pending queues, the finished results, the counters), so that copying
+// results, staging inputs, allocating a workspace and enqueueing a batch never
+// keep a caller's submit or harvest waiting.
 void scheduler(deepinv_server* s)
 {
     cudaSetDevice(s->dev);
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::vector<deepinv_result> ready;
     while (true) {
-        bool progressed = false, finished = false;
-        // 1. collect finished batches
+        bool progressed = false;
+        // 1. collect finished batches (results copied out without the lock)
         for (Slot& sl : s->slots) {
             if (!sl.busy) continue;
             const cudaError_t e = cudaEventQuery(sl.ev);
             if (e == cudaErrorNotReady) continue;
             if (e != cudaSuccess) cudaGetLastError();
-            finish_slot(s, sl, e == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA);
-            progressed = finished = true;
+            collect_slot(s, sl, e == cudaSuccess ? DEEPINV_OK : DEEPINV_ECUDA, ready);
+            progressed = true;
         }
-        if (finished) s->cv_done.notify_all();
         // 2. start batches on free streams, oldest waiting network first
         bool blocked = false;
         for (Slot& sl : s->slots) {
             if (sl.busy || blocked) continue;
             int best = -1;
-            for (size_t k = 0; k < s->pending.size(); ++k)
-                if (!s->pending[k].empty() &&
-                    (best < 0 || s->pending[k].front().t_submit < s->pending[best].front().t_submit))
-                    best = (int)k;
-            if (best < 0) break;
-            if (s->lease_bytes[best] > s->budget) {
-                // can never fit: fail this network's waiting requests
-                while (!s->pending[best].empty()) {
-                    fail_request(s, s->pending[best].front(), DEEPINV_ENOMEM);
-                    s->pending[best].pop_front();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (!ready.empty()) {
+                    publish(s, ready);
+                    s->cv_done.notify_all();
                 }
-                s->cv_done.notify_all();
-                progressed = true;
-                continue;
+                for (size_t k = 0; k < s->pending.size(); ++k)
+                    if (!s->pending[k].empty() &&
+                        (best < 0 || s->pending[k].front().t_submit < s->pending[best].front().t_submit))
+                        best = (int)k;
+                if (best < 0) break;
+                if (s->lease_bytes[best] > s->budget) {
+                    // can never fit: fail this network's waiting requests
+                    while (!s->pending[best].empty()) {
+                        fail_request(s, s->pending[best].front(), DEEPINV_ENOMEM);
+                        s->pending[best].pop_front();
+                    }
+                    s->cv_done.notify_all();
+                    progressed = true;
+                    continue;
+                }
             }
+            // workspace lease (may allocate) outside the lock
             Lease* l = acquire(s, best, sl.st);
             if (!l) {
+                std::lock_guard<std::mutex> lk(s->mu);
                 if (!s->waiting_admission) s->stats.admission_waits++;
                 s->waiting_admission = true;
                 blocked = true;
                 continue;
             }
-            s->waiting_admission = false;
-            // a batch that failed to launch has already queued its failed results
-            if (launch(s, sl, best, l) != DEEPINV_OK) s->cv_done.notify_all();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->waiting_admission = false;
+                std::deque<Req>& q = s->pending[best];
+                const size_t b = std::min<size_t>(q.size(), (size_t)s->max_batch);
+                sl.reqs.clear();
+                for (size_t i = 0; i < b; ++i) {
+                    sl.reqs.push_back(std::move(q.front()));
+                    q.pop_front();
+                }
+                s->stats.batches++;
+            }
+            if (launch(s, sl, best, l, ready) == DEEPINV_OK) {
+                int inflight = 0;
+                for (const Slot& o : s->slots) inflight += o.busy ? 1 : 0;
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->stats.max_in_flight = std::max(s->stats.max_in_flight, inflight);
+            }
             progressed = true;
         }
         bool any_busy = false, any_pending = false;
         for (const Slot& sl : s->slots) any_busy |= sl.busy;
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!ready.empty()) {
+            publish(s, ready);
+            s->cv_done.notify_all();
+        }
         for (const auto& q : s->pending) any_pending |= !q.empty();
         if (s->stop && !any_busy && !any_pending) break;
         if (progressed) continue;
         if (any_busy) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(10));
-            lk.lock();
         } else {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
         }
     }
+    std::lock_guard<std::mutex> lk(s->mu);
     s->cv_done.notify_all();
 }
 
@@ -339,6 +386,43 @@ int deepinv_serve_add_net(deepinv_server* s, deepinv_net* net, int* net_id)
         return rc;
     }
     *net_id = (int)s->nets.size() - 1;
+    // Workspaces for this network's batches, one per stream while the budget
+    // allows, are allocated here rather than when a batch first needs them: a
+    // fresh allocation can take milliseconds (the stream-ordered pool growing),
+    // and the scheduler would hold back every network's batches meanwhile.  The
+    // pool keeps released memory, so that a workspace evicted and leased again
+    // under a tight budget is quick to get back.
+    {
+        cudaSetDevice(dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+        const int id = *net_id;
+        const size_t need = s->lease_bytes[id];
+        cudaStream_t st0 = s->slots[0].st;
+        for (int k = 0; k < s->max_streams && s->held + need <= s->budget; ++k) {
+            char* p = nullptr;
+            if (cudaMallocAsync(reinterpret_cast<void**>(&p), need, st0) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            if (cudaMemsetAsync(p, 0, need, st0) != cudaSuccess) {   // zero borders, written once
+                cudaGetLastError();
+                cudaFreeAsync(p, st0);
+                break;
+            }
+            s->cache[id].push_back(new Lease{id, p, need});
+            s->held += need;
+        }
+        cudaStreamSynchronize(st0);
+        cudaGetLastError();
+        s->stats.workspace_bytes = s->held;
+        s->stats.peak_workspace_bytes = std::max(s->stats.peak_workspace_bytes, s->held);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
     if (!s->started) {
         s->started = true;
         s->thr = std::thread(scheduler, s);
@@ -354,23 +438,37 @@ int deepinv_serve(deepinv_server* s, const deepinv_request* in, int n_in, deepin
     DI_REQUIRE(n_in == 0 || in, "requests pointer is NULL");
     DI_REQUIRE(max_out == 0 || out, "results pointer is NULL");
     *n_out = 0;
-    std::unique_lock<std::mutex> lk(s->mu);
-    for (int i = 0; i < n_in; ++i) {
-        const deepinv_request& r = in[i];
-        DI_REQUIRE(r.net_id >= 0 && r.net_id < (int)s->nets.size(), "request %d: unknown net_id %d", i, r.net_id);
-        DI_REQUIRE(r.y && r.xhat, "request %d: null y or xhat", i);
+    // the requests' measurements are copied between two short holds of the lock
+    // (the first reads each request's measurement count)
+    std::vector<Req> reqs;
+    if (n_in > 0) {
+        std::vector<int> m(n_in);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            const int nnets = (int)s->nets.size();
+            for (int i = 0; i < n_in; ++i) {
+                const deepinv_request& r = in[i];
+                DI_REQUIRE(r.net_id >= 0 && r.net_id < nnets, "request %d: unknown net_id %d", i, r.net_id);
+                DI_REQUIRE(r.y && r.xhat, "request %d: null y or xhat", i);
+                m[i] = net_M(s->nets[r.net_id]);
+            }
+        }
+        reqs.resize(n_in);
+        const auto now = Clock::now();
+        for (int i = 0; i < n_in; ++i) {
+            const deepinv_request& r = in[i];
+            Req& q = reqs[i];
+            q.net = r.net_id;
+            q.tag = r.tag;
+            q.xhat = r.xhat;
+            q.y.assign(r.y, r.y + m[i]);
+            q.t_submit = now;
+        }
     }
-    const auto now = Clock::now();
-    for (int i = 0; i < n_in; ++i) {
-        const deepinv_request& r = in[i];
-        Req q;
-        q.net = r.net_id;
-        q.tag = r.tag;
-        q.xhat = r.xhat;
-        const int M = net_M(s->nets[r.net_id]);
-        q.y.assign(r.y, r.y + M);
-        q.t_submit = now;
-        s->pending[r.net_id].push_back(std::move(q));
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (Req& q : reqs) {
+        const int net = q.net;
+        s->pending[net].push_back(std::move(q));
         s->stats.submitted++;
         s->outstanding++;
     }
@@ -396,7 +494,6 @@ int deepinv_serve_get_stats(deepinv_server* s, deepinv_serve_stats* st)
     DI_REQUIRE(s && st, "null pointer");
     std::lock_guard<std::mutex> lk(s->mu);
     *st = s->stats;
-    st->workspace_bytes = s->held;
     return DEEPINV_OK;
 }
 
