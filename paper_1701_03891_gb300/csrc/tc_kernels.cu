@@ -1057,7 +1057,7 @@ struct Conv3Smem {
     uint32_t tmem_base;
     int abort_flag;
     int vote[2][4];
-    float halo[2][4][3][11][4];         // [tile parity][warp][lane 0..2][dy][e]
+    alignas(16) float halo[2][4][3][12];   // [tile parity][warp][target lane 29 + i][dy] halo sums
 };
 
 __host__ __device__ constexpr uint32_t conv3_wbytes(int cin) { return 3u * (cin / 16) * 2048u; }
@@ -1223,16 +1223,44 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&ss->aempty[s]));
+                // the previous warp's lane 29 + i needs, for each dy, the terms
+                // D[j][4 dy + j + 3 - i] of this warp's rows j = max(0, i - 2) .. i:
+                // lane i sums them (own e = 3 term, lane i - 1's e = 2, lane i - 2's e = 1)
+                float hs[12];
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) {
+                    const float e2 = __shfl_up_sync(0xffffffffu, v[4 * dy + 2], 1);
+                    const float e1 = __shfl_up_sync(0xffffffffu, v[4 * dy + 1], 2);
+                    hs[dy] = v[4 * dy + 3] + (lane >= 1 ? e2 : 0.f) + (lane >= 2 ? e1 : 0.f);
+                }
+                hs[11] = 0.f;
                 if (lane < 3) {
+                    float4* hd = reinterpret_cast<float4*>(ss->halo[s][warp][lane]);
 #pragma unroll
-                    for (int dy = 0; dy < 11; ++dy)
-#pragma unroll
-                        for (int e = 1; e < 4; ++e) ss->halo[s][warp][lane][dy][e] = v[4 * dy + e];
+                    for (int q4 = 0; q4 < 3; ++q4)
+                        hd[q4] = make_float4(hs[4 * q4], hs[4 * q4 + 1], hs[4 * q4 + 2], hs[4 * q4 + 3]);
                 }
             }
             if (lane == 0) ss->vote[s][warp] = ok ? 1 : 0;
             epi_bar();
             if (!(ss->vote[s][0] && ss->vote[s][1] && ss->vote[s][2] && ss->vote[s][3])) return false;
+            // rows past this warp come from the next warp's halo sums (never needed by
+            // warp 3's valid rows; the index is clamped so that the read stays in bounds)
+            float hv[12];
+            if (lane >= 29) {
+                const float4* hsrc = reinterpret_cast<const float4*>(ss->halo[s][warp < 3 ? warp + 1 : 3][lane - 29]);
+#pragma unroll
+                for (int q4 = 0; q4 < 3; ++q4) {
+                    const float4 h4 = hsrc[q4];
+                    hv[4 * q4] = h4.x;
+                    hv[4 * q4 + 1] = h4.y;
+                    hv[4 * q4 + 2] = h4.z;
+                    hv[4 * q4 + 3] = h4.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) hv[i] = 0.f;
+            }
             float tv[11];
 #pragma unroll
             for (int dy = 0; dy < 11; ++dy) {
@@ -1240,13 +1268,9 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
 #pragma unroll
                 for (int e = 1; e < 4; ++e) {
                     const float nb = __shfl_down_sync(0xffffffffu, v[4 * dy + e], e);
-                    // rows past this warp come from lanes 0..2 of the next warp (never needed by
-                    // warp 3's valid rows); the index is clamped so that the read stays in bounds
-                    const int hl = lane + e - 32;
-                    const float h = ss->halo[s][warp < 3 ? warp + 1 : 3][hl > 0 ? hl : 0][dy][e];
-                    t += hl < 0 ? nb : h;
+                    if (lane + e < 32) t += nb;
                 }
-                tv[dy] = t;
+                tv[dy] = t + hv[dy];
             }
             if (!FUSED) {
                 if (row_ok) {
