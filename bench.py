@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-deep", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--fused-steps", type=int, default=20)
     ap.add_argument("--deep-steps", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=10)
     ap.add_argument("--large-steps", type=int, default=10)
@@ -344,6 +346,57 @@ def large_bench(args):
     rel = np.linalg.norm(results["fp8"] - results["bf16"], axis=1) / np.linalg.norm(results["bf16"], axis=1)
     out["fp8_over_bf16"] = out["fp8"]["images_per_s"] / out["bf16"]["images_per_s"]
     out["fp8_vs_bf16_max_rel_l2"] = float(rel.max())
+    return out
+
+
+def fused_bench(args):
+    """conv1 + conv2 fused into one kernel (a1 kept in shared memory) against the
+    two kernels, on the bf16 forward pass: 64 x 64, M/N = 0.1, batch 1024 (the
+    benchmark workload, walked whole) and 256 x 256, M/N = 0.1, batch 256 (walked
+    as column strips).  Step = x^ = M(y) with y resident; CUDA events over the
+    steps; the library's stage events give conv1 + conv2 against the fused kernel.
+    The two results are compared bit for bit."""
+    import numpy as np
+    import torch
+    from paper_1701_03891_gb300 import deepinv, synth
+    out = {}
+    stream = torch.cuda.current_stream()
+    for n, B in ((64, 1024), (256, 256)):
+        N = n * n
+        M = synth.m_for_ratio(0.10, N)
+        phi = synth.gaussian_phi(M, N, seed=0)
+        params = synth.he_params(seed=1)
+        x = synth.voronoi_images(B, n, n, seed=3)
+        net = deepinv.Net(phi, params, n, n, prec="bf16")
+        net.reserve(B)
+        yd = net.measure(torch.from_numpy(x).cuda())
+        xh = torch.empty((B, N), device="cuda")
+        res, outs = {}, {}
+        for mode in ("two_kernels", "fused"):
+            net.set_fused(mode == "fused")
+            for _ in range(3):
+                net.forward(yd, out=xh)
+            torch.cuda.synchronize()
+            net.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.fused_steps):
+                net.forward(yd, out=xh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = net.profile_read()
+            net.profile(False)
+            ms = e0.elapsed_time(e1) / args.fused_steps
+            stage = {k: v[0] / max(1, v[1]) for k, v in st.items() if v[1]}
+            res[mode] = {"forward_ms": ms, "images_per_s": B / (ms / 1000.0),
+                         "conv1_plus_conv2_ms": stage.get("conv1", 0.0) + stage.get("conv2", 0.0),
+                         "stage_ms": stage}
+            outs[mode] = xh.cpu().numpy()
+        net.close()
+        res["fused_over_two_kernels"] = res["fused"]["images_per_s"] / res["two_kernels"]["images_per_s"]
+        res["bit_identical"] = bool(np.array_equal(outs["fused"], outs["two_kernels"]))
+        res["workload"] = "forward %dx%d, M/N=0.10 (M=%d), batch %d, y resident" % (n, n, M, B)
+        out["%dx%d" % (n, n)] = res
     return out
 
 
@@ -752,6 +805,9 @@ def run_native(args):
     deep = None
     if rank == 0 and not args.no_deep:
         deep = optional("deep_64", deep_bench, args)
+    fused = None
+    if rank == 0 and not args.no_fused:
+        fused = optional("fused12", fused_bench, args)
 
     evaluation = None
     if rank == 0 and args.eval:
@@ -779,6 +835,7 @@ def run_native(args):
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
             "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "deep_64": deep,
+            "fused12": fused,
             "eval_32": evaluation,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches,

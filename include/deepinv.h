@@ -195,6 +195,20 @@ size_t deepinv_saved_bytes(const deepinv_net* net, int B);
  * would not fit. */
 int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes);
 
+/* Runs the first two layers of Eq. (1) (conv1 + ReLU, conv2 + ReLU) as one
+ * fused kernel in the inference forward pass of a bfloat16 network (enable =
+ * 1) instead of two (0, the default).  The fused kernel keeps conv1's output
+ * in shared memory instead of writing it to HBM and reading it back: each CTA
+ * walks a run of conv2 tiles and produces conv1's output for the rows ahead
+ * of it once.  Images up to 70 columns are walked whole; wider ones as column
+ * strips of at most 55 columns, whose halos cost extra conv2 work.  The
+ * result is bit-identical to the two-kernel path.  Forward passes that save
+ * activations for deepinv_backward, e4m3 and float32 networks keep the
+ * two-kernel path.  With the profiler on, the fused kernel is timed as
+ * DEEPINV_STAGE_CONV2 (DEEPINV_STAGE_CONV1 then counts nothing).  Returns
+ * DEEPINV_EINVAL for a NULL net. */
+int deepinv_net_set_fused(deepinv_net* net, int enable);
+
 /* x^ = M(y, Omega) (Sec. 4): FC layer, reshape to n1 x n2, conv1 + ReLU,
  * conv2 + ReLU, each hidden layer + ReLU, conv3 (+ ReLU when final_relu).
  * y [B][M] -> xhat [B][N].  `saved` is NULL for inference, or a device buffer

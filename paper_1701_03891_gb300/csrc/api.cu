@@ -126,6 +126,7 @@ struct deepinv_net {
     float* amax_a1 = nullptr;   // calibrated max of a1
     float* amax_w = nullptr;    // [32] scratch
     bool calibrated = false;
+    bool fused12 = false;       // conv1 + conv2 as one kernel in inference passes
     // forward workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -509,15 +510,23 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
             DI_TRY(pack_kmajor(y, M, 1, B, M, nb, n->Kfc, w.ypk, st));
             DI_TRY(tc_gemm(n->fcA, w.ypk, n->Kfc, N, B, nb, GEMM_OUT_PLANE, nullptr, 0, xt, g, status, st));
         }
-        {
-            StageTimer t(n, st, DEEPINV_STAGE_CONV1);
-            DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, n->fp8 ? kConv1OutE4M3 : kConv1OutBF16, n->inv_sa,
-                            nullptr, status, st));
-        }
-        {
+        if (n->fused12 && !saved && !n->fp8) {
+            // a1 never leaves the kernel; its workspace holds the x~ strip planes of wide images
             StageTimer t(n, st, DEEPINV_STAGE_CONV2);
-            if (n->fp8) DI_TRY(conv2_tc(a1, B, g, n->w2q, n->b[1], n->oscale, true, a2, n->num_sms, status, st));
-            else DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], nullptr, false, a2, n->num_sms, status, st));
+            DI_REQUIRE(conv12_scratch_bytes(B, g) <= (size_t)B * 8 * g.plane * 8 * sizeof(bf16),
+                       "fused conv1/conv2: strip planes exceed the a1 workspace");
+            DI_TRY(conv12_tc(xt, B, g, n->w1p, n->b[0], n->w2p, n->b[1], a2, a1, n->num_sms, status, st));
+        } else {
+            {
+                StageTimer t(n, st, DEEPINV_STAGE_CONV1);
+                DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, n->fp8 ? kConv1OutE4M3 : kConv1OutBF16,
+                                n->inv_sa, nullptr, status, st));
+            }
+            {
+                StageTimer t(n, st, DEEPINV_STAGE_CONV2);
+                if (n->fp8) DI_TRY(conv2_tc(a1, B, g, n->w2q, n->b[1], n->oscale, true, a2, n->num_sms, status, st));
+                else DI_TRY(conv2_tc(a1, B, g, n->w2p, n->b[1], nullptr, false, a2, n->num_sms, status, st));
+            }
         }
         bf16* last = a2;
         if (n->d.hidden > 0) {
@@ -1283,6 +1292,13 @@ int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes)
 {
     DI_REQUIRE(net, "net is NULL");
     net->act_budget = bytes;
+    return DEEPINV_OK;
+}
+
+int deepinv_net_set_fused(deepinv_net* net, int enable)
+{
+    DI_REQUIRE(net, "net is NULL");
+    net->fused12 = enable != 0;
     return DEEPINV_OK;
 }
 

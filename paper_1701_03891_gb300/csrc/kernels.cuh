@@ -156,6 +156,13 @@ constexpr size_t kW2E4M3Bytes = 11 * 3 * 2 * 2 * 128 * 16;
 int pack_w2_e4m3(const float* w2, float* amax_scratch, uint8_t* w2q, float* sw, cudaStream_t st);
 int e4m3_scales(const float* amax_a1, const float* sw, float* inv_sa, float* oscale, cudaStream_t st);
 bool conv2_tc_supported(const Geo& g);
+// conv1 + conv2 fused (fused12.cu): x~ plane [B][plane] -> a2 bf16
+// [B][4][plane][8] (bias and ReLU after each layer, zero pad columns), a1 kept
+// in shared memory.  Images wider than 70 columns are walked as column strips
+// whose x~ planes are gathered into `xs` (conv12_scratch_bytes; 0 otherwise).
+size_t conv12_scratch_bytes(int B, const Geo& g);
+int conv12_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, const bf16* w2p,
+              const float* b2, bf16* a2, bf16* xs, int num_sms, int* status, cudaStream_t st);
 // conv3: a2 -> row partial sums T [images of one pass][11][tlen] -> xhat [B][n1 * n2] float32.
 // conv3 keeps its row sums (or, for pitches >= 125, its partial outputs) in a
 // shared-memory ring and needs no scratch, up to about 4000 columns; wider

@@ -80,6 +80,7 @@ SIGNATURES = {
     "deepinv_net_get_desc": (_I, [_P, ctypes.POINTER(NetDesc)]),
     "deepinv_net_reserve": (_I, [_P, _I, _P]),
     "deepinv_net_set_act_budget": (_I, [_P, ctypes.c_size_t]),
+    "deepinv_net_set_fused": (_I, [_P, _I]),
     "deepinv_net_measure": (_I, [_P, _P, _I, _P, _P]),
     "deepinv_saved_bytes": (ctypes.c_size_t, [_P, _I]),
     "deepinv_forward": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -390,6 +391,10 @@ class Net:
         """Activation budget of backward(saved=None): the forward activations are
         recomputed in chunks of images whose activations fit nbytes (0: one chunk)."""
         _check(lib().deepinv_net_set_act_budget(self._h, int(nbytes)))
+
+    def set_fused(self, enable: bool):
+        """conv1 + conv2 as one fused kernel in inference forward passes (bf16 networks)."""
+        _check(lib().deepinv_net_set_fused(self._h, 1 if enable else 0))
 
     def backward(self, y, x, saved=None, grads=None, stream=None):
         """Gradient of L = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4).  Returns (loss tensor, dW, db, dWfc).
