@@ -1056,7 +1056,6 @@ struct Conv3Smem {
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
-    int vote[2][4];
     alignas(16) float halo[2][4][3][12];   // [tile parity][warp][target lane 29 + i][dy] halo sums
 };
 
@@ -1070,6 +1069,31 @@ __host__ __device__ constexpr size_t conv3_base_smem(int cin)
 __host__ __device__ inline int conv3_ring(int P) { return (10 * P + 128 + 31) / 32 * 32; }
 
 enum { kConv3Global = 0, kConv3RingT = 1, kConv3RingAcc = 2 };
+
+// Row sums T[p][dy] read input positions p .. p + 10 only, so a tile whose
+// positions all read the input's zero border rows (the 5 rows above the image,
+// or the rows below it) has T = 0: the fused modes skip its loads and MMAs and
+// take the zeros as its row sums.
+__device__ __forceinline__ bool conv3_zero_tile(int pstart, int H, int P)
+{
+    return pstart + kConv3Valid + 10 <= kPad * P || pstart >= (H + kPad) * P;
+}
+
+// Named barrier of the 128 epilogue threads that also returns the OR of `v`
+// over them (the same value in every thread).
+__device__ __forceinline__ bool epi_bar_or3(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)(v ? 1 : 0))
+        : "memory");
+    return r != 0;
+}
 
 // Calls f(it, b, pstart, qa, qb) for the row-sum tiles of output tiles [lo, hi)
 // in order until f returns false.  FUSED: per image, tiles pstart = qa + 125 k
@@ -1153,7 +1177,10 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
         if (lane == 0) {
             int parity[kC3Stages];
             for (int s = 0; s < kC3Stages; ++s) parity[s] = -1;
-            conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int b, int pstart, int, int) {
+            int li = 0;                                         // loaded tiles
+            conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int, int b, int pstart, int, int) {
+                if (FUSED && conv3_zero_tile(pstart, H, P)) return true;
+                const int it = li++;
                 const int st = it % kC3Stages, n = it / kC3Stages;
                 if (!mbar_wait(smem_u32(&ss->xempty[st]), (n & 1) ^ 1, status, &ss->abort_flag)) return false;
                 mbar_arrive_expect_tx(smem_u32(&ss->xfull[st]), SB);
@@ -1177,9 +1204,13 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
                 ok = mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag);
                 if (!ok) mbar_wait_drain(smem_u32(&ss->wbar), 0);
             }
-            const uint32_t idesc = idesc_bf16(128, 64);
+            // N = 48: the 44 columns (dy, e) and 4 of zero weights
+            const uint32_t idesc = idesc_bf16(128, 48);
+            int li = 0;
             if (ok)
-                conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int, int, int, int) {
+                conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int, int, int pstart, int, int) {
+                    if (FUSED && conv3_zero_tile(pstart, H, P)) return true;
+                    const int it = li++;
                     const int s = it & 1, use = it >> 1;
                     const int st = it % kC3Stages, n = it / kC3Stages;
                     if (!mbar_wait(smem_u32(&ss->aempty[s]), (use & 1) ^ 1, status, &ss->abort_flag)) return false;
@@ -1211,7 +1242,14 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
         // fused bookkeeping: ring slot of pstart, and (row, column) of output q = pstart - 10 P + m
         int base = 0, orow = 0, ocol = 0, cur_b = -1, cur_qa = -1;
         const int step_r = kConv3Valid / P, step_c = kConv3Valid % P;
-        conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int it, int b, int pstart, int qa, int qb) {
+        int li = 0;                                             // tiles with MMAs
+        conv3_walk<FUSED>(tr.lo, tr.hi, tper, HP, P, [&](int, int b, int pstart, int qa, int qb) {
+            float tv[11];
+            if (FUSED && conv3_zero_tile(pstart, H, P)) {
+#pragma unroll
+                for (int dy = 0; dy < 11; ++dy) tv[dy] = 0.f;
+            } else {
+            const int it = li++;
             const int s = it & 1, use = it >> 1;
             bool ok = mbar_wait(smem_u32(&ss->afull[s]), use & 1, status, &ss->abort_flag);
             ok = __all_sync(0xffffffffu, ok);
@@ -1241,9 +1279,7 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
                         hd[q4] = make_float4(hs[4 * q4], hs[4 * q4 + 1], hs[4 * q4 + 2], hs[4 * q4 + 3]);
                 }
             }
-            if (lane == 0) ss->vote[s][warp] = ok ? 1 : 0;
-            epi_bar();
-            if (!(ss->vote[s][0] && ss->vote[s][1] && ss->vote[s][2] && ss->vote[s][3])) return false;
+            if (epi_bar_or3(!ok)) return false;
             // rows past this warp come from the next warp's halo sums (never needed by
             // warp 3's valid rows; the index is clamped so that the read stays in bounds)
             float hv[12];
@@ -1261,7 +1297,6 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
 #pragma unroll
                 for (int i = 0; i < 12; ++i) hv[i] = 0.f;
             }
-            float tv[11];
 #pragma unroll
             for (int dy = 0; dy < 11; ++dy) {
                 float t = v[4 * dy];
@@ -1271,6 +1306,7 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
                     if (lane + e < 32) t += nb;
                 }
                 tv[dy] = t + hv[dy];
+            }
             }
             if (!FUSED) {
                 if (row_ok) {
