@@ -395,6 +395,29 @@ __host__ __device__ constexpr size_t conv1_smem_bytes(int cout)
     return conv1_wbytes(cout) + 2 * (size_t)kC1XBytes + sizeof(Conv1Smem) + 16;
 }
 
+// Ring mode: one expanded window per CTA, row e = x~[e .. e + 7] of the image at
+// ring row e mod RS (RS a power of two), its first kC1ETail rows repeated past
+// the end so that no operand wraps.  Successive tiles share all but their last
+// 128 rows, so each tile writes 16 groups instead of rebuilding 11 pieces.  A
+// tile's window is 10 P + 136 rows; the producer of tile n may overwrite rows
+// of tile n - 2 only, so RS >= 10 P + 272.
+// The first tile of every image rebuilds the whole window and waits for the tile
+// before it, so the ring pays only where images have many tiles (measured at
+// batch 1024 / 256: 256 x 256, 536 tiles per image: 0.574 -> 0.551 ms; 64 x 64,
+// 35 tiles: 0.1576 -> 0.1591 ms): images of fewer than 64 tiles keep the pieces.
+constexpr int kC1ETail = 144;
+constexpr int kC1ERingMax = 4096;
+constexpr int kC1ERingMinTiles = 64;
+static inline int conv1_ering(int P, int t1)
+{
+    if (t1 < kC1ERingMinTiles) return 0;
+    const int need = 10 * P + 272;
+    int rs = 1024;
+    while (rs < need) rs *= 2;
+    return rs <= kC1ERingMax ? rs : 0;
+}
+static inline size_t conv1_xbytes(int ering) { return ering ? (size_t)(ering + kC1ETail) * 16 : 2 * (size_t)kC1XBytes; }
+
 // Window of tile (b, q0): piece dy starts at the 8-aligned plane index
 // a = (q0 + dy P) & ~7, group j of it (rows 8 j .. 8 j + 7) comes from the 16
 // values x~[a + 8 j .. a + 8 j + 15] (two aligned 16-byte loads; the plane
@@ -456,15 +479,17 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
                                                               const float* __restrict__ b1, void* __restrict__ a1,
                                                               int mode, const float* __restrict__ inv_sa,
                                                               float* __restrict__ amax,
-                                                              const bf16* __restrict__ mask_src, int* status)
+                                                              const bf16* __restrict__ mask_src, int ering,
+                                                              int* status)
 {
     constexpr uint32_t BBYTES = conv1_wbytes(COUT);
     constexpr int CPW = COUT / 2;                             // channels per epilogue warp
     constexpr uint32_t TCOLS = 2 * COUT < 32 ? 32 : 2 * COUT;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sB = smem_raw;
-    uint4* sX = reinterpret_cast<uint4*>(smem_raw + BBYTES);                       // [2][11][kC1Stride]
-    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + BBYTES + 2 * kC1XBytes);
+    uint4* sX = reinterpret_cast<uint4*>(smem_raw + BBYTES);   // pieces [2][11][kC1Stride], or the ring
+    const uint32_t xbytes = ering ? (uint32_t)(ering + kC1ETail) * 16u : 2u * kC1XBytes;
+    Conv1Smem* ss = reinterpret_cast<Conv1Smem*>(smem_raw + BBYTES + xbytes);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int HP = H * P;
@@ -492,7 +517,67 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
 
-    if (warp >= 8 && warp < 12) {
+    if (warp >= 8 && warp < 12 && ering) {
+        // ------------------------------------------------ window ring producers
+        const int pt = threadIdx.x - 256;
+        const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
+        const uint32_t rmask = (uint32_t)ering - 1u;
+        auto put_group = [&](int G, uint4 lo, uint4 hi) {
+            const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+            const uint32_t r0 = (uint32_t)(8 * G) & rmask;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    o[e] = (k & 1) ? __byte_perm(w[k / 2 + e], w[k / 2 + e + 1], 0x5432) : w[k / 2 + e];
+                const uint4 row = make_uint4(o[0], o[1], o[2], o[3]);
+                sX[r0 + k] = row;
+                if (r0 < (uint32_t)kC1ETail) sX[r0 + k + ering] = row;
+            }
+        };
+        int b = tr.lo / t1, tt = tr.lo % t1, gnext = 0;
+        // a tile after the first of an image adds 16 groups: threads pt < 16 load theirs
+        // into registers before waiting for the slot, so that the load's latency overlaps
+        // the wait
+        int pG = -1;
+        uint4 plo = make_uint4(0, 0, 0, 0), phi = plo;
+        for (int tile = tr.lo, it = 0; tile < tr.hi; ++tile, ++it) {
+            const int s = it & 1, use = it >> 1;
+            // the rows written overwrite those of tile it - 2; a new image rewrites the
+            // whole window, so tile it - 1 must be done too
+            const bool fresh = tile == tr.lo || tt == 0;
+            bool ok = mbar_wait(smem_u32(&ss->xempty[s]), (use & 1) ^ 1, status, &ss->abort_flag);
+            if (ok && fresh && it > 0)
+                ok = mbar_wait(smem_u32(&ss->xempty[(it - 1) & 1]), ((it - 1) >> 1) & 1, status, &ss->abort_flag);
+            if (!ok) break;
+            const int q0 = tt * 128;
+            const int g1 = (q0 + 10 * P + 135) >> 3;
+            const bf16* img = xt + (size_t)b * plane_len;
+            if (fresh) {
+                for (int G = (q0 >> 3) + pt; G <= g1; G += 128) {
+                    const uint4* src = reinterpret_cast<const uint4*>(img + 8 * G);
+                    put_group(G, __ldg(src), __ldg(src + 1));
+                }
+            } else if (pG >= 0) {
+                put_group(pG, plo, phi);
+            }
+            gnext = g1 + 1;
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&ss->xfull[s]));
+            if (++tt == t1) {
+                tt = 0;
+                ++b;
+            }
+            pG = -1;
+            if (tile + 1 < tr.hi && tt != 0 && pt < 16) {
+                pG = gnext + pt;
+                const uint4* src = reinterpret_cast<const uint4*>(img + 8 * pG);
+                plo = __ldg(src);
+                phi = __ldg(src + 1);
+            }
+        }
+    } else if (warp >= 8 && warp < 12) {
         // ------------------------------------------------ window producers
         const int pt = threadIdx.x - 256;
         const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
@@ -535,8 +620,9 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
                 const uint4* sx = sX + s * (11 * kC1Stride);
 #pragma unroll
                 for (int dy = 0; dy < 11; ++dy) {
-                    const int row = dy * kC1Stride + ((q0 + dy * P) & 7);
-                    const uint64_t ad = sdesc(smem_u32(sx + row), 128, 128);
+                    const int row = ering ? (int)((uint32_t)(q0 + dy * P) & (uint32_t)(ering - 1))
+                                          : dy * kC1Stride + ((q0 + dy * P) & 7);
+                    const uint64_t ad = sdesc(smem_u32((ering ? sX : sx) + row), 128, 128);
                     const uint64_t bd = sdesc(smem_u32(sB + dy * 2 * COUT * 16), COUT * 16, 128);
                     mma_bf16(d, ad, bd, idesc, dy > 0 ? 1u : 0u);
                 }
@@ -1562,7 +1648,8 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
              const float* inv_sa, float* amax, int* status, cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
-    const size_t smem = conv1_smem_bytes(64);
+    const int ering = conv1_ering(g.P, g.t1);
+    const size_t smem = conv1_wbytes(64) + conv1_xbytes(ering) + sizeof(Conv1Smem) + 16;
     int dev = 0, sms = 0;
     DI_CUDA(cudaGetDevice(&dev));
     DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1570,7 +1657,7 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
     const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conv1_kernel<64><<<grid, kC1Threads, smem, st>>>(xt, B, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa,
-                                                     amax, nullptr, status);
+                                                     amax, nullptr, ering, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1579,7 +1666,8 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
                    cudaStream_t st)
 {
     if (B <= 0) return DEEPINV_OK;
-    const size_t smem = conv1_smem_bytes(32);
+    const int ering = conv1_ering(g.P, g.t1);
+    const size_t smem = conv1_wbytes(32) + conv1_xbytes(ering) + sizeof(Conv1Smem) + 16;
     int dev = 0, sms = 0;
     DI_CUDA(cudaGetDevice(&dev));
     DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1587,7 +1675,7 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
     const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conv1_kernel<32><<<grid, kC1Threads, smem, st>>>(g3p, B, g.H, g.W, g.P, g.plane, g.t1, w3t, nullptr, g2,
-                                                     kConv1GradMask, nullptr, nullptr, a2, status);
+                                                     kConv1GradMask, nullptr, nullptr, a2, ering, status);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

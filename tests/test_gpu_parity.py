@@ -170,6 +170,8 @@ def test_forward_bf16_conv3_modes(di, n1, n2, ratio, B):
 @pytest.mark.parametrize("n1,n2,M,B", [
     (4, 130, 52, 2),        # pitch 135: conv1's input gradient in the partial-output ring
     (1, 4250, 425, 2),      # too wide for the 64-channel ring: global row-sum scratch
+    (72, 120, 864, 2),      # 71 tiles of 128 per image: conv1 and conv3's input gradient
+                            # read their expanded input from the window ring
 ])
 def test_backward_bf16_wide_train_fc(di, n1, n2, M, B):
     """bf16 backward with the FC layer trained (conv1's input gradient runs through
