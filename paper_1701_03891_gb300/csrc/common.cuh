@@ -53,6 +53,26 @@ void count_launch();
         ::di::count_launch();             \
     } while (0)
 
+// Launch that lets the kernel start while the stream's previous kernel finishes
+// (programmatic dependent launch); the kernel calls pdl_wait before it touches
+// memory that kernel may still read or write.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #define DI_TRY(expr)                  \
     do {                              \
         int rc_ = (expr);             \

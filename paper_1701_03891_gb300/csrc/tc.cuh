@@ -112,6 +112,14 @@ __device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity)
     }
 }
 
+// ---------------------------------------------------------------- dependent launch
+// Kernels launched with launch_pdl may start (set up barriers and TMEM) while the
+// previous kernel of the stream is still running: pdl_wait blocks until that
+// kernel has completed and its writes are visible (a no-op without the launch
+// attribute); pdl_trigger lets the next kernel be scheduled on SMs this grid frees.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------------- bulk copy
 // Global -> shared copy on the TMA engine, completing `bytes` of transaction
 // count on `bar`.  Both addresses 16-byte aligned, bytes a multiple of 16.

@@ -62,6 +62,8 @@ __device__ __forceinline__ uint4 pack16_e4m3(const float* v, float scale)
 __global__ void pack_kmajor_kernel(const float* __restrict__ src, long long rs, long long cs, int R,
                                    int K, int TR, int Kp, long long nchunks, bf16* __restrict__ dst)
 {
+    pdl_wait();
+    pdl_trigger();
     const int kcs = Kp / 8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nchunks;
          i += (long long)gridDim.x * blockDim.x) {
@@ -261,6 +263,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const bf16* __restrict_
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 0 && lane == 0) {
         // producer
@@ -390,10 +394,6 @@ __host__ __device__ constexpr int conv1_out_chunks(int cout, int mode)
 {
     return mode == kConv1OutE4M3 ? cout / 16 : (mode == kConv1AmaxOnly ? 0 : cout / 8);
 }
-__host__ __device__ constexpr size_t conv1_smem_bytes(int cout)
-{
-    return conv1_wbytes(cout) + 2 * (size_t)kC1XBytes + sizeof(Conv1Smem) + 16;
-}
 
 // Ring mode: one expanded window per CTA, row e = x~[e .. e + 7] of the image at
 // ring row e mod RS (RS a power of two), its first kC1ETail rows repeated past
@@ -516,6 +516,8 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp >= 8 && warp < 12 && ering) {
         // ------------------------------------------------ window ring producers
@@ -885,6 +887,8 @@ __global__ void __launch_bounds__(kConv2Threads, 1) conv2_kernel(const void* __r
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 6 && lane == 0) {
         // ------------------------------------------------ window producer
@@ -1276,6 +1280,8 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 4) {
         // ------------------------------------------------ producer
@@ -1539,7 +1545,8 @@ int pack_kmajor(const float* src, long long rs, long long cs, int R, int K, int 
 {
     const long long nchunks = (long long)cdiv(R, TR) * TR * (Kp / 8);
     if (nchunks <= 0) return DEEPINV_OK;
-    pack_kmajor_kernel<<<grid1d(nchunks), 256, 0, st>>>(src, rs, cs, R, K, TR, Kp, nchunks, dst);
+    DI_CUDA(launch_pdl(pack_kmajor_kernel, dim3(grid1d(nchunks)), dim3(256), 0, st, src, rs, cs, R, K, TR, Kp,
+                       nchunks, dst));
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1629,8 +1636,8 @@ int tc_gemm(const bf16* A, const bf16* B, int Kp, int Mr, int Nc, int NB, int mo
     do {                                                                                                               \
         DI_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<MODE_, MT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                      (int)smem));                                                                      \
-        tc_gemm_kernel<MODE_, MT_><<<grid, 192, smem, st>>>(A, B, Kp, Mr, Nc, NB, cols, out_f32, ldo, plane, geo.H,     \
-                                                             geo.W, geo.P, geo.plane, status);                         \
+        DI_CUDA(launch_pdl(tc_gemm_kernel<MODE_, MT_>, grid, dim3(192), smem, st, A, B, Kp, Mr, Nc, NB, cols, out_f32, \
+                           ldo, plane, geo.H, geo.W, geo.P, geo.plane, status));                                       \
     } while (0)
     if (mode == GEMM_OUT_F32) {
         if (mt == 2) DI_GEMM_LAUNCH(GEMM_OUT_F32, 2);
@@ -1656,8 +1663,8 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
     const int ntiles = B * g.t1;
     const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<64><<<grid, kC1Threads, smem, st>>>(xt, B, g.H, g.W, g.P, g.plane, g.t1, w1p, b1, a1, mode, inv_sa,
-                                                     amax, nullptr, ering, status);
+    DI_CUDA(launch_pdl(conv1_kernel<64>, dim3(grid), dim3(kC1Threads), smem, st, xt, B, g.H, g.W, g.P, g.plane, g.t1,
+                       w1p, b1, a1, mode, inv_sa, amax, (const bf16*)nullptr, ering, status));
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1674,8 +1681,9 @@ int conv3_dgrad_tc(const bf16* g3p, int B, const Geo& g, const bf16* w3t, const 
     const int ntiles = B * g.t1;
     const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv1_kernel<32><<<grid, kC1Threads, smem, st>>>(g3p, B, g.H, g.W, g.P, g.plane, g.t1, w3t, nullptr, g2,
-                                                     kConv1GradMask, nullptr, nullptr, a2, ering, status);
+    DI_CUDA(launch_pdl(conv1_kernel<32>, dim3(grid), dim3(kC1Threads), smem, st, g3p, B, g.H, g.W, g.P, g.plane,
+                       g.t1, w3t, (const float*)nullptr, (void*)g2, (int)kConv1GradMask, (const float*)nullptr,
+                       (float*)nullptr, a2, ering, status));
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1743,8 +1751,8 @@ static int launch_conv2_mode(const void* in, int B, const Geo& g, const void* wp
                              int* status, cudaStream_t st)
 {
     DI_CUDA(cudaFuncSetAttribute(conv2_kernel<ROWS, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conv2_kernel<ROWS, V><<<grid, kConv2Threads, smem, st>>>(in, B, g.H, g.W, g.P, g.plane, g.t2, nslab, wp, bias,
-                                                             oscale, mask_src, out, status);
+    DI_CUDA(launch_pdl(conv2_kernel<ROWS, V>, dim3(grid), dim3(kConv2Threads), smem, st, in, B, g.H, g.W, g.P,
+                       g.plane, g.t2, nslab, wp, bias, oscale, mask_src, out, status));
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
@@ -1866,8 +1874,8 @@ static int launch_conv3(const bf16* in, int B, const Geo& g, const bf16* w, floa
     const int mode = fused ? conv3_mode(g) : kConv3Global;
     auto go = [&](auto kern) -> int {
         DI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, kC3Threads, smem, st>>>(in, B, g.H, g.W, g.P, g.plane, tper, g.tlen, w, T, b3, final_relu, xhat,
-                                             R, status);
+        DI_CUDA(launch_pdl(kern, dim3(grid), dim3(kC3Threads), smem, st, in, B, g.H, g.W, g.P, g.plane, tper, g.tlen,
+                           w, T, b3, final_relu, xhat, R, status));
         return DEEPINV_OK;
     };
     if (mode == kConv3RingT) DI_TRY(go(conv3_kernel<CIN, kConv3RingT>));
