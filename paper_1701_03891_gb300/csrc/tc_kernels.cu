@@ -1359,6 +1359,9 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
             if (FUSED && conv3_zero_tile(pstart, H, P)) {
 #pragma unroll
                 for (int dy = 0; dy < 11; ++dy) tv[dy] = 0.f;
+                // the barrier every tile passes before its ring updates: it orders them
+                // after the previous tile's (another warp may hold the same ring slot)
+                epi_bar();
             } else {
             const int it = li++;
             const int s = it & 1, use = it >> 1;
@@ -1390,6 +1393,8 @@ __global__ void __launch_bounds__(kC3Threads) conv3_kernel(const bf16* __restric
                         hd[q4] = make_float4(hs[4 * q4], hs[4 * q4 + 1], hs[4 * q4 + 2], hs[4 * q4 + 3]);
                 }
             }
+            // also the per-tile barrier that orders this tile's ring updates after the
+            // previous tile's
             if (epi_bar_or3(!ok)) return false;
             // rows past this warp come from the next warp's halo sums (never needed by
             // warp 3's valid rows; the index is clamped so that the read stays in bounds)

@@ -275,6 +275,35 @@ def test_forward_bf16_full_batch_sampled(di):
     net.close()
 
 
+@pytest.mark.parametrize("n,B", [(256, 32), (128, 48), (64, 512)])
+def test_forward_bf16_multi_image_ranges_deterministic(di, n, B):
+    """Batches whose per-CTA tile ranges cross many image boundaries, in both of
+    conv3's ring modes (pitch >= 125: one partial sum per pending output; < 125:
+    row sums) and with conv1's window ring: every image against the float32 path
+    (an independent set of kernels), two sampled images against the oracle, and
+    three repeated passes bit for bit (a race between the tiles of a CTA shows up
+    as a difference)."""
+    phi, params, x = _case(n, n, 0.10, B, images="voronoi", bias_std=0.01)
+    xd = _cuda(x)
+    net = di.Net(phi, params, n, n, prec="bf16")
+    y = net.measure(xd)
+    runs = [net.forward(y).cpu().numpy() for _ in range(3)]
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r, runs[0])
+    xhat = runs[0]
+    netf = di.Net(phi, params, n, n, prec="f32")
+    xf = netf.forward(netf.measure(xd)).cpu().numpy()
+    netf.close()
+    idx = np.array([0, B - 1])
+    ref = oracle.forward(oracle.measure(phi, x[idx]), params, n, n, phi=phi)
+    rnd = rounded.forward_bf16(rounded.measure_bf16(phi, x[idx]), params, n, n, phi=phi)
+    floor, _ = check_images(xhat[idx], ref, rnd, what=("multi-image", n, B))
+    allrel = oracle.rel_l2(xhat, xf)
+    assert float(allrel.max()) <= TOL["bf16"], (n, B, float(allrel.max()), int(np.argmax(allrel)))
+    assert float(allrel.max()) <= 1.25 * 1.25 * floor, (n, B, float(allrel.max()), floor)
+    net.close()
+
+
 def test_forward_batch_sizes_reuse_workspace(di):
     """Growing and shrinking the batch on one network keeps results exact (zero borders preserved)."""
     phi, params, x = _case(32, 32, 0.1, 40)
