@@ -45,6 +45,7 @@ def _cuda(a):
     (64, 64, 0.10, 4, "voronoi"),
     (64, 64, 0.25, 3, "dct"),
     (128, 128, 0.05, 2, "voronoi"),     # row mode
+    (128, 128, 0.05, 8, "voronoi"),     # conv1's window ring, CTA tile ranges across images
     (20, 37, 0.20, 3, "dct"),           # ragged
 ])
 def test_forward_fp8(di, n1, n2, ratio, B, images):
@@ -60,6 +61,7 @@ def test_forward_fp8(di, n1, n2, ratio, B, images):
         net.forward(y)                       # not calibrated yet
     net.calibrate(y)
     xhat = net.forward(y).cpu().numpy()
+    np.testing.assert_array_equal(net.forward(y).cpu().numpy(), xhat)   # deterministic
     ref = oracle.forward(oracle.measure(phi, x), params, n1, n2, phi=phi)
     yb = rounded.measure_bf16(phi, x)
     rnd = rounded.forward_e4m3(yb, params, n1, n2, phi=phi, amax_a1=rounded.amax_a1(yb, params, n1, n2, phi=phi))
