@@ -93,11 +93,20 @@ __global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_
             acc[0] += __bfloat162float(src[(size_t)b * plane_len + p]);
     } else {
         const uint4* s4 = reinterpret_cast<const uint4*>(src + (((size_t)b * nch + ch) * plane_len) * 8);
-        for (int p = threadIdx.x; p < plane_len; p += blockDim.x) {
-            const uint4 u = s4[p];
-            const bf16* v = reinterpret_cast<const bf16*>(&u);
+        // four positions of this thread's sequence loaded before they are added (the
+        // same order of additions as one at a time, with the loads in flight together)
+        const int bd = blockDim.x;
+        for (int p = threadIdx.x; p < plane_len; p += 4 * bd) {
+            uint4 u[4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(v[e]);
+            for (int k = 0; k < 4; ++k) u[k] = p + k * bd < plane_len ? s4[p + k * bd] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (p + k * bd >= plane_len) break;
+                const bf16* v = reinterpret_cast<const bf16*>(&u[k]);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(v[e]);
+            }
         }
     }
     __shared__ double red[8][8];
