@@ -229,6 +229,7 @@ void scheduler(deepinv_server* s)
 {
     cudaSetDevice(s->dev);
     std::vector<deepinv_result> ready;
+    auto last_progress = std::chrono::steady_clock::now();
     while (true) {
         bool progressed = false;
         // 1. collect finished batches (results copied out without the lock)
@@ -305,10 +306,19 @@ void scheduler(deepinv_server* s)
         }
         for (const auto& q : s->pending) any_pending |= !q.empty();
         if (s->stop && !any_busy && !any_pending) break;
-        if (progressed) continue;
+        if (progressed) {
+            last_progress = std::chrono::steady_clock::now();
+            continue;
+        }
         if (any_busy) {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            // batches in flight: poll their events by yielding (a sleep of a few
+            // microseconds lasts tens of them on a loaded host) for up to 2 ms after
+            // the last progress, then sleep between polls
+            if (std::chrono::steady_clock::now() - last_progress < std::chrono::milliseconds(2))
+                std::this_thread::yield();
+            else
+                std::this_thread::sleep_for(std::chrono::microseconds(10));
         } else {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
         }
