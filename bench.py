@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-deep", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-ratios", action="store_true")
     ap.add_argument("--fused-steps", type=int, default=20)
     ap.add_argument("--deep-steps", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=10)
@@ -287,6 +288,48 @@ def roofline(stage_ms, B, n, M, pk, clk):
                             "peak": pk["bf16"], "unit": "TFLOP/s", "frac": conv_tflops / pk["bf16"],
                             "note": "conv1 + conv2 + conv3 (the target: >= 0.5 of dense bf16 peak)"},
             "hbm_stages": {"peak_gbs": pk["hbm"], "peak_note": "hbm_gbs of %s" % src, "stages": hbm}}
+
+
+def ratios_bench(args):
+    """The 64 x 64, batch-1024 workload at the other measurement ratios of the
+    batched-inference configuration (M/N = 0.25 and 0.05; 0.10 is the headline):
+    sense + recover per step, L2 flushed between steps, CUDA events, stage times."""
+    import torch
+    from paper_1701_03891_gb300 import deepinv, synth
+    n, B = 64, args.batch
+    N = n * n
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+    x = synth.voronoi_images(B, n, n, seed=3)
+    xd = torch.from_numpy(x).cuda()
+    for ratio in (0.25, 0.05):
+        M = synth.m_for_ratio(ratio, N)
+        net = deepinv.Net(synth.gaussian_phi(M, N, seed=0), synth.he_params(seed=1), n, n, prec="bf16")
+        net.reserve(B)
+        yd = torch.empty((B, M), device="cuda")
+        xh = torch.empty((B, N), device="cuda")
+        for _ in range(3):
+            net.measure(xd, out=yd)
+            net.forward(yd, out=xh)
+        net.profile(True)
+        times = []
+        for _ in range(args.fused_steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.measure(xd, out=yd)
+            net.forward(yd, out=xh)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = net.profile_read()
+        net.close()
+        ms = sorted(times)[len(times) // 2]
+        out["%.2f" % ratio] = {"M": M, "images_per_s": B / (ms / 1000.0), "ms_per_step": ms,
+                               "stage_ms": {k: v[0] / max(1, v[1]) for k, v in st.items() if v[1]}}
+    out["workload"] = "sense+recover 64x64, batch %d, L2 flushed between steps (median step)" % B
+    return out
 
 
 def large_bench(args):
@@ -812,6 +855,9 @@ def run_native(args):
     deep = None
     if rank == 0 and not args.no_deep:
         deep = optional("deep_64", deep_bench, args)
+    ratios = None
+    if rank == 0 and not args.no_ratios:
+        ratios = optional("ratios_64", ratios_bench, args)
     fused = None
     if rank == 0 and not args.no_fused:
         fused = optional("fused12", fused_bench, args)
@@ -842,7 +888,7 @@ def run_native(args):
                      "bf16_over_fp32": (world * B / (ms_per_step / 1000.0)) / (world * B / (f32_ms / 1000.0)),
                      "bf16_vs_fp32_max_rel_l2": float(rel.max())},
             "e2e": e2e, "serving": serving, "large_256": large, "train_64": train, "deep_64": deep,
-            "fused12": fused,
+            "fused12": fused, "ratios_64": ratios,
             "eval_32": evaluation,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches,
