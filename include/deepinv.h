@@ -51,7 +51,7 @@ typedef enum {
     DEEPINV_EINVAL = -1,       /* bad argument: null pointer, bad size, bad shape */
     DEEPINV_ENOMEM = -2,       /* device allocation failed */
     DEEPINV_ECUDA = -3,        /* a CUDA runtime call failed (message in deepinv_last_error) */
-    DEEPINV_EUNSUPPORTED = -4, /* valid request this build has no kernel for */
+    DEEPINV_EUNSUPPORTED = -4, /* valid request the library has no kernel for */
     DEEPINV_ETIMEOUT = -5,     /* a bounded wait ran out (in a kernel or in the server) */
     DEEPINV_EBUSY = -6         /* the server has requests in flight (deepinv_serve_add_net) */
 } deepinv_status;

@@ -1,5 +1,5 @@
 // TMA tensor-map helpers shared by the kernels that read planes or rows as
-// multi-dimensional boxes: the host-side encoder (the driver's
+// multi-dimensional boxes: the host-side encoder (the CUDA driver API's
 // cuTensorMapEncodeTiled, found through the runtime) and the box loads.
 #pragma once
 
