@@ -209,6 +209,18 @@ int deepinv_net_set_act_budget(deepinv_net* net, size_t bytes);
  * DEEPINV_EINVAL for a NULL net. */
 int deepinv_net_set_fused(deepinv_net* net, int enable);
 
+/* Chooses between two kernels for conv1 (the first layer of Eq. (1), 1 -> 64
+ * filters of 11 x 11, bias and ReLU) in bfloat16 and e4m3 networks.  Row tiles
+ * keep conv1's shifted input windows in tensor memory, where each serves the
+ * tiles of several rows (segments of at most 128 image columns, at most 5 rows
+ * per tile); the other kernel takes tiles of 128 consecutive plane positions.
+ * mode 0: never row tiles; 1 (the default): row tiles where they are faster
+ * (one row of at least 120 columns per tile, e.g. 128 or 256 columns); 2: row
+ * tiles wherever they fill at least 96 of a tile's 128 positions.  Both kernels
+ * issue the same products in the same order and give bit-identical results.
+ * Returns DEEPINV_EINVAL for a NULL net or a mode outside 0..2. */
+int deepinv_net_set_conv1_rows(deepinv_net* net, int mode);
+
 /* x^ = M(y, Omega) (Sec. 4): FC layer, reshape to n1 x n2, conv1 + ReLU,
  * conv2 + ReLU, each hidden layer + ReLU, conv3 (+ ReLU when final_relu).
  * y [B][M] -> xhat [B][N].  `saved` is NULL for inference, or a device buffer

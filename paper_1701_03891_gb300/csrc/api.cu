@@ -127,6 +127,7 @@ struct deepinv_net {
     float* amax_w = nullptr;    // [32] scratch
     bool calibrated = false;
     bool fused12 = false;       // conv1 + conv2 as one kernel in inference passes
+    int conv1_rows = 1;         // conv1 in row tiles: 0 never, 1 where faster, 2 where they fit
     // forward workspace
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -519,8 +520,12 @@ int forward_core(deepinv_net* n, const FwdWs& w, const float* y, int B, float* x
         } else {
             {
                 StageTimer t(n, st, DEEPINV_STAGE_CONV1);
-                DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, n->fp8 ? kConv1OutE4M3 : kConv1OutBF16,
-                                n->inv_sa, nullptr, status, st));
+                const int mode = n->fp8 ? kConv1OutE4M3 : kConv1OutBF16;
+                const int fit = conv1_rows_fit(g);
+                if ((n->conv1_rows == 1 && fit == 2) || (n->conv1_rows == 2 && fit >= 1))
+                    DI_TRY(conv1_rows_tc(xt, B, g, n->w1p, n->b[0], a1, mode, n->inv_sa, status, st));
+                else
+                    DI_TRY(conv1_tc(xt, B, g, n->w1p, n->b[0], a1, mode, n->inv_sa, nullptr, status, st));
             }
             {
                 StageTimer t(n, st, DEEPINV_STAGE_CONV2);
@@ -1299,6 +1304,14 @@ int deepinv_net_set_fused(deepinv_net* net, int enable)
 {
     DI_REQUIRE(net, "net is NULL");
     net->fused12 = enable != 0;
+    return DEEPINV_OK;
+}
+
+int deepinv_net_set_conv1_rows(deepinv_net* net, int mode)
+{
+    DI_REQUIRE(net, "net is NULL");
+    DI_REQUIRE(mode >= 0 && mode <= 2, "conv1 row-tile mode %d (0, 1 or 2)", mode);
+    net->conv1_rows = mode;
     return DEEPINV_OK;
 }
 

@@ -103,6 +103,13 @@ inline int gemm_ksplit(int Mr, int Nc, int NB, int Kp, int num_sms)
 enum { kConv1OutBF16 = 0, kConv1OutE4M3 = 1, kConv1AmaxOnly = 2, kConv1GradMask = 3 };
 int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
              const float* inv_sa, float* amax, int* status, cudaStream_t st);
+// conv1 in row tiles with its A operands kept in TMEM (kConv1OutBF16 or
+// kConv1OutE4M3 only; same output, bit for bit, as conv1_tc).  conv1_rows_fit:
+// 0 where row tiles would fill fewer than 96 of 128 positions, 1 where they fit,
+// 2 where they also measured faster than conv1_tc.
+int conv1_rows_fit(const Geo& g);
+int conv1_rows_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
+                  const float* inv_sa, int* status, cudaStream_t st);
 // conv2: a1 (bf16, or e4m3 when fp8) -> a2 bf16 [B][4][plane][8] (bias, ReLU,
 // zero pad columns); the e4m3 path multiplies the accumulators by oscale[co].
 int conv2_tc(const void* a1, int B, const Geo& g, const void* w2p, const float* b2, const float* oscale,

@@ -16,6 +16,8 @@
 //
 // Operands are K-major without swizzle (see tc.cuh; conv1's A is MN-major),
 // moved by the TMA engine with 1-D bulk copies; accumulators live in TMEM.
+#include <algorithm>
+#include <climits>
 #include <cstdlib>
 
 #include <cuda_fp8.h>
@@ -731,6 +733,371 @@ __global__ void __launch_bounds__(kC1Threads, 2) conv1_kernel(const bf16* __rest
     if (warp == 12) {
         tc_fence_after();
         tmem_dealloc(tbase, TCOLS);
+    }
+}
+
+// ---------------------------------------------------------------- conv1, row tiles
+// The same 11 MMAs per tile as conv1_kernel (kernel row dy: M = 128 positions,
+// N = 64 filters, K = 16 columns dx, weights of dx >= 11 zero, issued in the
+// same order), with the A operand in tensor memory and tiles aligned to image
+// rows so that one A operand serves several tiles.  The image's columns are cut
+// into nseg segments of Sw <= 128; a tile is R = 128 / Sw rows (at most
+// kC1RMaxRows) of one segment, position m = i Sw + c (row i, column c) in TMEM
+// lane m.  Kernel row dy of the tile whose first row is h0 reads the window
+//   A_s(m, k) = x~[(s + i) P + c0 + c + k],   s = h0 + dy,
+// which depends on s alone: the tile R rows further down reads the same window
+// at dy - R.  A CTA walks its tiles in runs down a column of tiles (one image
+// segment); a run of tiles rb0..rb1 reads windows s = R rb0 .. R rb1 + 10, each
+// built once into a ring of kC1RSlots TMEM slots of 8 columns (16 bf16 of K per
+// lane) and handed back once the last tile that reads it has its MMAs completed.
+// Only image positions are computed; each tile's epilogue writes the zeros of
+// the pad columns right of its rows.  Shared memory holds the weights and a ring
+// of x~ row pieces, so the tensor core's shared-memory reads per tile are the 11
+// B operands alone.
+//
+// Warp 13 copies the plane row pieces a run reads (Sw + 15 values from column
+// c0, widened to 16-byte bounds) into a ring of kC1RRows slots with bulk copies.
+// Warps 8..11 build windows: warp 8 + q owns TMEM lane quarter q; each thread
+// reads the three 16-byte pieces around its 16 values from its row's slot (8
+// neighbouring lanes read the same piece), shifts them into place and stores
+// them with tcgen05.st.  Warp 12 owns TMEM (2 accumulators of 64 columns, then
+// the window slots) and one of its threads issues the MMAs, committing each
+// tile to its accumulator's barrier and to a tile-done barrier the builders
+// wait on before reusing a slot.  Warps 0..7 drain an accumulator as in
+// conv1_kernel (bias, ReLU, bf16 or scaled e4m3, 16-byte stores).
+constexpr int kC1RThreads = 448;
+constexpr int kC1RSlots = 16;
+constexpr int kC1RMaxRows = kC1RSlots - 11;   // 11 windows in use + R being built
+constexpr uint32_t kC1RCols = 256;            // 2 x 64 accumulator columns + 16 x 8 slot columns
+constexpr int kC1RRows = 32;                  // x~ row piece slots
+constexpr int kC1RRowElems = 160;             // >= 7 + 127 + 24 values a slot is read at
+constexpr uint32_t kC1RRowBytes = kC1RRows * kC1RRowElems * 2;
+constexpr int kC1RDone = 8;                   // tile-done barriers
+constexpr int kC1RChunk = 3;                  // windows a builder pass produces
+
+// Tiles of an image: nseg column segments of Sw columns (the last may be
+// narrower) x nrb row blocks of R rows.
+struct Conv1RGeo {
+    int R, Sw, nseg, nrb;
+};
+// Row tiles are built where they fill at least 96 of the 128 TMEM lanes.
+static inline bool conv1_rows_geo(const Geo& g, Conv1RGeo& r)
+{
+    r.nseg = cdiv(g.W, 128);
+    r.Sw = cdiv(g.W, r.nseg);
+    r.R = std::min(128 / r.Sw, kC1RMaxRows);
+    r.nrb = cdiv(g.H, r.R);
+    return r.R * r.Sw >= 96;
+}
+
+struct Conv1RSmem {
+    alignas(16) float bias[64];
+    uint64_t wbar;
+    uint64_t rfull[kC1RRows], rempty[kC1RRows];
+    uint64_t wfull[kC1RSlots];
+    uint64_t tdone[kC1RDone];
+    uint64_t afull[2], aempty[2];
+    uint64_t drain;
+    int rel[4][kC1RSlots];                    // per builder warp: tile that hands back each slot's window
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// A run: tiles rb0..rb1 of column col (image b, segment starting at column c0).
+struct Conv1RRun {
+    int rb0, rb1, b, c0;
+};
+__device__ __forceinline__ Conv1RRun c1r_run(int tile, int hi, int nrb, int nseg, int Sw)
+{
+    const int col = tile / nrb, rb0 = tile - col * nrb;
+    const int b = col / nseg;
+    return {rb0, min(nrb - 1, rb0 + (hi - 1 - tile)), b, (col - b * nseg) * Sw};
+}
+
+// 16 consecutive bf16 starting at element o (0..7) of the 24 held in a, b, c,
+// as 8 words (element 2 j in the low half of word j).
+__device__ __forceinline__ void c1r_shift16(const uint4& a, const uint4& b, const uint4& c, int o, uint32_t* r)
+{
+    const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    uint32_t v[10], u[9];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) v[j] = (o & 4) ? w[j + 2] : w[j];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) u[j] = (o & 2) ? v[j + 1] : v[j];
+    const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = __byte_perm(u[j], u[j + 1], sel);
+}
+
+__global__ void __launch_bounds__(kC1RThreads, 2) conv1_rows_kernel(const bf16* __restrict__ xt, int B, int H,
+                                                                    int W, int P, int plane_len, Conv1RGeo rg,
+                                                                    const bf16* __restrict__ w1p,
+                                                                    const float* __restrict__ b1,
+                                                                    void* __restrict__ a1, int mode,
+                                                                    const float* __restrict__ inv_sa, int* status)
+{
+    constexpr uint32_t BBYTES = conv1_wbytes(64);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sB = smem_raw;
+    uint8_t* sRow = smem_raw + BBYTES;                         // [kC1RRows][kC1RRowElems] bf16
+    Conv1RSmem* ss = reinterpret_cast<Conv1RSmem*>(sRow + kC1RRowBytes);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int R = rg.R, Sw = rg.Sw, nrb = rg.nrb, nseg = rg.nseg;
+    const int ntiles = B * nseg * nrb;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&ss->wbar), 1);
+        for (int j = 0; j < kC1RRows; ++j) {
+            mbar_init(smem_u32(&ss->rfull[j]), 1);
+            mbar_init(smem_u32(&ss->rempty[j]), 4);
+        }
+        for (int j = 0; j < kC1RSlots; ++j) mbar_init(smem_u32(&ss->wfull[j]), 4);
+        for (int j = 0; j < kC1RDone; ++j) mbar_init(smem_u32(&ss->tdone[j]), 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&ss->afull[s]), 1);
+            mbar_init(smem_u32(&ss->aempty[s]), 8);
+        }
+        mbar_init(smem_u32(&ss->drain), 1);
+        ss->abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (threadIdx.x < 64) ss->bias[threadIdx.x] = b1 ? __ldg(&b1[threadIdx.x]) : 0.f;
+    if (warp == 12) {
+        tmem_alloc(smem_u32(&ss->tmem_base), kC1RCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = ss->tmem_base;
+    pdl_wait();
+    pdl_trigger();
+    const TileRange tr = tile_range(ntiles, blockIdx.x, gridDim.x);
+
+    if (warp == 13) {
+        // ------------------------------------------------ x~ row pieces
+        if (lane == 0) {
+            uint32_t k = 0;
+            bool ok = true;
+            for (int tile = tr.lo; tile < tr.hi && ok;) {
+                const Conv1RRun run = c1r_run(tile, tr.hi, nrb, nseg, Sw);
+                const bf16* img = xt + (size_t)run.b * plane_len;
+                const int r1 = R * run.rb1 + 10 + R - 1;
+                for (int r = R * run.rb0; r <= r1; ++r, ++k) {
+                    const uint32_t slot = k % kC1RRows;
+                    ok = mbar_wait(smem_u32(&ss->rempty[slot]), ((k / kC1RRows) & 1) ^ 1, status, &ss->abort_flag);
+                    if (!ok) break;
+                    const int e0 = r * P + run.c0, ea = e0 & ~7;
+                    const int ee = min((e0 + Sw + 15 + 7) & ~7, plane_len);
+                    if (ee > ea) {
+                        mbar_arrive_expect_tx(smem_u32(&ss->rfull[slot]), (uint32_t)(ee - ea) * 2u);
+                        bulk_g2s(smem_u32(sRow + slot * (kC1RRowElems * 2)), img + ea, (uint32_t)(ee - ea) * 2u,
+                                 smem_u32(&ss->rfull[slot]));
+                    } else {
+                        mbar_arrive(smem_u32(&ss->rfull[slot]));   // past the plane: only discarded lanes read it
+                    }
+                }
+                tile += run.rb1 - run.rb0 + 1;
+            }
+            // let copies in flight land before the CTA ends
+            for (uint32_t kk = k > (uint32_t)kC1RRows ? k - kC1RRows : 0; kk < k; ++kk)
+                mbar_wait_drain(smem_u32(&ss->rfull[kk % kC1RRows]), (kk / kC1RRows) & 1);
+        }
+    } else if (warp >= 8 && warp < 12) {
+        // ------------------------------------------------ window builders
+        // Windows go in chunks of up to kC1RChunk consecutive windows of a run: one
+        // wait for their rows, their pieces read and shifted, one wait for their
+        // slots, their TMEM stores issued back to back and completed together.
+        const int q = warp - 8;
+        const int m = threadIdx.x - 256;                      // TMEM lane = 32 q + lane
+        const int mi = m / Sw, mc = m - (m / Sw) * Sw;        // row and column in the tile
+        const bool live = mi < R;
+        const uint32_t tlane = tbase + ((uint32_t)(32 * q) << 16) + 128u;
+        int* rel = ss->rel[q];
+        uint32_t n = 0, k0 = 0, rwaited = 0, rfreed = 0;
+        int it0 = 0;                                          // CTA tile index of the run's first tile
+        bool ok = true;
+        for (int tile = tr.lo; tile < tr.hi && ok;) {
+            const Conv1RRun run = c1r_run(tile, tr.hi, nrb, nseg, Sw);
+            const int s0 = R * run.rb0, s1 = R * run.rb1 + 10;
+            for (int sa = s0; sa <= s1; sa += kC1RChunk) {
+                const int g = min(kC1RChunk, s1 - sa + 1);
+                // rows sa .. sa + g - 1 + R - 1 of the run: row numbers k0 + (row - s0)
+                const uint32_t kmax = k0 + (uint32_t)(sa + g - 1 - s0 + R - 1);
+                for (; rwaited <= kmax && ok; ++rwaited)
+                    ok = mbar_wait(smem_u32(&ss->rfull[rwaited % kC1RRows]), (rwaited / kC1RRows) & 1, status,
+                                   &ss->abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                uint32_t r[kC1RChunk][8];
+#pragma unroll
+                for (int j = 0; j < kC1RChunk; ++j) {
+                    if (j < g) {
+                        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, x2 = x0;
+                        int o = 0;
+                        if (live) {
+                            const int e0 = (sa + j + mi) * P + run.c0;
+                            const int off = (e0 & 7) + mc;
+                            const uint32_t a = smem_u32(sRow) +
+                                               ((k0 + (uint32_t)(sa + j - s0 + mi)) % kC1RRows) * (kC1RRowElems * 2) +
+                                               (uint32_t)(off & ~7) * 2u;
+                            x0 = lds128(a);
+                            x1 = lds128(a + 16);
+                            x2 = lds128(a + 32);
+                            o = off & 7;
+                        }
+                        c1r_shift16(x0, x1, x2, o, r[j]);
+                    }
+                }
+                // rows no later window of the run reads go back to the copier
+                __syncwarp();
+                const int slast = sa + g - 1;
+                const uint32_t kfree = slast < s1 ? k0 + (uint32_t)(slast - s0) : kmax;
+                if (lane == 0)
+                    for (uint32_t kk = rfreed; kk <= kfree; ++kk) mbar_arrive(smem_u32(&ss->rempty[kk % kC1RRows]));
+                rfreed = kfree + 1;
+                // the chunk's slots: free once the tile that read the last of their previous
+                // windows is done (tiles complete in order)
+                const uint32_t nlast = n + (uint32_t)g - 1u;
+                if (nlast >= (uint32_t)kC1RSlots) {
+                    const int itr = rel[nlast % kC1RSlots];
+                    ok = mbar_wait(smem_u32(&ss->tdone[itr % kC1RDone]), (itr / kC1RDone) & 1, status,
+                                   &ss->abort_flag);
+                }
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                if (lane == 0)
+                    for (int j = 0; j < g; ++j) rel[(n + (uint32_t)j) % kC1RSlots] = it0 + min((sa + j) / R, run.rb1) - run.rb0;
+                tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < kC1RChunk; ++j)
+                    if (j < g) tmem_st8_async(tlane + 8u * ((n + (uint32_t)j) % kC1RSlots), r[j]);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    for (int j = 0; j < g; ++j) mbar_arrive(smem_u32(&ss->wfull[(n + (uint32_t)j) % kC1RSlots]));
+                n += (uint32_t)g;
+            }
+            k0 += (uint32_t)(s1 - s0 + R);
+            it0 += run.rb1 - run.rb0 + 1;
+            tile += run.rb1 - run.rb0 + 1;
+        }
+    } else if (warp == 12) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            bool ok = true;
+            if (tr.lo < tr.hi) {
+                mbar_arrive_expect_tx(smem_u32(&ss->wbar), BBYTES);
+                bulk_g2s(smem_u32(sB), w1p, BBYTES, smem_u32(&ss->wbar));
+                ok = mbar_wait(smem_u32(&ss->wbar), 0, status, &ss->abort_flag);
+                if (!ok) mbar_wait_drain(smem_u32(&ss->wbar), 0);
+            }
+            const uint32_t idesc = idesc_bf16(128, 64);      // A from TMEM, B K-major
+            uint64_t bd[11];
+#pragma unroll
+            for (int dy = 0; dy < 11; ++dy) bd[dy] = sdesc(smem_u32(sB + dy * 2 * 64 * 16), 64 * 16, 128);
+            uint32_t waited = 0, nrun = 0;
+            int it = 0;
+            for (int tile = tr.lo; tile < tr.hi && ok;) {
+                const Conv1RRun run = c1r_run(tile, tr.hi, nrb, nseg, Sw);
+                for (int rb = run.rb0; rb <= run.rb1; ++rb, ++it) {
+                    const uint32_t n0 = nrun + (uint32_t)(R * (rb - run.rb0));   // window of kernel row 0
+                    for (; waited <= n0 + 10u && ok; ++waited)
+                        ok = mbar_wait(smem_u32(&ss->wfull[waited % kC1RSlots]), (waited / kC1RSlots) & 1, status,
+                                       &ss->abort_flag);
+                    if (!ok) break;
+                    const int a = it & 1, ause = it >> 1;
+                    if (!mbar_wait(smem_u32(&ss->aempty[a]), (ause & 1) ^ 1, status, &ss->abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tbase + (uint32_t)(64 * a);
+#pragma unroll
+                    for (int dy = 0; dy < 11; ++dy)
+                        mma_bf16_ta(d, tbase + 128u + 8u * ((n0 + (uint32_t)dy) % kC1RSlots), bd[dy], idesc,
+                                    dy > 0 ? 1u : 0u);
+                    mma_commit(smem_u32(&ss->afull[a]));
+                    mma_commit(smem_u32(&ss->tdone[it % kC1RDone]));
+                }
+                nrun += (uint32_t)(R * (run.rb1 - run.rb0) + 11);
+                tile += run.rb1 - run.rb0 + 1;
+            }
+            mma_commit(smem_u32(&ss->drain));
+            mbar_wait_drain(smem_u32(&ss->drain), 0);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 0..7)
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const int mi = m / Sw, mc = m - (m / Sw) * Sw;
+        const float isa = mode == kConv1OutE4M3 ? __ldg(inv_sa) : 1.f;
+        const int nch = conv1_out_chunks(64, mode);
+        const int wch = nch / 2;
+        const size_t cstride = (size_t)plane_len * 16;
+        int col = tr.lo / nrb, rb = tr.lo % nrb;
+        for (int tile = tr.lo, it = 0; tile < tr.hi; ++tile, ++it) {
+            if (tile > tr.lo && ++rb == nrb) {
+                rb = 0;
+                ++col;
+            }
+            const int b = col / nseg, sg = col - b * nseg;
+            uint8_t* img = reinterpret_cast<uint8_t*>(a1) + (size_t)b * nch * cstride;
+            // the 5 pad positions right of each row of the last segment hold zeros
+            // (R * 5 * nch <= 200 16-byte chunks: one per thread at most)
+            if (sg == nseg - 1) {
+                const int per_row = kPad * nch, e = half * 128 + m;
+                const int i = e / per_row, rem = e - i * per_row;
+                const int j = rem / nch, ch = rem - j * nch;
+                const int hh = R * rb + i;
+                if (i < R && hh < H)
+                    *reinterpret_cast<uint4*>(img + ch * cstride + ((size_t)(hh + kPad + 1) * P + j) * 16) =
+                        make_uint4(0, 0, 0, 0);
+            }
+            const int a = it & 1, ause = it >> 1;
+            const bool ok = mbar_wait(smem_u32(&ss->afull[a]), ause & 1, status, &ss->abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            float v[32];
+            tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(64 * a + 32 * half), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ss->aempty[a]));
+            const int h = R * rb + mi, w = sg * Sw + mc;
+            const bool valid = mi < R && h < H && w < W;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+                const float4 bb = *reinterpret_cast<const float4*>(&ss->bias[32 * half + i]);
+                v[i] = fmaxf(v[i] + bb.x, 0.f);
+                v[i + 1] = fmaxf(v[i + 1] + bb.y, 0.f);
+                v[i + 2] = fmaxf(v[i + 2] + bb.z, 0.f);
+                v[i + 3] = fmaxf(v[i + 3] + bb.w, 0.f);
+            }
+            if (valid) {
+                uint8_t* so = img + half * wch * cstride + ((size_t)(h + kPad) * P + kPad + w) * 16;
+                if (mode == kConv1OutBF16) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(so + c * cstride) = pack8_bf16(v + 8 * c);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+                        *reinterpret_cast<uint4*>(so + c * cstride) = pack16_e4m3(v + 16 * c, isa);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 12) {
+        tc_fence_after();
+        tmem_dealloc(tbase, kC1RCols);
     }
 }
 
@@ -1670,6 +2037,39 @@ int conv1_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* 
     DI_CUDA(cudaFuncSetAttribute(conv1_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DI_CUDA(launch_pdl(conv1_kernel<64>, dim3(grid), dim3(kC1Threads), smem, st, xt, B, g.H, g.W, g.P, g.plane, g.t1,
                        w1p, b1, a1, mode, inv_sa, amax, (const bf16*)nullptr, ering, status));
+    DI_LAUNCH_CHECK();
+    return DEEPINV_OK;
+}
+
+int conv1_rows_fit(const Geo& g)
+{
+    Conv1RGeo r;
+    if (!conv1_rows_geo(g, r)) return 0;
+    // measured (GB300, bf16): one row of >= 120 columns per tile is faster than the
+    // consecutive-position tiles (256 x 256: 0.51-0.53 against 0.56-0.57 ms at batch
+    // 256; 128 x 128: 0.288 against 0.296 ms at batch 512); several rows per tile
+    // (64 x 64: 0.196 against 0.157 ms) or partly filled tiles (100 x 100: 0.22
+    // against 0.19 ms) are slower
+    return r.R == 1 && r.Sw >= 120 ? 2 : 1;
+}
+
+int conv1_rows_tc(const bf16* xt, int B, const Geo& g, const bf16* w1p, const float* b1, void* a1, int mode,
+                  const float* inv_sa, int* status, cudaStream_t st)
+{
+    if (B <= 0) return DEEPINV_OK;
+    DI_REQUIRE(mode == kConv1OutBF16 || mode == kConv1OutE4M3, "conv1 row tiles: bf16 or e4m3 output only");
+    Conv1RGeo r;
+    DI_REQUIRE(conv1_rows_geo(g, r), "conv1 row tiles: fewer than 96 positions per tile");
+    const long long ntiles = (long long)B * r.nseg * r.nrb;
+    DI_REQUIRE(ntiles < INT_MAX, "conv1 row tiles: too many tiles");
+    const size_t smem = conv1_wbytes(64) + kC1RRowBytes + sizeof(Conv1RSmem) + 16;
+    int dev = 0, sms = 0;
+    DI_CUDA(cudaGetDevice(&dev));
+    DI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
+    DI_CUDA(cudaFuncSetAttribute(conv1_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DI_CUDA(launch_pdl(conv1_rows_kernel, dim3(grid), dim3(kC1RThreads), smem, st, xt, B, g.H, g.W, g.P, g.plane, r,
+                       w1p, b1, a1, mode, inv_sa, status));
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }

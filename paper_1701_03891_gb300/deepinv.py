@@ -81,6 +81,7 @@ SIGNATURES = {
     "deepinv_net_reserve": (_I, [_P, _I, _P]),
     "deepinv_net_set_act_budget": (_I, [_P, ctypes.c_size_t]),
     "deepinv_net_set_fused": (_I, [_P, _I]),
+    "deepinv_net_set_conv1_rows": (_I, [_P, _I]),
     "deepinv_net_measure": (_I, [_P, _P, _I, _P, _P]),
     "deepinv_saved_bytes": (ctypes.c_size_t, [_P, _I]),
     "deepinv_forward": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -395,6 +396,11 @@ class Net:
     def set_fused(self, enable: bool):
         """conv1 + conv2 as one fused kernel in inference forward passes (bf16 networks)."""
         _check(lib().deepinv_net_set_fused(self._h, 1 if enable else 0))
+
+    def set_conv1_rows(self, mode: int):
+        """conv1 in row tiles with its input windows in TMEM: 0 never, 1 where they
+        are faster (the default), 2 wherever they fit."""
+        _check(lib().deepinv_net_set_conv1_rows(self._h, int(mode)))
 
     def backward(self, y, x, saved=None, grads=None, stream=None):
         """Gradient of L = (1/B) sum_b ||x^_b - x_b||^2 (Sec. 4).  Returns (loss tensor, dW, db, dWfc).
