@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-deep", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-ratios", action="store_true")
+    ap.add_argument("--conv1-rows", type=int, default=1, choices=[0, 1, 2],
+                    help="conv1 kernel of the headline network: 0 position tiles, 1 row tiles where "
+                         "faster (the library default), 2 row tiles wherever they fit")
     ap.add_argument("--fused-steps", type=int, default=20)
     ap.add_argument("--deep-steps", type=int, default=10)
     ap.add_argument("--train-steps", type=int, default=10)
@@ -738,6 +741,7 @@ def run_native(args):
     pk = peaks()
 
     net = deepinv.Net(phi, params, n, n, prec="bf16")
+    net.set_conv1_rows(args.conv1_rows)
     net.reserve(B)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty((B, M), device="cuda")
