@@ -11,6 +11,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -63,6 +64,80 @@ double us_between(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double, std::micro>(b - a).count();
 }
 
+// Helper threads that share a batch's per-request host copies (staging the
+// measurements, handing back the results) with the scheduler thread: at a few
+// hundred thousand requests per second those copies are several GB/s, more
+// than one thread moves.  run(n, f) calls f(i) once for every i < n, on the
+// calling thread and on the helpers, and returns when all calls have returned.
+struct CopyPool {
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    const std::function<void(int)>* job = nullptr;
+    int n = 0, next = 0, active = 0;
+    uint64_t gen = 0;
+    bool stop = false;
+
+    void worker()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            cv.wait(lk, [&] { return stop || gen != seen; });
+            if (stop) return;
+            seen = gen;
+            ++active;
+            while (next < n) {
+                const int i = next++;
+                const std::function<void(int)>* f = job;
+                lk.unlock();
+                (*f)(i);
+                lk.lock();
+            }
+            if (--active == 0) cv_done.notify_all();
+        }
+    }
+    void start(int helpers)
+    {
+        for (int k = 0; k < helpers; ++k) th.emplace_back([this] { worker(); });
+    }
+    void run(int count, const std::function<void(int)>& f)
+    {
+        if (th.empty() || count < 2) {
+            for (int i = 0; i < count; ++i) f(i);
+            return;
+        }
+        std::unique_lock<std::mutex> lk(mu);
+        job = &f;
+        n = count;
+        next = 0;
+        ++gen;
+        cv.notify_all();
+        while (next < n) {
+            const int i = next++;
+            lk.unlock();
+            f(i);
+            lk.lock();
+        }
+        cv_done.wait(lk, [&] { return active == 0; });
+        job = nullptr;
+        n = next = 0;
+    }
+    void shutdown()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (std::thread& t : th) t.join();
+        th.clear();
+    }
+};
+
+// Batches whose copies are smaller than this stay on the scheduler thread.
+constexpr size_t kParallelCopyBytes = 256 << 10;
+
 }  // namespace
 
 struct deepinv_server {
@@ -83,6 +158,7 @@ struct deepinv_server {
     bool stop = false, started = false, waiting_admission = false;
     uint64_t outstanding = 0;   // submitted and not yet finished
     deepinv_serve_stats stats{};
+    CopyPool copies;            // used by the scheduler thread only
 };
 
 namespace {
@@ -157,9 +233,17 @@ void collect_slot(deepinv_server* s, Slot& sl, int status, std::vector<deepinv_r
 {
     const int N = net_N(s->nets[sl.net]);
     const auto now = Clock::now();
+    if (status == DEEPINV_OK) {
+        const std::function<void(int)> copy = [&](int i) {
+            std::memcpy(sl.reqs[i].xhat, sl.x_pin + (size_t)i * N, (size_t)N * sizeof(float));
+        };
+        const int b = (int)sl.reqs.size();
+        if ((size_t)b * N * sizeof(float) >= kParallelCopyBytes) s->copies.run(b, copy);
+        else
+            for (int i = 0; i < b; ++i) copy(i);
+    }
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
         Req& r = sl.reqs[i];
-        if (status == DEEPINV_OK) std::memcpy(r.xhat, sl.x_pin + i * (size_t)N, (size_t)N * sizeof(float));
         deepinv_result res{};
         res.tag = r.tag;
         res.status = status;
@@ -197,7 +281,12 @@ int launch(deepinv_server* s, Slot& sl, int net, Lease* lease, std::vector<deepi
     deepinv_net* n = s->nets[net];
     const int M = net_M(n), N = net_N(n);
     const int b = (int)sl.reqs.size();
-    for (int i = 0; i < b; ++i) std::memcpy(sl.y_pin + (size_t)i * M, sl.reqs[i].y.data(), (size_t)M * sizeof(float));
+    const std::function<void(int)> stage = [&](int i) {
+        std::memcpy(sl.y_pin + (size_t)i * M, sl.reqs[i].y.data(), (size_t)M * sizeof(float));
+    };
+    if ((size_t)b * M * sizeof(float) >= kParallelCopyBytes) s->copies.run(b, stage);
+    else
+        for (int i = 0; i < b; ++i) stage(i);
     sl.net = net;
     sl.lease = lease;
     sl.t_launch = Clock::now();
@@ -228,6 +317,10 @@ int launch(deepinv_server* s, Slot& sl, int net, Lease* lease, std::vector<deepi
 void scheduler(deepinv_server* s)
 {
     cudaSetDevice(s->dev);
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        s->copies.start(hw >= 8 ? 3 : (hw >= 4 ? 1 : 0));
+    }
     std::vector<deepinv_result> ready;
     auto last_progress = std::chrono::steady_clock::now();
     while (true) {
@@ -323,6 +416,7 @@ void scheduler(deepinv_server* s)
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
         }
     }
+    s->copies.shutdown();
     std::lock_guard<std::mutex> lk(s->mu);
     s->cv_done.notify_all();
 }
