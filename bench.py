@@ -585,6 +585,7 @@ def deep_bench(args):
 
 SERVE_SIZES = (32, 64, 128)
 SERVE_RATIOS = (0.05, 0.10, 0.25)
+SERVE_MAX_BATCH = 256   # requests per batch at most; batches take what has queued
 
 
 def serving_bench(args):
@@ -605,7 +606,7 @@ def serving_bench(args):
             y = (x.astype(np.float64) @ phi.astype(np.float64).T).astype(np.float32)
             nets.append(net)
             pools.append((np.ascontiguousarray(y), N))
-    srv = deepinv.Server(hbm_budget_bytes=40 << 30, max_streams=4, max_batch=64)
+    srv = deepinv.Server(hbm_budget_bytes=40 << 30, max_streams=4, max_batch=SERVE_MAX_BATCH)
     for net in nets:
         srv.add(net)
     # warm-up: every network runs a few batches first (the kernels' first launches
@@ -676,8 +677,9 @@ def serving_bench(args):
     sat = max(p["images_per_s"] for p in points) if points else None
     behind = [p["offered_rps"] for p in points if p["images_per_s"] < 0.9 * p["offered_rps"]]
     return {"workload": "9 bf16 networks: %s x M/N %s; Poisson arrivals, uniform over classes; "
-                        "4 streams, batches <= 64, 40 GB budget" % ("/".join("%d^2" % n for n in SERVE_SIZES),
-                                                                   "/".join(str(r) for r in SERVE_RATIOS)),
+                        "4 streams, batches <= %d, 40 GB budget" % ("/".join("%d^2" % n for n in SERVE_SIZES),
+                                                                   "/".join(str(r) for r in SERVE_RATIOS),
+                                                                   SERVE_MAX_BATCH),
             "latency": "scheduled arrival -> result in the request's host buffer",
             "points": points, "saturation_images_per_s": sat,
             "first_offered_rps_not_kept_up": behind[0] if behind else None,
