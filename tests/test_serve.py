@@ -91,6 +91,41 @@ def test_mixed_stream_equals_alone(di, prec, hidden):
     assert float(oracle.rel_l2(xh[None], ref)[0]) <= (1e-2 if prec == "bf16" else 1e-5)
 
 
+def test_large_batches_parallel_copies(di):
+    """Batches of up to 128 requests of 64 x 64 and 128 x 128 networks, whose
+    staging and result copies the server splits between its threads: every result
+    lands in its own buffer, bit-identical to the network run alone."""
+    import torch
+    nets = []
+    for i, (n, r) in enumerate([(128, 0.10), (64, 0.25)]):
+        N = n * n
+        phi = synth.gaussian_phi(synth.m_for_ratio(r, N), N, seed=40 + i)
+        p = synth.he_params(seed=50 + i, bias_std=0.01)
+        nets.append((di.Net(phi, p, n, n, prec="bf16"), phi, p, n, n))
+    srv = di.Server(hbm_budget_bytes=8 << 30, max_streams=2, max_batch=128)
+    for n in nets:
+        srv.add(n[0])
+    rng = np.random.default_rng(3)
+    reqs = []
+    for t in range(400):
+        k = int(rng.integers(0, 2))
+        net, phi, p, n1, n2 = nets[k]
+        y = rng.standard_normal(phi.shape[0]).astype(np.float32)
+        reqs.append((k, y, np.full(n1 * n2, np.nan, dtype=np.float32), t))
+    got = _drain(srv, len(reqs), first=reqs)
+    st = srv.stats()
+    srv.close()
+    assert len(got) == len(reqs) and all(r.status == 0 for r in got.values())
+    assert max(r.batch for r in got.values()) > 64          # large batches were formed
+    assert st["batches"] < len(reqs) // 8
+    for k in range(2):
+        mine = [q for q in reqs if q[0] == k]
+        ys = torch.from_numpy(np.stack([q[1] for q in mine])).cuda()
+        alone = nets[k][0].forward(ys).cpu().numpy()
+        for j, (_, y, xh, t) in enumerate(mine):
+            np.testing.assert_array_equal(xh, alone[j])
+
+
 def test_admission_under_tight_budget(di):
     """A budget that holds the largest workspace but not two of them: every request
     still finishes, the workspaces held never exceed the budget, batches wait for
