@@ -170,28 +170,55 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N)
 // positions.  A is an im2col of S built in shared memory (K-major); B is the C
 // plane itself (MN-major, bulk-copied).  Each CTA covers a run of 128-position
 // blocks, keeps its sum in TMEM and leaves a float32 partial.
+//
+// The window of S and the block of C a block reads arrive by bulk copies into a
+// ring of nst <= kTwStages stages (as many as shared memory holds), issued
+// nst - 1 blocks ahead; thread t builds im2col row
+// t from aligned 16-byte reads of the window, shifted into place (the shift is
+// the same for every chunk of the row).
 constexpr int kTwKB = 128;
-constexpr int kTwCtas = 456;          // 3 per SM
+constexpr int kTwStages = 3;
+constexpr int kTwCtas = 304;          // 2 per SM
 
 struct TwSmem {
-    uint64_t lbar, mbar;
+    uint64_t lbar[kTwStages], mbar;
     uint32_t tmem_base;
     int abort_flag;
 };
 
+// Window elements a stage holds: a block's 128 positions, the 10 P + 10 of its
+// taps' reach, rounded up to 16 bytes, and 8 more that the last aligned read of
+// a row may touch (never used).
+__host__ __device__ inline int tw_wlen(int P) { return (kTwKB + 10 * P + 10 + 7) / 8 * 8 + 8; }
+
+// 8 consecutive bf16 starting at element o (0..7) of the 16 held in a, b, as 4
+// words (element 2 j in the low half of word j).
+__device__ __forceinline__ uint4 tw_shift8(const uint4& a, const uint4& b, int o)
+{
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t v[6], u[5];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = (o & 4) ? w[j + 2] : w[j];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) u[j] = (o & 2) ? v[j + 1] : v[j];
+    const uint32_t sel = (o & 1) ? 0x5432u : 0x3210u;
+    return make_uint4(__byte_perm(u[0], u[1], sel), __byte_perm(u[1], u[2], sel), __byte_perm(u[2], u[3], sel),
+                      __byte_perm(u[3], u[4], sel));
+}
+
 template <int CJ, int SGN>
 __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ S, const bf16* __restrict__ C,
-                                                       int B, int P, int HP16, int plane_len,
+                                                       int B, int P, int HP16, int plane_len, int nst,
                                                        float* __restrict__ part, int* status)
 {
     constexpr uint32_t ABYTES = (kTwKB / 8) * 128 * 16;   // [16 chunks][128 rows][8]
     constexpr uint32_t BBYTES = (CJ / 8) * kTwKB * 16;    // [CJ/8 groups][128 positions][8]
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sA = smem_raw;
-    uint8_t* sB = smem_raw + ABYTES;
-    const int wlen = (kTwKB + 10 * P + 10 + 7) / 8 * 8;
-    bf16* sS = reinterpret_cast<bf16*>(sB + BBYTES);
-    TwSmem* ss = reinterpret_cast<TwSmem*>(sB + BBYTES + wlen * 2);
+    uint8_t* sB = smem_raw + ABYTES;                      // [stage][BBYTES]
+    const int wlen = tw_wlen(P);
+    uint8_t* sS = sB + nst * BBYTES;                      // [stage][wlen] bf16
+    TwSmem* ss = reinterpret_cast<TwSmem*>(sS + nst * wlen * 2);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nb_img = (HP16 + kTwKB - 1) / kTwKB;
     const long long total = (long long)B * nb_img;
@@ -199,7 +226,7 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
     const int u_begin = kPad * P + kPad;
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&ss->lbar), 1);
+        for (int s = 0; s < nst; ++s) mbar_init(smem_u32(&ss->lbar[s]), 1);
         mbar_init(smem_u32(&ss->mbar), 1);
         ss->abort_flag = 0;
         fence_mbar_init();
@@ -212,50 +239,56 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
+    // block k's operands into stage (k - blk0) % nst (thread 0)
+    auto issue = [&](long long k) {
+        const int st = (int)((k - blk0) % nst);
+        const int b = (int)(k / nb_img);
+        const int u0 = u_begin + (int)(k % nb_img) * kTwKB;
+        const int npos = min(kTwKB, u_begin + HP16 - u0);
+        const uint32_t bar = smem_u32(&ss->lbar[st]);
+        // the part of the window this block reads (stays inside the plane for the last block)
+        const int wcopy = (npos + 10 * P + 10 + 7) / 8 * 8;
+        mbar_arrive_expect_tx(bar, (uint32_t)wcopy * 2 + (CJ / 8) * npos * 16);
+        bulk_g2s(smem_u32(sS + st * wlen * 2), S + (size_t)b * plane_len + u0 - 5 * P - 5, (uint32_t)wcopy * 2, bar);
+        for (int c = 0; c < CJ / 8; ++c)
+            bulk_g2s(smem_u32(sB + st * BBYTES + c * kTwKB * 16),
+                     reinterpret_cast<const uint8_t*>(C) + (((size_t)b * (CJ / 8) + c) * plane_len + u0) * 16,
+                     npos * 16, bar);
+    };
     const int t = threadIdx.x;                                  // im2col row = tap
     const int dy = t / 11, dx = t % 11;
     const int base_t = SGN * ((dy - 5) * P + (dx - 5)) + 5 * P + 5;   // window index of position 0
     bool ok = true;
     int n = 0;
+    if (threadIdx.x == 0)
+        for (long long k = blk0; k < blk1 && k < blk0 + nst - 1; ++k) issue(k);
     for (long long k = blk0; k < blk1 && ok; ++k, ++n) {
-        const int b = (int)(k / nb_img);
+        const int st = n % nst;
         const int u0 = u_begin + (int)(k % nb_img) * kTwKB;
         const int npos = min(kTwKB, u_begin + HP16 - u0);
         if (threadIdx.x == 0) {
-            // the previous block's MMAs must be done before its operands are overwritten
+            // block n - 1's MMAs read sA and the stage block n + nst - 1 is about to fill
             if (n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag);
-            if (ok) {
-                const uint32_t bar = smem_u32(&ss->lbar);
-                // the part of the window this block reads (stays inside the plane for the last block)
-                const int wcopy = (npos + 10 * P + 10 + 7) / 8 * 8;
-                mbar_arrive_expect_tx(bar, (uint32_t)wcopy * 2 + (CJ / 8) * npos * 16);
-                bulk_g2s(smem_u32(sS), S + (size_t)b * plane_len + u0 - 5 * P - 5, (uint32_t)wcopy * 2, bar);
-                for (int c = 0; c < CJ / 8; ++c)
-                    bulk_g2s(smem_u32(sB + c * kTwKB * 16),
-                             reinterpret_cast<const uint8_t*>(C) + (((size_t)b * (CJ / 8) + c) * plane_len + u0) * 16,
-                             npos * 16, bar);
-                ok = mbar_wait(bar, n & 1, status, &ss->abort_flag);
-            }
+            if (ok && k + nst - 1 < blk1) issue(k + nst - 1);
+            if (ok) ok = mbar_wait(smem_u32(&ss->lbar[st]), (n / nst) & 1, status, &ss->abort_flag);
         }
         __syncthreads();
         ok = !ss->abort_flag;
         if (!ok) break;
         // im2col row t: S at window index base_t + position, 8 positions per chunk
-        const unsigned short* w16 = reinterpret_cast<const unsigned short*>(sS) + base_t;
-        for (int kc = 0; kc < npos / 8; ++kc) {
-            uint32_t u[4];
-#pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-                uint32_t lo, hi;
-                if (t < 121) {
-                    lo = w16[kc * 8 + 2 * e2];
-                    hi = w16[kc * 8 + 2 * e2 + 1];
-                } else {
-                    lo = hi = (SGN > 0 && t == 127) ? 0x3F80u : 0u;   // bf16 1.0 (bias row) or 0
-                }
-                u[e2] = lo | (hi << 16);
+        if (t < 121) {
+            const int o = base_t & 7;
+            const uint32_t a0 = smem_u32(sS + st * wlen * 2) + (uint32_t)(base_t & ~7) * 2u;
+            uint4 cur = lds128(a0);
+            for (int kc = 0; kc < npos / 8; ++kc) {
+                const uint4 nxt = lds128(a0 + 16u * (uint32_t)(kc + 1));
+                reinterpret_cast<uint4*>(sA)[kc * 128 + t] = tw_shift8(cur, nxt, o);
+                cur = nxt;
             }
-            reinterpret_cast<uint4*>(sA)[kc * 128 + t] = make_uint4(u[0], u[1], u[2], u[3]);
+        } else {
+            const uint32_t fill = (SGN > 0 && t == 127) ? 0x3F803F80u : 0u;   // bf16 1.0 (bias row) or 0
+            for (int kc = 0; kc < npos / 8; ++kc)
+                reinterpret_cast<uint4*>(sA)[kc * 128 + t] = make_uint4(fill, fill, fill, fill);
         }
         fence_proxy_async();
         __syncthreads();
@@ -265,14 +298,21 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
                                    ((uint32_t)(128 >> 4) << 24);
             for (int ks = 0; ks < npos / 16; ++ks) {
                 const uint64_t ad = sdesc(smem_u32(sA + ks * 2 * 2048), 2048, 128);
-                const uint64_t bd = sdesc(smem_u32(sB + ks * 256), 128, kTwKB * 16);
+                const uint64_t bd = sdesc(smem_u32(sB + st * BBYTES + ks * 256), 128, kTwKB * 16);
                 mma_bf16(tbase, ad, bd, idesc, (k == blk0 && ks == 0) ? 0u : 1u);
             }
             mma_commit(smem_u32(&ss->mbar));
         }
     }
-    // wait for the last MMAs, then write this CTA's partial
-    if (threadIdx.x == 0 && n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag) && ok;
+    // wait for the last MMAs and for copies still in flight, then write this CTA's partial
+    if (threadIdx.x == 0) {
+        if (n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag) && ok;
+        // copies issued for blocks this CTA did not reach (after an abort)
+        for (long long k = blk0 + n; k < blk1 && k < blk0 + n + nst - 1; ++k) {
+            const int m2 = (int)(k - blk0);
+            mbar_wait_drain(smem_u32(&ss->lbar[m2 % nst]), (m2 / nst) & 1);
+        }
+    }
     __syncthreads();
     tc_fence_after();
     ok = __all_sync(0xffffffffu, !ss->abort_flag);
@@ -618,22 +658,28 @@ int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, 
                  int* status, cudaStream_t st)
 {
     const int HP16 = (g.HP + 15) / 16 * 16;
-    const int wlen = (kTwKB + 10 * g.P + 10 + 7) / 8 * 8;
+    const int wlen = tw_wlen(g.P);
     const int CJ = conv1 ? 64 : 32;
-    const size_t smem = (size_t)(kTwKB / 8) * 128 * 16 + (size_t)(CJ / 8) * kTwKB * 16 + (size_t)wlen * 2 +
-                        sizeof(TwSmem) + 16;
+    // as many load stages as fit (wide images: fewer, down to one)
+    int nst = kTwStages;
+    auto smem_for = [&](int k) {
+        return (size_t)(kTwKB / 8) * 128 * 16 + (size_t)k * ((size_t)(CJ / 8) * kTwKB * 16 + (size_t)wlen * 2) +
+               sizeof(TwSmem) + 16;
+    };
+    while (nst > 1 && smem_for(nst) > 227 * 1024) --nst;
+    const size_t smem = smem_for(nst);
     if (smem > 227 * 1024) {
         set_error("weight gradient: image width %d too large for the shared-memory window", g.W);
         return DEEPINV_EUNSUPPORTED;
     }
     if (conv1) {
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tapwgrad_kernel<64, 1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
+        tapwgrad_kernel<64, 1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
         DI_LAUNCH_CHECK();
         tapwgrad_reduce_kernel<64><<<122, 64 * kTwGroups, 0, st>>>(part, kTwCtas, dw, db);
     } else {
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tapwgrad_kernel<32, -1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, part, status);
+        tapwgrad_kernel<32, -1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
         DI_LAUNCH_CHECK();
         tapwgrad_reduce_kernel<32><<<122, 32 * kTwGroups, 0, st>>>(part, kTwCtas, dw, nullptr);
     }
