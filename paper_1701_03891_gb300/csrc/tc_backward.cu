@@ -171,17 +171,22 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N)
 // plane itself (MN-major, bulk-copied).  Each CTA covers a run of 128-position
 // blocks, keeps its sum in TMEM and leaves a float32 partial.
 //
-// The window of S and the block of C a block reads arrive by bulk copies into a
-// ring of nst <= kTwStages stages (as many as shared memory holds), issued
-// nst - 1 blocks ahead; thread t builds im2col row
-// t from aligned 16-byte reads of the window, shifted into place (the shift is
-// the same for every chunk of the row).
+// Warps 0..3: thread t builds im2col row t of each block from aligned 16-byte
+// reads of the block's window of S, shifted into place (the shift is the same
+// for every chunk of the row), into one of two A buffers.  Warp 4 runs the
+// block pipeline: its lanes issue the bulk copies of a block's window and C
+// planes (one copy per lane) into one of two load stages as soon as the MMAs of
+// the block that last used the stage are done, and its lane 0 issues each
+// block's MMAs once the im2col warps have built its A.  With two stages (nst;
+// images too wide for two windows in shared memory take one) block n's MMAs
+// overlap block n + 1's im2col and block n + 2's copies.
 constexpr int kTwKB = 128;
-constexpr int kTwStages = 3;
+constexpr int kTwStages = 2;          // at most: load stages and A buffers
 constexpr int kTwCtas = 304;          // 2 per SM
+constexpr int kTwThreads = 160;
 
 struct TwSmem {
-    uint64_t lbar[kTwStages], mbar;
+    uint64_t lfull[kTwStages], afull[kTwStages], mdone[kTwStages];
     uint32_t tmem_base;
     int abort_flag;
 };
@@ -207,15 +212,15 @@ __device__ __forceinline__ uint4 tw_shift8(const uint4& a, const uint4& b, int o
 }
 
 template <int CJ, int SGN>
-__global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ S, const bf16* __restrict__ C,
-                                                       int B, int P, int HP16, int plane_len, int nst,
-                                                       float* __restrict__ part, int* status)
+__global__ void __launch_bounds__(kTwThreads) tapwgrad_kernel(const bf16* __restrict__ S, const bf16* __restrict__ C,
+                                                              int B, int P, int HP16, int plane_len, int nst,
+                                                              float* __restrict__ part, int* status)
 {
     constexpr uint32_t ABYTES = (kTwKB / 8) * 128 * 16;   // [16 chunks][128 rows][8]
     constexpr uint32_t BBYTES = (CJ / 8) * kTwKB * 16;    // [CJ/8 groups][128 positions][8]
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* sA = smem_raw;
-    uint8_t* sB = smem_raw + ABYTES;                      // [stage][BBYTES]
+    uint8_t* sA = smem_raw;                               // [stage][ABYTES]
+    uint8_t* sB = sA + nst * ABYTES;                      // [stage][BBYTES]
     const int wlen = tw_wlen(P);
     uint8_t* sS = sB + nst * BBYTES;                      // [stage][wlen] bf16
     TwSmem* ss = reinterpret_cast<TwSmem*>(sS + nst * wlen * 2);
@@ -223,15 +228,19 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
     const int nb_img = (HP16 + kTwKB - 1) / kTwKB;
     const long long total = (long long)B * nb_img;
     const long long blk0 = total * blockIdx.x / gridDim.x, blk1 = total * (blockIdx.x + 1) / gridDim.x;
+    const int nblk = (int)(blk1 - blk0);
     const int u_begin = kPad * P + kPad;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < nst; ++s) mbar_init(smem_u32(&ss->lbar[s]), 1);
-        mbar_init(smem_u32(&ss->mbar), 1);
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(smem_u32(&ss->lfull[s]), 1);
+            mbar_init(smem_u32(&ss->afull[s]), 128);
+            mbar_init(smem_u32(&ss->mdone[s]), 1);
+        }
         ss->abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 0) {
+    if (warp == 4) {
         tmem_alloc(smem_u32(&ss->tmem_base), CJ < 32 ? 32 : CJ);
         tmem_relinquish();
     }
@@ -239,95 +248,126 @@ __global__ void __launch_bounds__(128) tapwgrad_kernel(const bf16* __restrict__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = ss->tmem_base;
-    // block k's operands into stage (k - blk0) % nst (thread 0)
-    auto issue = [&](long long k) {
-        const int st = (int)((k - blk0) % nst);
-        const int b = (int)(k / nb_img);
-        const int u0 = u_begin + (int)(k % nb_img) * kTwKB;
-        const int npos = min(kTwKB, u_begin + HP16 - u0);
-        const uint32_t bar = smem_u32(&ss->lbar[st]);
-        // the part of the window this block reads (stays inside the plane for the last block)
-        const int wcopy = (npos + 10 * P + 10 + 7) / 8 * 8;
-        mbar_arrive_expect_tx(bar, (uint32_t)wcopy * 2 + (CJ / 8) * npos * 16);
-        bulk_g2s(smem_u32(sS + st * wlen * 2), S + (size_t)b * plane_len + u0 - 5 * P - 5, (uint32_t)wcopy * 2, bar);
-        for (int c = 0; c < CJ / 8; ++c)
-            bulk_g2s(smem_u32(sB + st * BBYTES + c * kTwKB * 16),
-                     reinterpret_cast<const uint8_t*>(C) + (((size_t)b * (CJ / 8) + c) * plane_len + u0) * 16,
-                     npos * 16, bar);
+    auto block_pos = [&](int n, int& b, int& u0, int& npos) {
+        const long long k = blk0 + n;
+        b = (int)(k / nb_img);
+        u0 = u_begin + (int)(k % nb_img) * kTwKB;
+        npos = min(kTwKB, u_begin + HP16 - u0);
     };
-    const int t = threadIdx.x;                                  // im2col row = tap
-    const int dy = t / 11, dx = t % 11;
-    const int base_t = SGN * ((dy - 5) * P + (dx - 5)) + 5 * P + 5;   // window index of position 0
     bool ok = true;
-    int n = 0;
-    if (threadIdx.x == 0)
-        for (long long k = blk0; k < blk1 && k < blk0 + nst - 1; ++k) issue(k);
-    for (long long k = blk0; k < blk1 && ok; ++k, ++n) {
-        const int st = n % nst;
-        const int u0 = u_begin + (int)(k % nb_img) * kTwKB;
-        const int npos = min(kTwKB, u_begin + HP16 - u0);
-        if (threadIdx.x == 0) {
-            // block n - 1's MMAs read sA and the stage block n + nst - 1 is about to fill
-            if (n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag);
-            if (ok && k + nst - 1 < blk1) issue(k + nst - 1);
-            if (ok) ok = mbar_wait(smem_u32(&ss->lbar[st]), (n / nst) & 1, status, &ss->abort_flag);
-        }
-        __syncthreads();
-        ok = !ss->abort_flag;
-        if (!ok) break;
-        // im2col row t: S at window index base_t + position, 8 positions per chunk
-        if (t < 121) {
-            const int o = base_t & 7;
-            const uint32_t a0 = smem_u32(sS + st * wlen * 2) + (uint32_t)(base_t & ~7) * 2u;
-            uint4 cur = lds128(a0);
-            for (int kc = 0; kc < npos / 8; ++kc) {
-                const uint4 nxt = lds128(a0 + 16u * (uint32_t)(kc + 1));
-                reinterpret_cast<uint4*>(sA)[kc * 128 + t] = tw_shift8(cur, nxt, o);
-                cur = nxt;
+    if (warp == 4) {
+        // ------------------------------------------------ copies and MMAs
+        // block n's window and C planes into stage n % nst: lane 0 the window, lane
+        // 1 + c the C plane c (lane 0 first sets the stage's byte count)
+        auto issue = [&](int n) {
+            int b, u0, npos;
+            block_pos(n, b, u0, npos);
+            const int st = n % nst;
+            const uint32_t bar = smem_u32(&ss->lfull[st]);
+            const int wcopy = (npos + 10 * P + 10 + 7) / 8 * 8;   // stays inside the plane for the last block
+            if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)wcopy * 2 + (CJ / 8) * npos * 16);
+            __syncwarp();
+            if (lane == 0)
+                bulk_g2s(smem_u32(sS + st * wlen * 2), S + (size_t)b * plane_len + u0 - 5 * P - 5,
+                         (uint32_t)wcopy * 2, bar);
+            else if (lane <= CJ / 8)
+                bulk_g2s(smem_u32(sB + st * BBYTES + (lane - 1) * kTwKB * 16),
+                         reinterpret_cast<const uint8_t*>(C) +
+                             (((size_t)b * (CJ / 8) + (lane - 1)) * plane_len + u0) * 16,
+                         npos * 16, bar);
+        };
+        for (int n = 0; n < nblk && n < nst; ++n) issue(n);
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(CJ >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+        for (int n = 0; n < nblk && ok; ++n) {
+            const int st = n % nst, use = n / nst;
+            int b, u0, npos;
+            block_pos(n, b, u0, npos);
+            ok = mbar_wait(smem_u32(&ss->afull[st]), use & 1, status, &ss->abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
             }
-        } else {
-            const uint32_t fill = (SGN > 0 && t == 127) ? 0x3F803F80u : 0u;   // bf16 1.0 (bias row) or 0
-            for (int kc = 0; kc < npos / 8; ++kc)
-                reinterpret_cast<uint4*>(sA)[kc * 128 + t] = make_uint4(fill, fill, fill, fill);
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(CJ >> 3) << 17) |
-                                   ((uint32_t)(128 >> 4) << 24);
-            for (int ks = 0; ks < npos / 16; ++ks) {
-                const uint64_t ad = sdesc(smem_u32(sA + ks * 2 * 2048), 2048, 128);
-                const uint64_t bd = sdesc(smem_u32(sB + st * BBYTES + ks * 256), 128, kTwKB * 16);
-                mma_bf16(tbase, ad, bd, idesc, (k == blk0 && ks == 0) ? 0u : 1u);
+            if (lane == 0) {
+                tc_fence_after();
+                for (int ks = 0; ks < npos / 16; ++ks) {
+                    const uint64_t ad = sdesc(smem_u32(sA + st * ABYTES + ks * 2 * 2048), 2048, 128);
+                    const uint64_t bd = sdesc(smem_u32(sB + st * BBYTES + ks * 256), 128, kTwKB * 16);
+                    mma_bf16(tbase, ad, bd, idesc, (n == 0 && ks == 0) ? 0u : 1u);
+                }
+                mma_commit(smem_u32(&ss->mdone[st]));
             }
-            mma_commit(smem_u32(&ss->mbar));
+            // stage st is free again once these MMAs are done: fill it with block n + nst
+            if (n + nst < nblk) {
+                ok = mbar_wait(smem_u32(&ss->mdone[st]), use & 1, status, &ss->abort_flag);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                issue(n + nst);
+            }
+        }
+        // the last MMAs, and copies in flight after an abort
+        if (lane == 0) {
+            for (int n = max(0, nblk - nst); n < nblk; ++n)
+                mbar_wait_drain(smem_u32(&ss->mdone[n % nst]), (n / nst) & 1);
+            for (int n = max(0, nblk - nst); n < nblk; ++n)
+                mbar_wait_drain(smem_u32(&ss->lfull[n % nst]), (n / nst) & 1);
+        }
+    } else {
+        // ------------------------------------------------ im2col (warps 0..3)
+        const int t = threadIdx.x;                              // im2col row = tap
+        const int dy = t / 11, dx = t % 11;
+        const int base_t = SGN * ((dy - 5) * P + (dx - 5)) + 5 * P + 5;   // window index of position 0
+        const int o = base_t & 7;
+        for (int n = 0; n < nblk && ok; ++n) {
+            const int st = n % nst, use = n / nst;
+            int b, u0, npos;
+            block_pos(n, b, u0, npos);
+            ok = mbar_wait(smem_u32(&ss->lfull[st]), use & 1, status, &ss->abort_flag);
+            // A buffer st was read by block n - nst's MMAs
+            if (ok && n >= nst)
+                ok = mbar_wait(smem_u32(&ss->mdone[st]), (use - 1) & 1, status, &ss->abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
+            }
+            uint4* dA = reinterpret_cast<uint4*>(sA + st * ABYTES);
+            if (t < 121) {
+                const uint32_t a0 = smem_u32(sS + st * wlen * 2) + (uint32_t)(base_t & ~7) * 2u;
+                uint4 cur = lds128(a0);
+                for (int kc = 0; kc < npos / 8; ++kc) {
+                    const uint4 nxt = lds128(a0 + 16u * (uint32_t)(kc + 1));
+                    dA[kc * 128 + t] = tw_shift8(cur, nxt, o);
+                    cur = nxt;
+                }
+            } else {
+                const uint32_t fill = (SGN > 0 && t == 127) ? 0x3F803F80u : 0u;   // bf16 1.0 (bias row) or 0
+                for (int kc = 0; kc < npos / 8; ++kc) dA[kc * 128 + t] = make_uint4(fill, fill, fill, fill);
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&ss->afull[st]));
         }
     }
-    // wait for the last MMAs and for copies still in flight, then write this CTA's partial
-    if (threadIdx.x == 0) {
-        if (n > 0) ok = mbar_wait(smem_u32(&ss->mbar), (n - 1) & 1, status, &ss->abort_flag) && ok;
-        // copies issued for blocks this CTA did not reach (after an abort)
-        for (long long k = blk0 + n; k < blk1 && k < blk0 + n + nst - 1; ++k) {
-            const int m2 = (int)(k - blk0);
-            mbar_wait_drain(smem_u32(&ss->lbar[m2 % nst]), (m2 / nst) & 1);
-        }
-    }
+    // this CTA's partial
     __syncthreads();
     tc_fence_after();
-    ok = __all_sync(0xffffffffu, !ss->abort_flag);
-    float* dst = part + ((size_t)blockIdx.x * 128 + warp * 32 + lane) * CJ;
-    for (int c0 = 0; c0 < CJ; c0 += 16) {
-        float v[16];
-        if (ok && n > 0) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c0, v);
-        else
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    ok = !ss->abort_flag;
+    if (warp < 4) {
+        float* dst = part + ((size_t)blockIdx.x * 128 + warp * 32 + lane) * CJ;
+        for (int c0 = 0; c0 < CJ; c0 += 16) {
+            float v[16];
+            if (ok && nblk > 0) tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + c0, v);
+            else
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4*>(dst + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 4) {
         tc_fence_after();
         tmem_dealloc(tbase, CJ < 32 ? 32 : CJ);
     }
@@ -660,13 +700,11 @@ int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, 
     const int HP16 = (g.HP + 15) / 16 * 16;
     const int wlen = tw_wlen(g.P);
     const int CJ = conv1 ? 64 : 32;
-    // as many load stages as fit (wide images: fewer, down to one)
-    int nst = kTwStages;
     auto smem_for = [&](int k) {
-        return (size_t)(kTwKB / 8) * 128 * 16 + (size_t)k * ((size_t)(CJ / 8) * kTwKB * 16 + (size_t)wlen * 2) +
+        return k * ((size_t)(kTwKB / 8) * 128 * 16 + (size_t)(CJ / 8) * kTwKB * 16 + (size_t)wlen * 2) +
                sizeof(TwSmem) + 16;
     };
-    while (nst > 1 && smem_for(nst) > 227 * 1024) --nst;
+    const int nst = smem_for(kTwStages) <= 227 * 1024 ? kTwStages : 1;
     const size_t smem = smem_for(nst);
     if (smem > 227 * 1024) {
         set_error("weight gradient: image width %d too large for the shared-memory window", g.W);
@@ -674,12 +712,12 @@ int tap_wgrad_tc(bool conv1, const bf16* S, const bf16* C, int B, const Geo& g, 
     }
     if (conv1) {
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tapwgrad_kernel<64, 1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
+        tapwgrad_kernel<64, 1><<<kTwCtas, kTwThreads, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
         DI_LAUNCH_CHECK();
         tapwgrad_reduce_kernel<64><<<122, 64 * kTwGroups, 0, st>>>(part, kTwCtas, dw, db);
     } else {
         DI_CUDA(cudaFuncSetAttribute(tapwgrad_kernel<32, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        tapwgrad_kernel<32, -1><<<kTwCtas, 128, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
+        tapwgrad_kernel<32, -1><<<kTwCtas, kTwThreads, smem, st>>>(S, C, B, g.P, HP16, g.plane, nst, part, status);
         DI_LAUNCH_CHECK();
         tapwgrad_reduce_kernel<32><<<122, 32 * kTwGroups, 0, st>>>(part, kTwCtas, dw, nullptr);
     }
