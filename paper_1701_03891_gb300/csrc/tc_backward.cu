@@ -80,48 +80,57 @@ __global__ void grad_plane_kernel(const float* __restrict__ g, int B, int H, int
     }
 }
 
-// Per-image channel sums of a chunked bf16 plane [B][C/8][plane][8] (C % 8 == 0)
-// or of a one-channel plane (C == 1): part[b][c] in float64.  One block per
-// (image, 8-channel chunk); float32 per thread, float64 across threads.
-__global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_len, double* __restrict__ part)
+// Channel sums of a chunked bf16 plane [B][C/8][plane][8] (C % 8 == 0) or of a
+// one-channel plane (C == 1), per image and segment of the plane:
+// part[b nseg + seg][c] in float64.  One block per (image, 8-channel chunk,
+// segment); each thread loads 16 bytes at a time (8 channels of a position, or
+// 8 positions of the one-channel plane), four loads in flight before they are
+// added (the same order of additions as one at a time); float32 per thread and
+// across a warp, float64 across warps and blocks.
+__global__ void plane_sum_kernel(const bf16* __restrict__ src, int C, int plane_len, int nseg,
+                                 double* __restrict__ part)
 {
-    const int b = blockIdx.x, ch = blockIdx.y;
+    const int b = blockIdx.x, ch = blockIdx.y, seg = blockIdx.z;
     const int nch = C == 1 ? 1 : C / 8;
+    // 16-byte units of this (image, chunk) plane and this block's segment of them
+    const int units = C == 1 ? plane_len / 8 : plane_len;
+    const int u_lo = (int)((long long)units * seg / nseg), u_hi = (int)((long long)units * (seg + 1) / nseg);
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + ((size_t)b * nch + ch) * plane_len * (C == 1 ? 1 : 8));
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (C == 1) {
-        for (int p = threadIdx.x; p < plane_len; p += blockDim.x)
-            acc[0] += __bfloat162float(src[(size_t)b * plane_len + p]);
-    } else {
-        const uint4* s4 = reinterpret_cast<const uint4*>(src + (((size_t)b * nch + ch) * plane_len) * 8);
-        // four positions of this thread's sequence loaded before they are added (the
-        // same order of additions as one at a time, with the loads in flight together)
-        const int bd = blockDim.x;
-        for (int p = threadIdx.x; p < plane_len; p += 4 * bd) {
-            uint4 u[4];
+    const int bd = blockDim.x;
+    for (int p = u_lo + threadIdx.x; p < u_hi; p += 4 * bd) {
+        uint4 u[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) u[k] = p + k * bd < plane_len ? s4[p + k * bd] : make_uint4(0, 0, 0, 0);
+        for (int k = 0; k < 4; ++k) u[k] = p + k * bd < u_hi ? s4[p + k * bd] : make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (p + k * bd >= plane_len) break;
-                const bf16* v = reinterpret_cast<const bf16*>(&u[k]);
+        for (int k = 0; k < 4; ++k) {
+            if (p + k * bd >= u_hi) break;
+            const bf16* v = reinterpret_cast<const bf16*>(&u[k]);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(v[e]);
-            }
+            for (int e = 0; e < 8; ++e) acc[e] += __bfloat162float(v[e]);
         }
+    }
+    // a fixed butterfly over the warp in float32 (float64 arithmetic is slow on this
+    // GPU), then the warps' sums in float64
+    const int nc = C == 1 ? 1 : 8;
+    if (C == 1) {
+#pragma unroll
+        for (int e = 1; e < 8; ++e) acc[0] += acc[e];
     }
     __shared__ double red[8][8];
     const int w = threadIdx.x / 32;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        double t = acc[e];
+        if (e >= nc) break;
+        float t = acc[e];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if ((threadIdx.x & 31) == 0) red[w][e] = t;
+        if ((threadIdx.x & 31) == 0) red[w][e] = (double)t;
     }
     __syncthreads();
     if (threadIdx.x < (C == 1 ? 1 : 8)) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += red[k][threadIdx.x];
-        part[(size_t)b * C + (C == 1 ? 0 : ch * 8 + threadIdx.x)] = t;
+        part[((size_t)b * nseg + seg) * C + (C == 1 ? 0 : ch * 8 + threadIdx.x)] = t;
     }
 }
 
@@ -420,9 +429,11 @@ int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st)
 
 int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st)
 {
-    plane_sum_kernel<<<dim3(B, C == 1 ? 1 : C / 8), 256, 0, st>>>(src, C, geo.plane, part);
+    // segments per plane: the partials fill part's B x 64 entries at most
+    const int nseg = C == 1 ? 16 : 64 / C;
+    plane_sum_kernel<<<dim3(B, C == 1 ? 1 : C / 8, nseg), 256, 0, st>>>(src, C, geo.plane, nseg, part);
     DI_LAUNCH_CHECK();
-    sum_parts_kernel<<<C, 32, 0, st>>>(part, B, C, out);
+    sum_parts_kernel<<<C, 32, 0, st>>>(part, B * nseg, C, out);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
