@@ -8,6 +8,8 @@
 //                       run by the forward kernels (conv1<32>, conv2 DGRAD);
 //   weight gradient: dW[dy][dx] = sum_u G[u] A[u + (dy-5) P + (dx-5)]^T over
 //                    plane positions u (G is zero off the data positions).
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -69,14 +71,19 @@ __global__ void pack_dgrad_weights_kernel(const float* __restrict__ w1, const fl
 }
 
 // Gradient plane of x^: gp[b][q + 5 P + 5] = g[b][r n2 + c], q = r P + c (other entries untouched).
+// Images over grid.y (striding past 65535), pixels over grid.x: 32-bit index
+// arithmetic within an image.
 __global__ void grad_plane_kernel(const float* __restrict__ g, int B, int H, int W, int P, int plane_len,
                                   bf16* __restrict__ gp)
 {
-    const long long n = (long long)B * H * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % W), r = (int)((i / W) % H);
-        const long long b = i / ((long long)W * H);
-        gp[(size_t)b * plane_len + (size_t)r * P + c + kPad * P + kPad] = __float2bfloat16_rn(g[i]);
+    const int N = H * W;
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const float* gi = g + (size_t)b * N;
+        bf16* pi = gp + (size_t)b * plane_len + kPad * P + kPad;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+            const int r = j / W, c = j - r * W;
+            pi[r * P + c] = __float2bfloat16_rn(gi[j]);
+        }
     }
 }
 
@@ -421,8 +428,10 @@ int pack_dgrad_weights(const float* w1, const float* w2, const float* w3, bf16* 
 
 int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st)
 {
-    const long long n = (long long)B * geo.H * geo.W;
-    grad_plane_kernel<<<grid_for(n), 256, 0, st>>>(g, B, geo.H, geo.W, geo.P, geo.plane, gp);
+    if (B <= 0) return DEEPINV_OK;
+    const int N = geo.H * geo.W;
+    dim3 grid((unsigned)std::min((N + 255) / 256, 64), (unsigned)std::min(B, 65535));
+    grad_plane_kernel<<<grid, 256, 0, st>>>(g, B, geo.H, geo.W, geo.P, geo.plane, gp);
     DI_LAUNCH_CHECK();
     return DEEPINV_OK;
 }
