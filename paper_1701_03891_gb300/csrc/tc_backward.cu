@@ -438,8 +438,9 @@ int grad_plane(const float* g, int B, const Geo& geo, bf16* gp, cudaStream_t st)
 
 int plane_channel_sums(const bf16* src, int B, int C, const Geo& geo, double* part, float* out, cudaStream_t st)
 {
-    // segments per plane: the partials fill part's B x 64 entries at most
-    const int nseg = C == 1 ? 16 : 64 / C;
+    // segments per plane (the partials fill part's B x 64 entries at most); the
+    // one-channel plane's partials are all added by one warp, so it takes fewer
+    const int nseg = C == 1 ? 4 : 64 / C;
     plane_sum_kernel<<<dim3(B, C == 1 ? 1 : C / 8, nseg), 256, 0, st>>>(src, C, geo.plane, nseg, part);
     DI_LAUNCH_CHECK();
     sum_parts_kernel<<<C, 32, 0, st>>>(part, B * nseg, C, out);
